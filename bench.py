@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the catalog shift-and-stack hot path (Sec. 2.1 steps 1-3) on GB300.
+
+One step = one full search (ingest, bucket, shift tables, stack, exact counts,
+ordering, contributing ids) over the DECam-CCD-like outer-solar-system field:
+2048x4096 px, 100 epochs over 4 h, 3000 noise detections per epoch plus 200
+injected movers, a 111x111 velocity lattice (364 mpx/h spacing), 2 px bins,
+N_min = 25.  The metric is detection-shifts per second: in-domain
+(detection, velocity) pairs processed per second.
+
+  value     device-resident inputs, CUDA events around each step on the stream
+            the library launches on, L2 flushed (256 MiB write) between steps
+  e2e       the same search through the C ABI with pinned host buffers: the
+            host->device copy of the catalog and the device->host copy of the
+            candidates and ids are inside the timed region (wall clock)
+  roofline  the stack kernel against the shared-memory atomic peak measured in
+            this run by the library's probe (one atomic per detection-shift)
+
+--impl reference times the CPU oracle (the plain definition, single thread) on
+a bounded lattice-row sample of the same workload.
+Multi-GPU (torchrun): each rank searches its own field (weak scaling); the
+only collectives are the timing barrier and the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_26279_gb300 import workloads as W  # noqa: E402
+
+METRIC = "detection-shifts/s"
+UNIT = "det-shifts/s"
+L2_FLUSH_BYTES = 256 << 20
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def workload_desc(w: W.Workload, cat) -> dict:
+    r, g = w.recipe, w.grid
+    return {
+        "workload": (f"{w.name}: {r.width_px}x{r.height_px} px, {r.n_epochs} epochs over "
+                     f"{r.span_h:g} h, {r.noise_per_epoch} noise/epoch + {r.n_movers} movers, "
+                     f"{g.nvx}x{g.nvy} velocity lattice at {g.dvx} mpx/h, bin {g.bin / 1000:g} px, "
+                     f"N_min {w.n_min}"),
+        "n_detections": int(cat.n),
+        "n_velocities": int(g.nvx * g.nvy),
+        "seed": int(w.seed),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stack_traffic(n_pairs: int):
+    """DRAM bytes per stack launch from the committed ncu summary, if it was taken
+    on the current stack kernel source; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "stack_traffic.json")
+    src = os.path.join(ROOT, "paper_2509_26279_gb300", "csrc", "sas_stack.cu")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("stack_source_sha256") != h:
+            return None
+        return int(d["dram_bytes_per_launch_full_size"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def cpu_baseline(w: W.Workload, cat, budget_s: float = 15.0) -> dict:
+    """The oracle as it stands, single thread, on whole lattice rows of the same
+    workload, grown until about `budget_s` seconds of CPU work."""
+    import oracle
+    g = w.grid
+    rows, pairs, secs = 0, 0, 0.0
+    row = g.nvy // 2
+    while secs < budget_s and rows < g.nvy:
+        ky = (row + rows) % g.nvy
+        t0 = time.perf_counter()
+        r = oracle.stack(cat, g, w.n_min, ky * g.nvx, (ky + 1) * g.nvx)
+        secs += time.perf_counter() - t0
+        pairs += r.n_pairs
+        rows += 1
+    return {"value": pairs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rows} lattice rows x {g.nvx} velocities of the same field "
+                      f"({pairs} detection-shifts in {secs:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = W.decam_tno()
+    cat = W.load(w)
+    import oracle
+    g = w.grid
+    per_step = 12                      # lattice points per step (about a second of CPU)
+    nv = g.nvx * g.nvy
+    def step(i):
+        a = (nv // 2 + i * per_step) % (nv - per_step)
+        t0 = time.perf_counter()
+        pairs = oracle.stack(cat, g, w.n_min, a, a + per_step).n_pairs
+        return pairs, time.perf_counter() - t0
+    for i in range(args.warmup):
+        step(i)
+    tot_p, tot_s = 0, 0.0
+    for i in range(args.steps):
+        p, s = step(args.warmup + i)
+        tot_p += p
+        tot_s += s
+    v = tot_p / tot_s
+    cfg = workload_desc(w, cat)
+    cfg["sample"] = f"{per_step} consecutive lattice points of the field per step"
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": cfg["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="decam_tno", choices=["decam_tno", "fast_movers", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2509_26279_gb300 import sas
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = getattr(W, args.workload)()
+    w = W.Workload(w.name, w.recipe, w.grid, w.n_min, w.seed + 1000 * rank)  # own field per rank
+    cat = W.load(w)
+    grid = sas.Grid(w.grid)
+    stream = torch.cuda.current_stream(dev)
+    dx = torch.from_numpy(cat.x).to(dev)
+    dy = torch.from_numpy(cat.y).to(dev)
+    de = torch.from_numpy(cat.epoch.view(np.int16)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def dev_step():
+        return sas.sas_stack(grid, dx, dy, de, cat.t, cat.ticks_per_hour, w.n_min,
+                             on_device=True, stream=stream)
+
+    for _ in range(args.warmup):
+        r = dev_step()
+        info0 = r.info()
+        r.free()
+    peak_ops, probe_mhz = sas.sas_probe_shared_atomic_peak(2048, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stack_ms, pairs = [], []
+    launches0 = sas.sas_kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()                          # L2 flush, outside the timed step
+            ev[i][0].record(stream)
+            r = dev_step()
+            ev[i][1].record(stream)
+            inf = r.info()
+            stack_ms.append(inf["ms_stack"])
+            pairs.append(inf["n_pairs"])
+            r.free()
+        barrier()
+    launches = sas.sas_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_pairs = int(pairs[0])
+    assert all(p == n_pairs for p in pairs), "detection-shift count changed between steps"
+    value = n_pairs * args.steps * world / (total_ms * 1e-3)
+
+    # end-to-end through host buffers (pinned), copies inside the timed region
+    hx = torch.from_numpy(cat.x).pin_memory()
+    hy = torch.from_numpy(cat.y).pin_memory()
+    he = torch.from_numpy(cat.epoch.view(np.int16)).pin_memory()
+    hxn, hyn, hen = hx.numpy(), hy.numpy(), he.numpy().view(np.uint16)
+    e2e_s, d2h = 0.0, 0
+    for i in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = sas.sas_stack(grid, hxn, hyn, hen, cat.t, cat.ticks_per_hour, w.n_min, stream=stream)
+        cands, ids = r.candidates()
+        e2e_s += time.perf_counter() - t0
+        d2h = cands.nbytes + ids.nbytes
+        r.free()
+        n_e2e = i + 1
+    e2e_value = n_pairs * n_e2e * world / e2e_s
+    h2d = cat.n * 10 + cat.n_epochs * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    achieved = n_pairs / (statistics.mean(stack_ms) * 1e-3)
+    roof = {"bound": "smem_atomic", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+            "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": stack_traffic(n_pairs),
+            "kernel": "k_stack", "stack_ms": statistics.mean(stack_ms),
+            "peak_source": f"sas_probe_shared_atomic_peak, this run ({probe_mhz:.0f} MHz)"}
+    cfg = workload_desc(w, cat)
+    cfg.update({"l2": "flushed between steps (256 MiB write)", "n_pairs_per_step": n_pairs,
+                "candidates": int(info0["n_candidates"]),
+                "tile": [info0["tile_kx"], info0["tile_ky"], info0["tile_bx"], info0["tile_by"]],
+                "counter_bits": int(info0["counter_bits"]), "parallelism": f"replicas{world}"})
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+           "config": cfg, "clocks": clk.summary(),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": int(launches), "roofline": roof}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, cat, args.cpu_budget_s)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

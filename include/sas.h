@@ -1,0 +1,197 @@
+/*
+ * sas.h -- C ABI of the GB300 (sm_103a) catalog shift-and-stack library.
+ *
+ * The operation (Stetzler et al., "An Efficient Shift-and-Stack Algorithm
+ * Applied to Detection Catalogs", Sec. 2.1): given a detection catalog
+ * C = [x_i, y_i, t_i], a set of hypothesis velocities V, a clustering radius
+ * (bin size) Delta-x and a threshold N_min,
+ *   1. Project every detection to the reference epoch t0 = the earliest time
+ *      in the catalog:  x' = x - floor(vx (t - t0) / TPH),  y' likewise
+ *      (linear motion model, Sec. 2 Eq. 1-2; residuals Eq. 3-8);
+ *   2. Cluster: for every velocity build a 2-D histogram of the projected
+ *      positions at resolution Delta-x; a cell counts the DISTINCT epochs of
+ *      the detections in it (and the raw number of detections);
+ *   3. Find clusters, in threshold form: every cell with at least N_min
+ *      distinct epochs is a candidate, together with the ids of all the
+ *      detections that contributed to it.
+ * Candidates come out ordered by (distinct desc, raw desc, v_idx asc, by asc,
+ * bx asc) -- Sec. 3.3 ranks clusters by their number of detections -- and may be
+ * cut to the first K (the paper keeps the first 1000).
+ *
+ * Integer fixed point, so every step is exact:
+ *   positions  int32 milli-pixels (mpx)      velocities  int32 mpx per hour
+ *   times      int64 ticks, ticks_per_hour (TPH) > 0
+ *   shift      floor(v * (t - t0) / TPH)     bin  floor((x' - x_min) / bin)
+ * ("floor" is the mathematical floor, also for negative values; bins are
+ * half-open.)
+ *
+ * Exact-integer limits (violations return SAS_ERR_RANGE, nothing is computed):
+ *   |x|, |y| < 2^29 for every detection;  |x_min|, |y_min| < 2^28;
+ *   nbx*bin < 2^28 and nby*bin < 2^28;    nvx*nvy < 2^31;
+ *   |shift| < 2^28 for every lattice velocity and every epoch that has a
+ *   detection;  max(t) - min(t) < 2^32;  n < 2^31;  1 <= E <= SAS_MAX_EPOCHS.
+ *
+ * Threading and streams: every call enqueues its device work on the caller's
+ * CUDA stream (NULL = the legacy default stream) and returns when its outputs
+ * are complete.  Handles are not safe for concurrent use from several threads.
+ * Errors: every entry point returns a sas_status; sas_last_error() gives a
+ * message (thread-local, valid until the next call on that thread).
+ */
+#ifndef SAS_H_
+#define SAS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAS_ABI_VERSION 1
+#define SAS_MAX_EPOCHS 1024
+
+typedef enum sas_status {
+  SAS_OK = 0,
+  SAS_ERR_ARG = 1,       /* null pointer, zero size or inconsistent descriptor      */
+  SAS_ERR_RANGE = 2,     /* an input is outside the exact-integer limits above      */
+  SAS_ERR_OVERFLOW = 3,  /* a caller buffer is too small; the needed sizes are set  */
+  SAS_ERR_CUDA = 4,      /* CUDA runtime error (message in sas_last_error)          */
+  SAS_ERR_OOM = 5,       /* device or host allocation failed                        */
+  SAS_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up                      */
+  SAS_ERR_INTERNAL = 7   /* internal invariant violated (a bug: please report)      */
+} sas_status;
+
+/* Velocity lattice and histogram domain (the set V and the bin size Delta-x of
+ * Sec. 2.1; the lattice spacing follows the bound Delta-v <= Delta-x / Delta-t
+ * of Sec. 2, Eq. 15-16).  Lattice point (kx, ky), 0 <= kx < nvx, 0 <= ky < nvy,
+ * has velocity (vx0 + kx*dvx, vy0 + ky*dvy) mpx/h and index v_idx = ky*nvx + kx.
+ * If speed_min or speed_max is nonzero only lattice points with
+ * speed_min^2 <= vx^2 + vy^2 <= speed_max^2 are searched ("all on-sky angles"
+ * over a rate range, Sec. 3.3); v_idx numbering is unchanged.  The histogram
+ * covers [x_min, x_min + nbx*bin) x [y_min, y_min + nby*bin) mpx; projections
+ * outside it are dropped. */
+typedef struct sas_grid_desc {
+  int32_t vx0, vy0;
+  int32_t dvx, dvy;          /* any sign, zero allowed                            */
+  uint32_t nvx, nvy;         /* >= 1                                              */
+  int32_t speed_min;         /* mpx/h, >= 0                                       */
+  int32_t speed_max;         /* mpx/h, >= speed_min (both 0 = whole lattice)      */
+  int32_t x_min, y_min;      /* mpx                                               */
+  uint32_t nbx, nby;         /* >= 1                                              */
+  int32_t bin;               /* mpx, >= 1                                         */
+} sas_grid_desc;
+
+/* Detection catalog C = [x_i, y_i, t_i] (Sec. 2.1), structure of arrays.
+ * Detection i was observed at time t[epoch[i]].  The caller owns every array.
+ * With on_device = 1, x, y and epoch are device pointers (the library only
+ * reads them, during the call); with on_device = 0 they are host pointers and
+ * are copied.  t is always a host array of n_epochs entries. */
+typedef struct sas_catalog {
+  uint64_t n;
+  const int32_t* x;          /* [n] mpx                                           */
+  const int32_t* y;          /* [n] mpx                                           */
+  const uint16_t* epoch;     /* [n] each < n_epochs                               */
+  uint32_t n_epochs;         /* E                                                 */
+  const int64_t* t;          /* [E] ticks, host memory                            */
+  int64_t ticks_per_hour;    /* TPH                                               */
+  int32_t on_device;
+  int32_t reserved;
+} sas_catalog;
+
+/* Optional knobs of sas_stack (pass NULL for defaults).  Tile fields of 0 let
+ * the library choose (built-in table or the autotuner cache). */
+typedef struct sas_opts {
+  uint64_t v_begin, v_end;   /* search only lattice indices [v_begin, v_end); 0,0 = all */
+  uint64_t max_candidates;   /* keep the first K candidates in output order; 0 = all    */
+  uint32_t tile_kx, tile_ky; /* velocities per tile (kx a multiple of 4, <= 8 each)     */
+  uint32_t tile_bx, tile_by; /* bins per tile                                           */
+  uint32_t counter_bits;     /* 8, 16 or 32; 0 = choose                                 */
+  uint32_t coarse_bins;      /* spatial bucket size in bins; 0 = choose                 */
+  uint32_t ctas_per_sm;      /* 0 = choose                                              */
+  uint32_t reserved;
+} sas_opts;
+
+/* One candidate trajectory: the cell (v_idx, bx, by) of the 3-D histogram with
+ * count >= N_min distinct epochs, its raw number of detections and the range
+ * [id_off, id_off + id_len) of its contributing detection ids (ascending
+ * indices into the caller's catalog arrays) in the id array.  id_len == raw. */
+typedef struct sas_candidate {
+  uint32_t v_idx;
+  uint32_t bx, by;
+  uint32_t count;            /* distinct epochs                                   */
+  uint32_t raw;              /* detections                                        */
+  uint32_t id_len;
+  uint64_t id_off;
+} sas_candidate;
+
+/* Summary of a finished search. */
+typedef struct sas_result_info {
+  uint64_t n_candidates;     /* after the optional top-K cut                      */
+  uint64_t n_ids;            /* total contributing ids of those candidates        */
+  uint64_t n_pairs;          /* in-domain (detection, velocity) pairs = detection-shifts */
+  uint64_t n_emitted;        /* cells that crossed the counter threshold (superset) */
+  int64_t t0;                /* reference epoch (ticks)                           */
+  uint32_t counter_bits;     /* counter width the stack kernel ran with           */
+  uint32_t tile_kx, tile_ky, tile_bx, tile_by;
+  uint32_t reserved;
+  float ms_stack;            /* device time of the stack kernel (CUDA events)     */
+  float ms_total;            /* device time of the whole call                     */
+} sas_result_info;
+
+typedef struct sas_grid sas_grid;      /* opaque, owned by the library */
+typedef struct sas_result sas_result;  /* opaque, owned by the library */
+
+/* Library version string and the ABI version it implements. */
+const char* sas_version(void);
+int sas_abi_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads): a diagnostic for counting launches per search. */
+uint64_t sas_kernel_launches(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sas_last_error(void);
+
+/* Validate a grid descriptor and return a handle (host memory only).
+ * Errors: SAS_ERR_ARG (null, zero sizes, speed_max < speed_min),
+ * SAS_ERR_RANGE (limits above).  *out is untouched on error. */
+int sas_create_grid(const sas_grid_desc* desc, sas_grid** out);
+void sas_destroy_grid(sas_grid* grid);
+
+/* Run the search (Sec. 2.1 steps 1-3) on the current CUDA device.
+ * grid, cat: see above.  n_min >= 1.  opts may be NULL.  stream: a
+ * cudaStream_t (NULL = legacy default).  On success *out holds a new result
+ * that the caller releases with sas_result_free; the result owns its device
+ * memory.  The call synchronizes the stream before returning.
+ * Errors: SAS_ERR_ARG, SAS_ERR_RANGE (catalog or shifts out of limits, or an
+ * epoch index >= n_epochs), SAS_ERR_OOM, SAS_ERR_CUDA; *out is untouched. */
+int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
+              const sas_opts* opts, void* stream, sas_result** out);
+
+int sas_result_get_info(const sas_result* result, sas_result_info* info);
+
+/* Copy the candidates and their ids out of a result, in output order.
+ * out[0..min(cap, n)) and ids[0..min(ids_cap, n_ids)) are written; *n_total
+ * and *n_ids_total (either may be NULL) receive the full sizes.  With
+ * on_device = 1 the destinations are device pointers.  Returns
+ * SAS_ERR_OVERFLOW (after the partial copy) when cap or ids_cap is too small;
+ * out or ids may be NULL with cap or ids_cap 0 to query sizes. */
+int sas_candidates(const sas_result* result, sas_candidate* out, uint64_t cap,
+                   uint64_t* n_total, uint32_t* ids, uint64_t ids_cap,
+                   uint64_t* n_ids_total, int on_device);
+
+void sas_result_free(sas_result* result);
+
+/* Measurement utility: throughput of conflict-free 32-bit shared-memory
+ * atomicAdd on every SM of the current device, in operations per second,
+ * measured with CUDA events over `iters` operations per thread; this is the
+ * peak against which the stack kernel's detection-shifts/s are compared.
+ * Also reports the median SM clock (MHz) implied by clock64() over the run. */
+int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s,
+                                 double* sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAS_H_ */

@@ -1,0 +1,600 @@
+// C ABI of the shift-and-stack library: validation, planning and the launch
+// sequence of one search (Sec. 2.1 steps 1-3).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sas_internal.cuh"
+
+using namespace sas;
+
+struct sas_grid {
+  sas_grid_desc d;
+};
+
+struct sas_result {
+  int device;
+  sas_candidate* d_cands;
+  uint32_t* d_ids;
+  sas_result_info info;
+};
+
+namespace sas {
+std::atomic<unsigned long long> g_launches{0};
+void note_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace sas
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? SAS_ERR_OOM : SAS_ERR_CUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+
+struct DevInfo {
+  int sms = 0;
+  int smem_optin = 0;
+  int smem_per_sm = 0;
+  bool ready = false;
+};
+
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+
+int device_info(int dev, DevInfo* out) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev < 0 || dev >= 64) return fail(SAS_ERR_ARG, "device ordinal %d out of range", dev);
+  DevInfo& d = g_dev[dev];
+  if (!d.ready) {
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // Keep freed stream-ordered allocations cached in the pool between calls.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    d.ready = true;
+  }
+  *out = d;
+  return SAS_OK;
+}
+
+// Stream-ordered scratch, released when the search returns.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+};
+
+bool fits_i32(int64_t v) { return v >= INT32_MIN && v <= INT32_MAX; }
+
+uint32_t magic_for(int32_t bin) {  // ceil(2^32 / bin) for bin >= 2
+  return (uint32_t)(((uint64_t)1 << 32) / (uint64_t)bin + 1);
+}
+
+// (X_max) * (magic * bin - 2^32) < 2^32 makes umulhi(X, magic) == X / bin for X <= X_max.
+bool magic_exact(int32_t bin, int64_t x_max) {
+  if (bin == 1) return true;
+  const uint64_t m = magic_for(bin);
+  const uint64_t err = m * (uint64_t)bin - ((uint64_t)1 << 32);
+  return (unsigned __int128)x_max * err < ((unsigned __int128)1 << 32);
+}
+
+constexpr int kSegCap = 1024;
+constexpr int kEmitCap = 256;
+constexpr int kStackThreads = 512;
+
+struct Plan {
+  TileCfg tc;
+  CoarseGeom cg;
+  int ky_lo, ky_hi;
+};
+
+// Upper bound of |floor(v*dt/TPH) - floor(v'*dt/TPH)| over dt in [0, dT] for
+// |v - v'| <= dv_span.
+int64_t spread_bound(int64_t dv_span, int64_t dT, int64_t tph) {
+  const long double s = (long double)dv_span * (long double)dT / (long double)tph + 2.0L;
+  return s > (long double)kLimDomain ? kLimDomain : (int64_t)s;
+}
+
+int choose_tiles(const sas_grid_desc& d, uint32_t E, int64_t dT, int64_t tph, int kx, int ky,
+                 int cb, int ctas, const sas_opts& o, const DevInfo& di, const CoarseGeom* fixed_cg,
+                 Plan* p) {
+  if (!stack_config_supported(kx, ky, cb))
+    return fail(SAS_ERR_ARG, "unsupported tile (kx=%d, ky=%d, counter_bits=%d)", kx, ky, cb);
+  TileCfg tc{};
+  tc.kx = kx;
+  tc.ky = ky;
+  tc.cb = cb;
+  tc.nt = kStackThreads;
+  tc.ctas_per_sm = ctas;
+  tc.seg_cap = kSegCap;
+  tc.emit_cap = kEmitCap;
+  const int64_t budget =
+      std::min<int64_t>(di.smem_optin, (int64_t)di.smem_per_sm / ctas - 1024);
+  const int64_t spread_y = spread_bound((int64_t)(ky - 1) * std::llabs((int64_t)d.dvy), dT, tph);
+  int ec = (int)std::min<uint32_t>(E, 256);
+  int tx = (int)o.tile_bx, ty = (int)o.tile_by;
+  for (int iter = 0; iter < 64; ++iter) {
+    tc.ec = ec;
+    tc.tx = tx > 0 ? tx : 4;
+    tc.ty = ty > 0 ? ty : 4;
+    const int64_t fixed = (int64_t)stack_smem_bytes(tc) - (int64_t)ky * kx * tc.tx * tc.ty * cb / 8;
+    if (tx <= 0 || ty <= 0) {
+      const int64_t cells = budget - fixed;
+      int side = (int)std::sqrt((double)cells * 8.0 / ((double)kx * ky * cb));
+      side &= ~3;
+      tc.tx = std::min<int>(side, ((int)d.nbx + 3) & ~3);
+      tc.ty = std::min<int>(side, ((int)d.nby + 3) & ~3);
+      if (tc.tx < 4) tc.tx = 4;
+      if (tc.ty < 4) tc.ty = 4;
+      // use the room a narrow domain leaves along one axis for the other
+      if (tc.tx < side) tc.ty = std::min<int>(((int)(cells * 8 / ((int64_t)kx * ky * cb * tc.tx))) & ~3,
+                                              ((int)d.nby + 3) & ~3);
+      if (tc.ty < side && tc.tx == side)
+        tc.tx = std::min<int>(((int)(cells * 8 / ((int64_t)kx * ky * cb * tc.ty))) & ~3,
+                              ((int)d.nbx + 3) & ~3);
+      tc.tx = std::max(tc.tx, 4);
+      tc.ty = std::max(tc.ty, 4);
+    }
+    if (((int64_t)tc.tx * tc.ty) % 4 != 0)
+      return fail(SAS_ERR_ARG, "tile_bx * tile_by must be a multiple of 4");
+    while (!magic_exact(d.bin, (int64_t)std::max(tc.tx, tc.ty) * d.bin - 1) && tc.tx > 4 && tc.ty > 4) {
+      tc.tx = std::max(4, (tc.tx / 2) & ~3);
+      tc.ty = std::max(4, (tc.ty / 2) & ~3);
+    }
+    if (!magic_exact(d.bin, (int64_t)std::max(tc.tx, tc.ty) * d.bin - 1))
+      return fail(SAS_ERR_RANGE, "bin %d too large for exact reciprocal division", d.bin);
+    // coarse bucket cell
+    CoarseGeom cg{};
+    if (fixed_cg) {
+      cg = *fixed_cg;
+    } else {
+      int cbins = o.coarse_bins > 0 ? (int)o.coarse_bins : std::max(1, tc.ty / 4);
+      int64_t cell = (int64_t)cbins * d.bin;
+      // by default a tile's source window spans at most about 8 bucket rows
+      if (o.coarse_bins == 0) cell = std::max<int64_t>(cell, ((int64_t)tc.ty * d.bin + spread_y + 7) / 8);
+      cg.cell = (int32_t)std::min<int64_t>(cell, kLimDomain);
+    }
+    const int64_t rows = ((int64_t)tc.ty * d.bin + spread_y) / cg.cell + 2;
+    if (rows > kSegCap) {
+      if (fixed_cg) return fail(SAS_ERR_INTERNAL, "segment rows exceed capacity");
+      return fail(SAS_ERR_ARG, "coarse_bins too small for this tile (%lld rows)", (long long)rows);
+    }
+    int new_ec = (int)std::min<int64_t>(std::min<int64_t>(E, kStackThreads), kSegCap / rows);
+    if (new_ec < 1) new_ec = 1;
+    tc.ec = new_ec;
+    tc.smem = stack_smem_bytes(tc);
+    if ((int64_t)tc.smem > budget) {
+      if (tx > 0 && ty > 0) return fail(SAS_ERR_ARG, "tile does not fit in shared memory");
+      // shrink and retry
+      tx = tx > 0 ? tx : std::max(4, (tc.tx - 4) & ~3);
+      ty = ty > 0 ? ty : std::max(4, (tc.ty - 4) & ~3);
+      continue;
+    }
+    p->tc = tc;
+    p->cg = cg;
+    return SAS_OK;
+  }
+  return fail(SAS_ERR_INTERNAL, "could not size the stack tile");
+}
+
+int64_t ceil_div64(int64_t a, int64_t b) { return -floor_div64(-a, b); }
+
+}  // namespace
+
+extern "C" {
+
+const char* sas_version(void) { return "sas-gb300 0.1 (sm_103a)"; }
+int sas_abi_version(void) { return SAS_ABI_VERSION; }
+uint64_t sas_kernel_launches(void) { return sas::g_launches.load(); }
+const char* sas_last_error(void) { return g_err.c_str(); }
+
+int sas_create_grid(const sas_grid_desc* desc, sas_grid** out) {
+  if (!desc || !out) return fail(SAS_ERR_ARG, "null argument");
+  const sas_grid_desc& d = *desc;
+  if (d.nvx < 1 || d.nvy < 1 || d.nbx < 1 || d.nby < 1 || d.bin < 1)
+    return fail(SAS_ERR_ARG, "lattice and domain sizes and the bin must be >= 1");
+  if (d.speed_min < 0 || d.speed_max < d.speed_min)
+    return fail(SAS_ERR_ARG, "need 0 <= speed_min <= speed_max");
+  if ((uint64_t)d.nvx * d.nvy >= ((uint64_t)1 << 31))
+    return fail(SAS_ERR_RANGE, "nvx*nvy must be < 2^31");
+  if (std::llabs((int64_t)d.x_min) >= kLimDomain || std::llabs((int64_t)d.y_min) >= kLimDomain)
+    return fail(SAS_ERR_RANGE, "|x_min|, |y_min| must be < 2^28");
+  if ((int64_t)d.nbx * d.bin >= kLimDomain || (int64_t)d.nby * d.bin >= kLimDomain)
+    return fail(SAS_ERR_RANGE, "nbx*bin and nby*bin must be < 2^28");
+  if (!fits_i32((int64_t)d.vx0 + (int64_t)(d.nvx - 1) * d.dvx) ||
+      !fits_i32((int64_t)d.vy0 + (int64_t)(d.nvy - 1) * d.dvy))
+    return fail(SAS_ERR_RANGE, "lattice velocities must fit in int32");
+  sas_grid* g = new (std::nothrow) sas_grid;
+  if (!g) return fail(SAS_ERR_OOM, "host allocation");
+  g->d = d;
+  *out = g;
+  return SAS_OK;
+}
+
+void sas_destroy_grid(sas_grid* grid) { delete grid; }
+
+int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* opts,
+              void* stream, sas_result** out) {
+  if (!grid || !cat || !out) return fail(SAS_ERR_ARG, "null argument");
+  const sas_grid_desc& d = grid->d;
+  const uint32_t E = cat->n_epochs;
+  const uint64_t n = cat->n;
+  if (n_min < 1) return fail(SAS_ERR_ARG, "n_min must be >= 1");
+  if (E < 1 || E > SAS_MAX_EPOCHS) return fail(SAS_ERR_RANGE, "n_epochs must be in [1, %d]", SAS_MAX_EPOCHS);
+  if (!cat->t) return fail(SAS_ERR_ARG, "null epoch time table");
+  if (cat->ticks_per_hour <= 0) return fail(SAS_ERR_ARG, "ticks_per_hour must be > 0");
+  if (n >= ((uint64_t)1 << 31)) return fail(SAS_ERR_RANGE, "n must be < 2^31");
+  if (n > 0 && (!cat->x || !cat->y || !cat->epoch)) return fail(SAS_ERR_ARG, "null catalog array");
+  sas_opts o{};
+  if (opts) o = *opts;
+  const uint64_t nv = (uint64_t)d.nvx * d.nvy;
+  uint64_t v_begin = o.v_begin, v_end = o.v_end;
+  if (v_begin == 0 && v_end == 0) v_end = nv;
+  if (v_begin > v_end || v_end > nv) return fail(SAS_ERR_ARG, "bad lattice index range");
+  int64_t tmin = cat->t[0], tmax = cat->t[0];
+  for (uint32_t e = 1; e < E; ++e) {
+    tmin = std::min(tmin, cat->t[e]);
+    tmax = std::max(tmax, cat->t[e]);
+  }
+  if ((__int128)tmax - tmin >= ((__int128)1 << 32)) return fail(SAS_ERR_RANGE, "time span must be < 2^32 ticks");
+  const int64_t dT = tmax - tmin;
+  const int64_t tph = cat->ticks_per_hour;
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+  DevInfo di;
+  if (int rc = device_info(dev, &di)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  int cb = (int)o.counter_bits;
+  if (cb == 0) cb = n_min <= 255 ? 8 : (n_min <= 65535 ? 16 : 32);
+  if (cb != 8 && cb != 16 && cb != 32) return fail(SAS_ERR_ARG, "counter_bits must be 8, 16 or 32");
+  if (cb == 8 && n_min > 255) cb = 16;
+  if (cb == 16 && n_min > 65535) cb = 32;
+  const int kx = o.tile_kx ? (int)o.tile_kx : 4;
+  const int ky = o.tile_ky ? (int)o.tile_ky : 4;
+  const int ctas = o.ctas_per_sm ? (int)o.ctas_per_sm : 2;
+
+  sas_result* res = new (std::nothrow) sas_result;
+  if (!res) return fail(SAS_ERR_OOM, "host allocation");
+  memset(res, 0, sizeof(*res));
+  res->device = dev;
+
+  if (n == 0 || v_begin == v_end) {
+    res->info.t0 = 0;
+    *out = res;
+    return SAS_OK;
+  }
+
+  Plan plan;
+  if (int rc = choose_tiles(d, E, dT, tph, kx, ky, cb, ctas, o, di, nullptr, &plan)) {
+    delete res;
+    return rc;
+  }
+  // Bucket grid: every detection that can project into the domain for some
+  // lattice velocity and some dt in [0, dT] lies inside it.
+  const int64_t vxa = d.vx0, vxb = (int64_t)d.vx0 + (int64_t)(d.nvx - 1) * d.dvx;
+  const int64_t vya = d.vy0, vyb = (int64_t)d.vy0 + (int64_t)(d.nvy - 1) * d.dvy;
+  auto clampd = [](int64_t v) { return std::max(-kLimDomain, std::min(kLimDomain, v)); };
+  const int64_t sx_lo = clampd(floor_div64(std::min<int64_t>(std::min(vxa, vxb), 0) * dT, tph));
+  const int64_t sx_hi = clampd(ceil_div64(std::max<int64_t>(std::max(vxa, vxb), 0) * dT, tph));
+  const int64_t sy_lo = clampd(floor_div64(std::min<int64_t>(std::min(vya, vyb), 0) * dT, tph));
+  const int64_t sy_hi = clampd(ceil_div64(std::max<int64_t>(std::max(vya, vyb), 0) * dT, tph));
+  CoarseGeom& cg = plan.cg;
+  for (;;) {
+    cg.gx0 = (int32_t)(d.x_min + sx_lo);
+    cg.gy0 = (int32_t)(d.y_min + sy_lo);
+    cg.ncx = (int32_t)ceil_div64((int64_t)d.nbx * d.bin + (sx_hi - sx_lo) + 1, cg.cell);
+    cg.ncy = (int32_t)ceil_div64((int64_t)d.nby * d.bin + (sy_hi - sy_lo) + 1, cg.cell);
+    if ((uint64_t)E * cg.ncx * cg.ncy <= ((uint64_t)1 << 27)) break;
+    if (cg.cell >= kLimDomain / 2) break;
+    cg.cell *= 2;  // fewer, larger buckets
+  }
+  {  // the bucket cell may have grown: recompute the per-chunk epoch count
+    Plan p2;
+    if (int rc = choose_tiles(d, E, dT, tph, kx, ky, cb, ctas, o, di, &cg, &p2)) {
+      delete res;
+      return rc;
+    }
+    plan.tc = p2.tc;
+  }
+  const uint64_t nb = (uint64_t)E * cg.ncx * cg.ncy;
+
+  SearchGeom g{};
+  g.vx0 = d.vx0; g.vy0 = d.vy0; g.dvx = d.dvx; g.dvy = d.dvy;
+  g.nvx = (int32_t)d.nvx; g.nvy = (int32_t)d.nvy;
+  g.smin = d.speed_min; g.smax = d.speed_max;
+  g.x_min = d.x_min; g.y_min = d.y_min;
+  g.nbx = (int32_t)d.nbx; g.nby = (int32_t)d.nby; g.bin = d.bin;
+  g.E = E; g.tph = tph;
+  g.v_begin = v_begin; g.v_end = v_end;
+
+  cudaEvent_t ev0, ev1, evs0, evs1;
+  cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&evs0); cudaEventCreate(&evs1);
+  struct EvGuard {
+    cudaEvent_t a, b, c, d;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); cudaEventDestroy(d); }
+  } evg{ev0, ev1, evs0, evs1};
+  cudaEventRecord(ev0, s);
+
+  int rc = SAS_OK;
+  {
+    Scratch sc(s);
+#define CK(expr, where)                          \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) {                     \
+      rc = cuda_fail(e_, where);                 \
+      goto done;                                 \
+    }                                            \
+  } while (0)
+    const int32_t* dx = cat->x;
+    const int32_t* dy = cat->y;
+    const uint16_t* dep = cat->epoch;
+    int32_t *hx = nullptr, *hy = nullptr;
+    uint16_t* hep = nullptr;
+    int64_t *d_t = nullptr, *d_dt = nullptr, *d_t0 = nullptr;
+    uint32_t *d_ecount = nullptr, *d_bcount = nullptr, *d_boff = nullptr, *d_cursor = nullptr,
+             *d_bof = nullptr, *d_scan = nullptr;
+    Det* d_dets = nullptr;
+    int32_t *d_sxt = nullptr, *d_syt = nullptr;
+    uint32_t* d_small = nullptr;  // [0] flags [1] n_emit [2] n_valid
+    unsigned long long* d_small64 = nullptr;  // [0] pairs [1] tile counter [2] raw total
+    Emit* d_emits = nullptr;
+    Key* d_keys = nullptr;
+    uint32_t* d_raw = nullptr;
+    unsigned long long *d_idoff = nullptr, *d_scan64 = nullptr;
+    uint32_t* d_ids_tmp = nullptr;
+    uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1u << 14, n / 4), 1u << 26);
+    uint32_t h_small[3] = {0, 0, 0};
+    unsigned long long h_small64[3] = {0, 0, 0};
+    int64_t h_t0 = 0;
+    uint32_t n_out = 0;
+    unsigned long long n_ids = 0;
+    StackArgs sa{};
+
+    if (!cat->on_device) {
+      CK(sc.alloc(&hx, n), "alloc x");
+      CK(sc.alloc(&hy, n), "alloc y");
+      CK(sc.alloc(&hep, n), "alloc epoch");
+      CK(cudaMemcpyAsync(hx, cat->x, n * 4, cudaMemcpyHostToDevice, s), "copy x");
+      CK(cudaMemcpyAsync(hy, cat->y, n * 4, cudaMemcpyHostToDevice, s), "copy y");
+      CK(cudaMemcpyAsync(hep, cat->epoch, n * 2, cudaMemcpyHostToDevice, s), "copy epoch");
+      dx = hx; dy = hy; dep = hep;
+    }
+    CK(sc.alloc(&d_t, E), "alloc t");
+    CK(sc.alloc(&d_dt, E), "alloc dt");
+    CK(sc.alloc(&d_t0, 1), "alloc t0");
+    CK(cudaMemcpyAsync(d_t, cat->t, E * 8, cudaMemcpyHostToDevice, s), "copy t");
+    CK(sc.alloc(&d_ecount, E), "alloc ecount");
+    CK(sc.alloc(&d_bcount, nb), "alloc bucket counts");
+    CK(sc.alloc(&d_boff, nb + 1), "alloc bucket offsets");
+    CK(sc.alloc(&d_cursor, nb), "alloc cursor");
+    CK(sc.alloc(&d_scan, scan_scratch_elems(nb)), "alloc scan scratch");
+    CK(sc.alloc(&d_bof, n), "alloc bucket_of");
+    CK(sc.alloc(&d_dets, n), "alloc dets");
+    CK(sc.alloc(&d_sxt, (size_t)d.nvx * E), "alloc sx table");
+    CK(sc.alloc(&d_syt, (size_t)d.nvy * E), "alloc sy table");
+    CK(sc.alloc(&d_small, 4), "alloc counters");
+    CK(sc.alloc(&d_small64, 4), "alloc counters64");
+    CK(cudaMemsetAsync(d_ecount, 0, E * 4, s), "memset");
+    CK(cudaMemsetAsync(d_bcount, 0, nb * 4, s), "memset");
+    CK(cudaMemsetAsync(d_small, 0, 16, s), "memset");
+    CK(cudaMemsetAsync(d_small64, 0, 32, s), "memset");
+
+    // a1-a3: ingest and validate, bucket, reference epoch, shift tables
+    CK(launch_ingest(dx, dy, dep, n, E, cg, d_bcount, d_ecount, d_bof, &d_small[0], s), "ingest");
+    CK(launch_scan_u32(d_bcount, d_boff, nb, d_scan, s), "bucket scan");
+    CK(cudaMemcpyAsync(d_cursor, d_boff, nb * 4, cudaMemcpyDeviceToDevice, s), "cursor");
+    CK(launch_scatter(dx, dy, dep, n, d_bof, d_cursor, d_dets, s), "scatter");
+    CK(launch_epoch_setup(E, d_t, d_ecount, d_dt, d_t0, s), "epoch setup");
+    CK(launch_shift_tables(g, d_dt, d_ecount, d_sxt, d_syt, &d_small[0], s), "shift tables");
+
+    // a4-a6: the stack kernel; reruns (exact) with wider counters if one wrapped
+    // or with a longer emission list if it overflowed.
+    for (int attempt = 0;; ++attempt) {
+      const TileCfg& tc = plan.tc;
+      CK(sc.alloc(&d_emits, emit_cap), "alloc emissions");
+      CK(stack_set_smem_attr(tc.kx, tc.ky, tc.cb, tc.smem), "smem attribute");
+      sa.g = g;
+      sa.cg = cg;
+      sa.tc = tc;
+      sa.magic = d.bin >= 2 ? magic_for(d.bin) : 0u;
+      sa.bin_is_one = d.bin == 1;
+      sa.n_min = n_min;
+      plan.ky_lo = (int)(v_begin / d.nvx);
+      plan.ky_hi = (int)((v_end - 1) / d.nvx);
+      sa.kx_lo = 0;
+      sa.ky_lo = plan.ky_lo;
+      sa.nvt_x = (int)div_ceil_u32(d.nvx, tc.kx);
+      sa.nvt_y = (int)div_ceil_u32((uint32_t)(plan.ky_hi - plan.ky_lo + 1), tc.ky);
+      sa.nst_x = (int)div_ceil_u32(d.nbx, tc.tx);
+      sa.nst_y = (int)div_ceil_u32(d.nby, tc.ty);
+      sa.n_tiles = (uint64_t)sa.nvt_x * sa.nvt_y * sa.nst_x * sa.nst_y;
+      sa.dets = d_dets;
+      sa.boff = d_boff;
+      sa.ecount = d_ecount;
+      sa.sxt = d_sxt;
+      sa.syt = d_syt;
+      sa.emits = d_emits;
+      sa.emit_cap = emit_cap;
+      sa.n_emit = &d_small[1];
+      sa.n_pairs = &d_small64[0];
+      sa.flags = &d_small[0];
+      sa.tile_counter = &d_small64[1];
+      CK(cudaMemsetAsync(&d_small[1], 0, 4, s), "memset");
+      CK(cudaMemsetAsync(d_small64, 0, 16, s), "memset");
+      const int grid_sz = di.sms * tc.ctas_per_sm;
+      cudaEventRecord(evs0, s);
+      CK(launch_stack(sa, grid_sz, s), "stack kernel");
+      cudaEventRecord(evs1, s);
+      CK(cudaMemcpyAsync(h_small, d_small, 12, cudaMemcpyDeviceToHost, s), "read counters");
+      CK(cudaMemcpyAsync(h_small64, d_small64, 16, cudaMemcpyDeviceToHost, s), "read counters");
+      CK(cudaMemcpyAsync(&h_t0, d_t0, 8, cudaMemcpyDeviceToHost, s), "read t0");
+      CK(cudaStreamSynchronize(s), "stack sync");
+      if (h_small[0] & kFlagEpoch) { rc = fail(SAS_ERR_RANGE, "an epoch index is >= n_epochs"); goto done; }
+      if (h_small[0] & kFlagPos) { rc = fail(SAS_ERR_RANGE, "a detection has |x| or |y| >= 2^29"); goto done; }
+      if (h_small[0] & kFlagShift) { rc = fail(SAS_ERR_RANGE, "a shift |v*(t-t0)/TPH| >= 2^28"); goto done; }
+      if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "stack kernel invariant"); goto done; }
+      if (attempt >= 4) { rc = fail(SAS_ERR_INTERNAL, "stack kernel did not converge"); goto done; }
+      if (h_small[0] & kFlagCounter) {
+        CK(cudaMemsetAsync(&d_small[0], 0, 4, s), "memset");
+        const int wider = plan.tc.cb * 2;
+        Plan p2;
+        if (int r2 = choose_tiles(d, E, dT, tph, kx, ky, wider, ctas, o, di, &cg, &p2)) { rc = r2; goto done; }
+        plan.tc = p2.tc;
+        continue;
+      }
+      if (h_small[1] > emit_cap || (h_small[0] & kFlagEmitCap)) {
+        if (h_small[1] >= (1u << 28)) {
+          rc = fail(SAS_ERR_OOM, "more than 2^28 cells reach the threshold; raise n_min");
+          goto done;
+        }
+        CK(cudaMemsetAsync(&d_small[0], 0, 4, s), "memset");
+        emit_cap = h_small[1] + h_small[1] / 4 + 1024;
+        continue;
+      }
+      break;
+    }
+    {
+      const uint32_t n_emit = h_small[1];
+      uint32_t n_pad = 1;
+      while (n_pad < n_emit) n_pad <<= 1;
+      CK(sc.alloc(&d_keys, n_pad), "alloc keys");
+      // a5/a7: exact distinct and raw counts of every emitted cell, then a8: order
+      CK(launch_cell_count(d_emits, n_emit, g, cg, d_dets, d_boff, d_ecount, d_sxt, d_syt, n_min,
+                           d_keys, &d_small[2], &d_small64[2], s), "cell count");
+      CK(launch_sort_keys(d_keys, n_emit, n_pad, s), "sort");
+      CK(cudaMemcpyAsync(&h_small[2], &d_small[2], 4, cudaMemcpyDeviceToHost, s), "read n_valid");
+      CK(cudaMemcpyAsync(&h_small64[2], &d_small64[2], 8, cudaMemcpyDeviceToHost, s), "read raw");
+      CK(cudaStreamSynchronize(s), "count sync");
+      n_out = h_small[2];
+      if (o.max_candidates > 0 && n_out > o.max_candidates) n_out = (uint32_t)o.max_candidates;
+      const uint64_t id_cap = std::max<uint64_t>(h_small64[2], 1);
+      CK(sc.alloc(&d_raw, n_out), "alloc raw");
+      CK(sc.alloc(&d_idoff, (size_t)n_out + 1), "alloc id offsets");
+      CK(sc.alloc(&d_scan64, scan_scratch_elems(n_out)), "alloc scan scratch");
+      CK(sc.alloc(&d_ids_tmp, id_cap), "alloc ids");
+      CK(cudaMallocAsync((void**)&res->d_ids, id_cap * 4, s), "alloc result ids");
+      CK(cudaMallocAsync((void**)&res->d_cands, std::max<size_t>(n_out, 1) * sizeof(sas_candidate), s),
+         "alloc result candidates");
+      // a7: contributing ids, ascending per candidate
+      CK(launch_key_raw(d_keys, n_out, d_raw, s), "raw");
+      CK(launch_scan_u32_to_u64(d_raw, d_idoff, n_out, d_scan64, s), "id offsets");
+      CK(launch_gather_ids(d_keys, n_out, d_idoff, g, cg, d_dets, d_boff, d_ecount, d_sxt, d_syt,
+                           d_ids_tmp, res->d_ids, &d_small[0], s), "gather ids");
+      CK(launch_write_candidates(d_keys, n_out, d_idoff, res->d_cands, s), "write candidates");
+      CK(cudaMemcpyAsync(&n_ids, &d_idoff[n_out], 8, cudaMemcpyDeviceToHost, s), "read n_ids");
+      CK(cudaMemcpyAsync(&h_small[0], &d_small[0], 4, cudaMemcpyDeviceToHost, s), "read flags");
+      cudaEventRecord(ev1, s);
+      CK(cudaStreamSynchronize(s), "final sync");
+      if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "id gather invariant"); goto done; }
+      res->info.n_candidates = n_out;
+      res->info.n_ids = n_ids;
+      res->info.n_pairs = h_small64[0];
+      res->info.n_emitted = n_emit;
+      res->info.t0 = h_t0;
+      res->info.counter_bits = (uint32_t)plan.tc.cb;
+      res->info.tile_kx = (uint32_t)plan.tc.kx;
+      res->info.tile_ky = (uint32_t)plan.tc.ky;
+      res->info.tile_bx = (uint32_t)plan.tc.tx;
+      res->info.tile_by = (uint32_t)plan.tc.ty;
+      cudaEventElapsedTime(&res->info.ms_stack, evs0, evs1);
+      cudaEventElapsedTime(&res->info.ms_total, ev0, ev1);
+    }
+  done:;
+#undef CK
+  }
+  if (rc != SAS_OK) {
+    if (res->d_ids) cudaFreeAsync(res->d_ids, s);
+    if (res->d_cands) cudaFreeAsync(res->d_cands, s);
+    cudaStreamSynchronize(s);
+    delete res;
+    return rc;
+  }
+  *out = res;
+  return SAS_OK;
+}
+
+int sas_result_get_info(const sas_result* r, sas_result_info* info) {
+  if (!r || !info) return fail(SAS_ERR_ARG, "null argument");
+  *info = r->info;
+  return SAS_OK;
+}
+
+int sas_candidates(const sas_result* r, sas_candidate* out, uint64_t cap, uint64_t* n_total,
+                   uint32_t* ids, uint64_t ids_cap, uint64_t* n_ids_total, int on_device) {
+  if (!r) return fail(SAS_ERR_ARG, "null result");
+  const uint64_t nc = r->info.n_candidates, ni = r->info.n_ids;
+  if (n_total) *n_total = nc;
+  if (n_ids_total) *n_ids_total = ni;
+  const uint64_t c1 = std::min(cap, nc), i1 = std::min(ids_cap, ni);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c1) {
+    if (!out) return fail(SAS_ERR_ARG, "null candidate buffer");
+    cudaError_t e = cudaMemcpy(out, r->d_cands, c1 * sizeof(sas_candidate), kind);
+    if (e != cudaSuccess) return cuda_fail(e, "copy candidates");
+  }
+  if (i1) {
+    if (!ids) return fail(SAS_ERR_ARG, "null id buffer");
+    cudaError_t e = cudaMemcpy(ids, r->d_ids, i1 * sizeof(uint32_t), kind);
+    if (e != cudaSuccess) return cuda_fail(e, "copy ids");
+  }
+  if (cap < nc || ids_cap < ni)
+    return fail(SAS_ERR_OVERFLOW, "buffers too small: need %llu candidates and %llu ids",
+                (unsigned long long)nc, (unsigned long long)ni);
+  return SAS_OK;
+}
+
+void sas_result_free(sas_result* r) {
+  if (!r) return;
+  if (r->d_cands) cudaFree(r->d_cands);
+  if (r->d_ids) cudaFree(r->d_ids);
+  delete r;
+}
+
+int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s, double* sm_mhz) {
+  if (!ops_per_s || !sm_mhz || iters == 0) return fail(SAS_ERR_ARG, "bad argument");
+  cudaError_t e = run_atomic_probe(iters, (cudaStream_t)stream, ops_per_s, sm_mhz);
+  if (e != cudaSuccess) return cuda_fail(e, "atomic probe");
+  return SAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations of the sm_103a shift-and-stack library.
+// Shared by the library's translation units only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/sas.h"
+
+namespace sas {
+
+// Exact-integer limits (see sas.h).
+constexpr int64_t kLimPos = int64_t(1) << 29;     // |x|, |y|
+constexpr int64_t kLimDomain = int64_t(1) << 28;  // |x_min|, nbx*bin, |shift|
+
+// Device-side error flags (bitwise OR into one word).
+enum : uint32_t {
+  kFlagEpoch = 1u,       // an epoch index >= n_epochs
+  kFlagPos = 2u,         // |x| or |y| >= 2^29
+  kFlagShift = 4u,       // |shift| >= 2^28 for a used epoch
+  kFlagCounter = 8u,     // a stack counter saturated (rerun with wider counters)
+  kFlagTimeout = 16u,    // a bounded wait gave up
+  kFlagInternal = 32u,   // invariant violated
+  kFlagEmitCap = 64u,    // emission list capacity exceeded (rerun with more)
+};
+
+constexpr uint32_t kInvalidBucket = 0xFFFFFFFFu;
+
+// A detection after bucketing: 16 bytes, so every bucket range is 16-byte aligned.
+struct __align__(16) Det {
+  int32_t x, y;
+  uint32_t e;
+  uint32_t id;
+};
+
+// Spatial buckets: detections sorted by (epoch, cy, cx) with coarse cells of
+// `cell` mpx whose origin is (gx0, gy0).  Bucket b = (e*ncy + cy)*ncx + cx.
+struct CoarseGeom {
+  int32_t gx0, gy0;
+  int32_t cell;
+  int32_t ncx, ncy;
+};
+
+// Everything a search kernel needs to know about the lattice and domain.
+struct SearchGeom {
+  int32_t vx0, vy0, dvx, dvy;
+  int32_t nvx, nvy;
+  int32_t smin, smax;
+  int32_t x_min, y_min;
+  int32_t nbx, nby;
+  int32_t bin;
+  uint32_t E;
+  int64_t tph;
+  uint64_t v_begin, v_end;
+};
+
+// Emitted cell (threshold crossing of the stack counters).
+struct __align__(16) Emit {
+  uint32_t v_idx, bx, by, pad;
+};
+
+// Candidate sort key, compared lexicographically (a, b, c):
+//   a = (~distinct << 32) | ~raw,  b = (v_idx << 32) | by,  c = bx.
+struct __align__(8) Key {
+  uint64_t a, b;
+  uint32_t c, pad;
+};
+
+// Stack kernel tile configuration.
+struct TileCfg {
+  int kx, ky;        // velocities per tile (lattice block)
+  int tx, ty;        // bins per tile
+  int cb;            // counter bits: 8, 16, 32
+  int nt;            // threads per CTA
+  int ctas_per_sm;
+  int ec;            // epochs per segment chunk
+  int seg_cap;       // segment slots per chunk
+  int emit_cap;      // per-CTA emission buffer entries
+  size_t smem;       // dynamic shared memory bytes
+};
+
+struct StackArgs {
+  SearchGeom g;
+  CoarseGeom cg;
+  TileCfg tc;
+  uint32_t magic;      // umulhi(X, magic) = X / bin for 0 <= X < tile extent
+  int32_t bin_is_one;  // bin == 1: the quotient is X itself
+  uint32_t n_min;
+  int32_t nvt_x, nvt_y;      // velocity tiles along kx, ky
+  int32_t kx_lo, ky_lo;      // first lattice column/row covered by the tiles
+  int32_t nst_x, nst_y;      // spatial tiles
+  uint64_t n_tiles;
+  const Det* dets;
+  const uint32_t* boff;      // [E*ncy*ncx + 1]
+  const uint32_t* ecount;    // [E] detections per epoch
+  const int32_t* sxt;        // [nvx][E] shift in x
+  const int32_t* syt;        // [nvy][E] shift in y
+  Emit* emits;
+  uint32_t emit_cap;
+  uint32_t* n_emit;
+  unsigned long long* n_pairs;
+  uint32_t* flags;
+  unsigned long long* tile_counter;
+};
+
+// Process-wide count of kernels launched by the library (sas_kernel_launches).
+void note_launch(uint32_t k = 1);
+
+// ---- launchers (defined in the .cu files) ----------------------------------
+
+// sas_prep.cu
+cudaError_t launch_ingest(const int32_t* x, const int32_t* y, const uint16_t* epoch, uint64_t n,
+                          uint32_t E, CoarseGeom cg, uint32_t* bucket_count, uint32_t* ecount,
+                          uint32_t* bucket_of, uint32_t* flags, cudaStream_t s);
+cudaError_t launch_scatter(const int32_t* x, const int32_t* y, const uint16_t* epoch, uint64_t n,
+                           const uint32_t* bucket_of, uint32_t* cursor, Det* dets, cudaStream_t s);
+cudaError_t launch_epoch_setup(uint32_t E, const int64_t* t, const uint32_t* ecount, int64_t* dt,
+                               int64_t* t0, cudaStream_t s);
+cudaError_t launch_shift_tables(const SearchGeom& g, const int64_t* dt, const uint32_t* ecount,
+                                int32_t* sxt, int32_t* syt, uint32_t* flags, cudaStream_t s);
+// exclusive scan, out[i] = sum(in[0..i)), out has n+1 entries
+cudaError_t launch_scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* scratch,
+                            cudaStream_t s);
+cudaError_t launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, uint64_t n,
+                                   unsigned long long* scratch, cudaStream_t s);
+size_t scan_scratch_elems(uint64_t n);
+
+// sas_stack.cu
+bool stack_config_supported(int kx, int ky, int cb);
+size_t stack_smem_bytes(const TileCfg& tc);
+cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s);
+cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
+
+// sas_post.cu
+cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, const SearchGeom& g,
+                              const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
+                              const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
+                              uint32_t n_min, Key* keys, uint32_t* n_valid,
+                              unsigned long long* raw_total, cudaStream_t s);
+cudaError_t launch_sort_keys(Key* keys, uint32_t n, uint32_t n_pad, cudaStream_t s);
+cudaError_t launch_key_raw(const Key* keys, uint32_t n, uint32_t* raw, cudaStream_t s);
+cudaError_t launch_gather_ids(const Key* keys, uint32_t n, const unsigned long long* id_off,
+                              const SearchGeom& g, const CoarseGeom& cg, const Det* dets,
+                              const uint32_t* boff, const uint32_t* ecount, const int32_t* sxt,
+                              const int32_t* syt, uint32_t* ids_tmp, uint32_t* ids,
+                              uint32_t* flags, cudaStream_t s);
+cudaError_t launch_write_candidates(const Key* keys, uint32_t n, const unsigned long long* id_off,
+                                    sas_candidate* out, cudaStream_t s);
+
+// sas_probe.cu
+cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
+
+// ---- small device helpers ---------------------------------------------------
+
+__host__ __device__ inline int64_t floor_div64(int64_t a, int64_t b) {  // b > 0
+  int64_t q = a / b;
+  if ((a % b) != 0 && a < 0) q -= 1;
+  return q;
+}
+
+__host__ __device__ inline int32_t floor_div32(int32_t a, int32_t b) {  // b > 0
+  int32_t q = a / b;
+  if ((a % b) != 0 && a < 0) q -= 1;
+  return q;
+}
+
+__host__ __device__ inline uint32_t div_ceil_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
+}  // namespace sas

@@ -1,0 +1,84 @@
+// Shared-memory atomic throughput probe: the roofline peak of the stack kernel.
+//
+// Every thread of every resident CTA issues `iters` x 8 32-bit atomicAdd to
+// shared memory.  Lane l of warp w always touches word (w*32 + l) + k*blockDim,
+// so the 32 lanes of a warp hit 32 distinct banks (conflict-free) and the
+// addresses are compile-time offsets of one base register: the loop is bound by
+// the shared-memory atomic unit, not by address arithmetic.
+#include "sas_internal.cuh"
+
+namespace sas {
+
+namespace {
+
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeUnroll = 8;
+
+__global__ void __launch_bounds__(kProbeThreads, 2)
+    k_atomic_probe(uint32_t iters, uint32_t* sink, unsigned long long* cycles) {
+  __shared__ uint32_t s[kProbeThreads * kProbeUnroll];
+  for (int i = threadIdx.x; i < kProbeThreads * kProbeUnroll; i += blockDim.x) s[i] = 0;
+  __syncthreads();
+  const long long c0 = clock64();
+  uint32_t* base = s + threadIdx.x;
+  uint32_t acc = 0;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < kProbeUnroll; ++k) acc += atomicAdd(base + k * kProbeThreads, 1u);
+  }
+  __syncthreads();
+  const long long c1 = clock64();
+  if (threadIdx.x == 0) {
+    atomicAdd(cycles, (unsigned long long)(c1 - c0));
+    sink[blockIdx.x] = s[0] + acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s, double* sm_mhz) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_atomic_probe, kProbeThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = sms * per_sm;
+  uint32_t* sink = nullptr;
+  unsigned long long* cycles = nullptr;
+  if ((e = cudaMallocAsync(&sink, blocks * sizeof(uint32_t), st)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync(&cycles, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best_ms = 1e30f;
+  double mhz = 0;
+  for (int rep = 0; rep < 4; ++rep) {  // rep 0 warms up
+    cudaMemsetAsync(cycles, 0, sizeof(unsigned long long), st);
+    cudaEventRecord(a, st);
+    k_atomic_probe<<<blocks, kProbeThreads, 0, st>>>(iters, sink, cycles);
+    note_launch();
+    cudaEventRecord(b, st);
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    unsigned long long cyc = 0;
+    cudaMemcpy(&cyc, cycles, sizeof(cyc), cudaMemcpyDeviceToHost);
+    if (rep > 0 && ms < best_ms) {
+      best_ms = ms;
+      mhz = (double)cyc / blocks / (ms * 1e3);
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFreeAsync(sink, st);
+  cudaFreeAsync(cycles, st);
+  if (e != cudaSuccess) return e;
+  const double ops = (double)blocks * kProbeThreads * (double)iters * kProbeUnroll;
+  *ops_per_s = ops / (best_ms * 1e-3);
+  *sm_mhz = mhz;
+  return cudaGetLastError();
+}
+
+}  // namespace sas

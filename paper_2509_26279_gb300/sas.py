@@ -1,0 +1,245 @@
+"""Thin ctypes binding of the sm_103a shift-and-stack library (include/sas.h).
+
+Argument marshalling only: every step of the search runs in the library's CUDA
+kernels.  There is no CPU fallback -- importing this module raises if the
+compiled library is missing (build it with ``__graft_entry__.build()``).
+
+Host arrays are NumPy arrays; device arrays may be anything exposing
+``data_ptr()`` (torch CUDA tensors) or ``__cuda_array_interface__``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsas.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsas.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SAS_OK, SAS_ERR_ARG, SAS_ERR_RANGE, SAS_ERR_OVERFLOW = 0, 1, 2, 3
+SAS_ERR_CUDA, SAS_ERR_OOM, SAS_ERR_TIMEOUT, SAS_ERR_INTERNAL = 4, 5, 6, 7
+STATUS_NAMES = {0: "SAS_OK", 1: "SAS_ERR_ARG", 2: "SAS_ERR_RANGE", 3: "SAS_ERR_OVERFLOW",
+                4: "SAS_ERR_CUDA", 5: "SAS_ERR_OOM", 6: "SAS_ERR_TIMEOUT", 7: "SAS_ERR_INTERNAL"}
+
+
+class SasError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sas_grid_desc(ctypes.Structure):
+    _fields_ = [("vx0", ctypes.c_int32), ("vy0", ctypes.c_int32), ("dvx", ctypes.c_int32),
+                ("dvy", ctypes.c_int32), ("nvx", ctypes.c_uint32), ("nvy", ctypes.c_uint32),
+                ("speed_min", ctypes.c_int32), ("speed_max", ctypes.c_int32),
+                ("x_min", ctypes.c_int32), ("y_min", ctypes.c_int32), ("nbx", ctypes.c_uint32),
+                ("nby", ctypes.c_uint32), ("bin", ctypes.c_int32)]
+
+
+class sas_catalog(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("epoch", ctypes.c_void_p), ("n_epochs", ctypes.c_uint32), ("t", ctypes.c_void_p),
+                ("ticks_per_hour", ctypes.c_int64), ("on_device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class sas_opts(ctypes.Structure):
+    _fields_ = [("v_begin", ctypes.c_uint64), ("v_end", ctypes.c_uint64),
+                ("max_candidates", ctypes.c_uint64), ("tile_kx", ctypes.c_uint32),
+                ("tile_ky", ctypes.c_uint32), ("tile_bx", ctypes.c_uint32),
+                ("tile_by", ctypes.c_uint32), ("counter_bits", ctypes.c_uint32),
+                ("coarse_bins", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class sas_result_info(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_uint64), ("n_ids", ctypes.c_uint64),
+                ("n_pairs", ctypes.c_uint64), ("n_emitted", ctypes.c_uint64),
+                ("t0", ctypes.c_int64), ("counter_bits", ctypes.c_uint32),
+                ("tile_kx", ctypes.c_uint32), ("tile_ky", ctypes.c_uint32),
+                ("tile_bx", ctypes.c_uint32), ("tile_by", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("ms_stack", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+
+# sas_candidate as a NumPy record (32 bytes, same layout as the C struct)
+CANDIDATE_DTYPE = np.dtype([("v_idx", "<u4"), ("bx", "<u4"), ("by", "<u4"), ("count", "<u4"),
+                            ("raw", "<u4"), ("id_len", "<u4"), ("id_off", "<u8")])
+assert CANDIDATE_DTYPE.itemsize == 32
+
+_p = ctypes.c_void_p
+_lib.sas_version.restype = ctypes.c_char_p
+_lib.sas_abi_version.restype = ctypes.c_int
+_lib.sas_kernel_launches.restype = ctypes.c_uint64
+_lib.sas_last_error.restype = ctypes.c_char_p
+_lib.sas_create_grid.argtypes = [ctypes.POINTER(sas_grid_desc), ctypes.POINTER(_p)]
+_lib.sas_destroy_grid.argtypes = [_p]
+_lib.sas_destroy_grid.restype = None
+_lib.sas_stack.argtypes = [_p, ctypes.POINTER(sas_catalog), ctypes.c_uint32,
+                           ctypes.POINTER(sas_opts), _p, ctypes.POINTER(_p)]
+_lib.sas_result_get_info.argtypes = [_p, ctypes.POINTER(sas_result_info)]
+_lib.sas_candidates.argtypes = [_p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p,
+                                ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+_lib.sas_result_free.argtypes = [_p]
+_lib.sas_result_free.restype = None
+_lib.sas_probe_shared_atomic_peak.argtypes = [ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+
+EXPORTED = ["sas_version", "sas_abi_version", "sas_kernel_launches", "sas_last_error", "sas_create_grid",
+            "sas_destroy_grid", "sas_stack", "sas_result_get_info", "sas_candidates",
+            "sas_result_free", "sas_probe_shared_atomic_peak"]
+
+
+def _check(status: int):
+    if status != SAS_OK:
+        raise SasError(status, _lib.sas_last_error().decode())
+
+
+def sas_version() -> str:
+    return _lib.sas_version().decode()
+
+
+def sas_kernel_launches() -> int:
+    return int(_lib.sas_kernel_launches())
+
+
+def _dev_ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    if hasattr(a, "__cuda_array_interface__"):
+        return int(a.__cuda_array_interface__["data"][0])
+    raise TypeError("device array expected (torch CUDA tensor or __cuda_array_interface__)")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+class Grid:
+    """sas_create_grid / sas_destroy_grid.  Accepts a workloads.GridSpec or the
+    same fields as keyword arguments."""
+
+    def __init__(self, spec=None, **kw):
+        f = dict(spec.__dict__) if spec is not None else {}
+        f.update(kw)
+        self.desc = sas_grid_desc(
+            vx0=f["vx0"], vy0=f["vy0"], dvx=f["dvx"], dvy=f["dvy"], nvx=f["nvx"], nvy=f["nvy"],
+            speed_min=f.get("speed_min", 0), speed_max=f.get("speed_max", 0), x_min=f["x_min"],
+            y_min=f["y_min"], nbx=f["nbx"], nby=f["nby"], bin=f["bin"])
+        self.nvx, self.nvy = int(f["nvx"]), int(f["nvy"])
+        h = _p()
+        _check(_lib.sas_create_grid(ctypes.byref(self.desc), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.sas_destroy_grid(h)
+            self._h = _p()
+
+
+class Result:
+    """A finished search (sas_result); owns device memory until freed."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def info(self) -> dict:
+        inf = sas_result_info()
+        _check(_lib.sas_result_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in sas_result_info._fields_ if k != "reserved"}
+
+    def candidates(self):
+        """(candidates: structured array of CANDIDATE_DTYPE, ids: uint32 array)."""
+        nc, ni = ctypes.c_uint64(), ctypes.c_uint64()
+        inf = self.info()
+        nc_v, ni_v = inf["n_candidates"], inf["n_ids"]
+        cands = np.zeros(nc_v, CANDIDATE_DTYPE)
+        ids = np.zeros(ni_v, np.uint32)
+        _check(_lib.sas_candidates(self._h, cands.ctypes.data if nc_v else None, nc_v,
+                                   ctypes.byref(nc), ids.ctypes.data if ni_v else None, ni_v,
+                                   ctypes.byref(ni), 0))
+        return cands, ids
+
+    def candidates_into(self, cands_dev, ids_dev, cap: int, ids_cap: int):
+        """Copy into caller-owned device buffers (sas_candidates with on_device=1)."""
+        nc, ni = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.sas_candidates(self._h, _dev_ptr(cands_dev), cap, ctypes.byref(nc),
+                                   _dev_ptr(ids_dev), ids_cap, ctypes.byref(ni), 1))
+        return nc.value, ni.value
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.sas_result_free(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_opts(**kw) -> sas_opts:
+    o = sas_opts()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def sas_stack(grid: Grid, x, y, epoch, t, ticks_per_hour: int, n_min: int, *,
+              on_device: bool = False, opts: sas_opts | None = None, stream=None) -> Result:
+    """Run the search.  With on_device=False, x/y/epoch are NumPy host arrays
+    (int32, int32, uint16); with on_device=True they are device arrays of those
+    types.  t (int64 epoch times) is always a host array."""
+    t = np.ascontiguousarray(t, np.int64)
+    if on_device:
+        n = int(x.numel() if hasattr(x, "numel") else len(x))
+        px, py, pe = _dev_ptr(x), _dev_ptr(y), _dev_ptr(epoch)
+        keep = ()
+    else:
+        x = np.ascontiguousarray(x, np.int32)
+        y = np.ascontiguousarray(y, np.int32)
+        epoch = np.ascontiguousarray(epoch, np.uint16)
+        n = int(x.shape[0])
+        px, py, pe = x.ctypes.data, y.ctypes.data, epoch.ctypes.data
+        keep = (x, y, epoch)
+    cat = sas_catalog(n=n, x=px, y=py, epoch=pe, n_epochs=int(t.shape[0]), t=t.ctypes.data,
+                      ticks_per_hour=int(ticks_per_hour), on_device=1 if on_device else 0)
+    h = _p()
+    _check(_lib.sas_stack(grid.handle, ctypes.byref(cat), int(n_min),
+                          ctypes.byref(opts) if opts is not None else None,
+                          _stream_handle(stream), ctypes.byref(h)))
+    del keep
+    return Result(h)
+
+
+def stack_catalog(grid: Grid, cat, n_min: int, **kw) -> Result:
+    """sas_stack on a workloads.Catalog held in host memory."""
+    return sas_stack(grid, cat.x, cat.y, cat.epoch, cat.t, cat.ticks_per_hour, n_min, **kw)
+
+
+def sas_probe_shared_atomic_peak(iters: int = 4096, stream=None):
+    """(ops/s, SM MHz) of conflict-free 32-bit shared atomicAdd on all SMs."""
+    ops, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sas_probe_shared_atomic_peak(int(iters), _stream_handle(stream), ctypes.byref(ops),
+                                             ctypes.byref(mhz)))
+    return ops.value, mhz.value
+
+
+def library():
+    return _lib
