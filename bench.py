@@ -242,7 +242,7 @@ def main():
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    stack_ms, pairs = [], []
+    stack_ms, pairs, phases = [], [], []
     launches0 = sas.sas_kernel_launches()
     with ClockSampler(local) as clk:
         barrier()
@@ -253,6 +253,7 @@ def main():
             ev[i][1].record(stream)
             inf = r.info()
             stack_ms.append(inf["ms_stack"])
+            phases.append([inf["ms_prep"], inf["ms_stack"], inf["ms_count"], inf["ms_ids"]])
             pairs.append(inf["n_pairs"])
             r.free()
         barrier()
@@ -299,7 +300,12 @@ def main():
     cfg.update({"l2": "flushed between steps (256 MiB write)", "n_pairs_per_step": n_pairs,
                 "candidates": int(info0["n_candidates"]),
                 "tile": [info0["tile_kx"], info0["tile_ky"], info0["tile_bx"], info0["tile_by"]],
-                "counter_bits": int(info0["counter_bits"]), "parallelism": f"replicas{world}"})
+                "counter_bits": int(info0["counter_bits"]), "superbin": int(info0["superbin"]),
+                "velocity_block": [info0["vblock_x"], info0["vblock_y"]],
+                "staged_cap": int(info0["staged_cap"]), "emitted": int(info0["n_emitted"]),
+                "phase_ms": dict(zip(["prep", "stack", "count_sort", "ids"],
+                                     [round(statistics.mean(c), 4) for c in zip(*phases)])),
+                "parallelism": f"replicas{world}"})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",

@@ -29,7 +29,9 @@
  *   |x|, |y| < 2^29 for every detection;  |x_min|, |y_min| < 2^28;
  *   nbx*bin < 2^28 and nby*bin < 2^28;    nvx*nvy < 2^31;
  *   |shift| < 2^28 for every lattice velocity and every epoch that has a
- *   detection;  max(t) - min(t) < 2^32;  n < 2^31;  1 <= E <= SAS_MAX_EPOCHS.
+ *   detection;  (tile_kx - 1) * |dvx| * (max(t) - min(t)) / TPH < 2^23 and
+ *   likewise for y (the shift spread inside one velocity tile);
+ *   max(t) - min(t) < 2^32;  n < 2^31;  1 <= E <= SAS_MAX_EPOCHS.
  *
  * Threading and streams: every call enqueues its device work on the caller's
  * CUDA stream (NULL = the legacy default stream) and returns when its outputs
@@ -103,12 +105,13 @@ typedef struct sas_catalog {
 typedef struct sas_opts {
   uint64_t v_begin, v_end;   /* search only lattice indices [v_begin, v_end); 0,0 = all */
   uint64_t max_candidates;   /* keep the first K candidates in output order; 0 = all    */
-  uint32_t tile_kx, tile_ky; /* velocities per tile (kx a multiple of 4, <= 8 each)     */
-  uint32_t tile_bx, tile_by; /* bins per tile                                           */
+  uint32_t tile_kx, tile_ky; /* lattice points per velocity tile: kx 4 or 8, ky 1, 2 or 4 */
+  uint32_t tile_bx, tile_by; /* counters (super-bins) per spatial tile side             */
   uint32_t counter_bits;     /* 8, 16 or 32; 0 = choose                                 */
   uint32_t coarse_bins;      /* spatial bucket size in bins; 0 = choose                 */
-  uint32_t ctas_per_sm;      /* 0 = choose                                              */
-  uint32_t reserved;
+  uint32_t superbin;         /* bins per counter side, 1..4; 0 = choose                 */
+  uint32_t velocity_block;   /* velocity tiles per side sharing one staged detection
+                                set, 1..8; 0 = choose                                   */
 } sas_opts;
 
 /* One candidate trajectory: the cell (v_idx, bx, by) of the 3-D histogram with
@@ -132,10 +135,17 @@ typedef struct sas_result_info {
   uint64_t n_emitted;        /* cells that crossed the counter threshold (superset) */
   int64_t t0;                /* reference epoch (ticks)                           */
   uint32_t counter_bits;     /* counter width the stack kernel ran with           */
-  uint32_t tile_kx, tile_ky, tile_bx, tile_by;
+  uint32_t tile_kx, tile_ky, tile_bx, tile_by;  /* the plan it ran with             */
+  uint32_t superbin;         /* bins per counter side                             */
+  uint32_t vblock_x, vblock_y;  /* velocity tiles per staged detection set          */
+  uint32_t staged_cap;       /* staged detection records per CTA                  */
   uint32_t reserved;
   float ms_stack;            /* device time of the stack kernel (CUDA events)     */
   float ms_total;            /* device time of the whole call                     */
+  float ms_prep;             /* ingest, buckets, reference epoch, shift tables    */
+  float ms_count;            /* exact counts of emitted cells + ordering          */
+  float ms_ids;              /* contributing ids + candidate records (+ host sync) */
+  float reserved_f;
 } sas_result_info;
 
 typedef struct sas_grid sas_grid;      /* opaque, owned by the library */

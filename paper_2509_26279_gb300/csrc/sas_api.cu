@@ -2,6 +2,8 @@
 // sequence of one search (Sec. 2.1 steps 1-3).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +18,9 @@ using namespace sas;
 
 struct sas_grid {
   sas_grid_desc d;
+  // emission count of the previous search on this grid: sizes the next
+  // emission list so that repeated searches do not need an exact rerun
+  std::atomic<uint32_t> emit_hint{0};
 };
 
 struct sas_result {
@@ -102,6 +107,19 @@ struct Scratch {
 
 bool fits_i32(int64_t v) { return v >= INT32_MIN && v <= INT32_MAX; }
 
+// Opt-in host-side tracing (environment variable SAS_TRACE=1): microseconds
+// since the start of the call at each phase boundary, on stderr.
+struct Tracer {
+  bool on;
+  std::chrono::steady_clock::time_point t0;
+  Tracer() : on(std::getenv("SAS_TRACE") != nullptr), t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* what) const {
+    if (!on) return;
+    const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    std::fprintf(stderr, "[sas] %9.1f us  %s\n", us, what);
+  }
+};
+
 uint32_t magic_for(int32_t bin) {  // ceil(2^32 / bin) for bin >= 2
   return (uint32_t)(((uint64_t)1 << 32) / (uint64_t)bin + 1);
 }
@@ -114,9 +132,10 @@ bool magic_exact(int32_t bin, int64_t x_max) {
   return (unsigned __int128)x_max * err < ((unsigned __int128)1 << 32);
 }
 
-constexpr int kSegCap = 1024;
+constexpr int kStackThreads = 1024;
+constexpr int kSegCap = kStackThreads;  // one (epoch, bucket row) segment per thread
 constexpr int kEmitCap = 256;
-constexpr int kStackThreads = 512;
+constexpr int kMaxEpochChunk = 256;     // staged records carry the epoch in 8 bits
 
 struct Plan {
   TileCfg tc;
@@ -131,79 +150,147 @@ int64_t spread_bound(int64_t dv_span, int64_t dT, int64_t tph) {
   return s > (long double)kLimDomain ? kLimDomain : (int64_t)s;
 }
 
-int choose_tiles(const sas_grid_desc& d, uint32_t E, int64_t dT, int64_t tph, int kx, int ky,
-                 int cb, int ctas, const sas_opts& o, const DevInfo& di, const CoarseGeom* fixed_cg,
-                 Plan* p) {
+// log P(Poisson(lam) >= k), summed in log space.
+double log_poisson_tail(double lam, int k) {
+  if (k <= 0) return 0.0;
+  if (lam <= 0) return -1e300;
+  double lt = -lam + k * std::log(lam) - std::lgamma(k + 1.0), acc = lt, term = lt;
+  for (int i = k + 1; i < k + 200; ++i) {
+    term += std::log(lam) - std::log((double)i);
+    acc = std::max(acc, term) + std::log1p(std::exp(-std::fabs(acc - term)));
+    if (term < acc - 40) break;
+  }
+  return acc;
+}
+
+// Super-bin size: the largest s in 1..3 for which uniform noise of the
+// catalog's mean density is expected to push few super-bins over n_min across
+// the searched lattice -- at most max(4000, pairs / 1e5), each emission costing
+// one exact recount.  Larger super-bins mean fewer counters to reset per
+// detection-shift but more cells near true movers reach the threshold; measured
+// on the DECam-like fields, s = 3 balances the two and s = 4 does not pay.
+int choose_superbin(const sas_grid_desc& d, uint64_t n, uint32_t n_min, uint64_t nv) {
+  if (n_min < 2) return 1;
+  const double bins = (double)d.nbx * d.nby;
+  const double lam_bin = (double)n / bins;  // detections per bin over all epochs
+  const double pairs = (double)n * (double)nv;  // upper bound of detection-shifts
+  const double budget = std::max(4000.0, pairs / 1e5);
+  int best = 1;
+  for (int s = 2; s <= 3; ++s) {
+    if ((int64_t)s * d.bin >= kLimDomain / 4) break;
+    const double cells = (double)nv * bins / (s * s);
+    const double lt = log_poisson_tail(lam_bin * s * s, (int)n_min);
+    if (std::log(cells) + lt < std::log(budget)) best = s;
+  }
+  return best;
+}
+
+int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int64_t tph, int kx,
+                 int ky, int cb, int sb, const sas_opts& o, const DevInfo& di, int n_rows,
+                 const CoarseGeom* fixed_cg, Plan* p) {
   if (!stack_config_supported(kx, ky, cb))
     return fail(SAS_ERR_ARG, "unsupported tile (kx=%d, ky=%d, counter_bits=%d)", kx, ky, cb);
   TileCfg tc{};
   tc.kx = kx;
   tc.ky = ky;
   tc.cb = cb;
+  tc.s = sb;
   tc.nt = kStackThreads;
-  tc.ctas_per_sm = ctas;
   tc.seg_cap = kSegCap;
   tc.emit_cap = kEmitCap;
-  const int64_t budget =
-      std::min<int64_t>(di.smem_optin, (int64_t)di.smem_per_sm / ctas - 1024);
-  const int64_t spread_y = spread_bound((int64_t)(ky - 1) * std::llabs((int64_t)d.dvy), dT, tph);
-  int ec = (int)std::min<uint32_t>(E, 256);
-  int tx = (int)o.tile_bx, ty = (int)o.tile_by;
-  for (int iter = 0; iter < 64; ++iter) {
-    tc.ec = ec;
-    tc.tx = tx > 0 ? tx : 4;
-    tc.ty = ty > 0 ? ty : 4;
-    const int64_t fixed = (int64_t)stack_smem_bytes(tc) - (int64_t)ky * kx * tc.tx * tc.ty * cb / 8;
-    if (tx <= 0 || ty <= 0) {
-      const int64_t cells = budget - fixed;
-      int side = (int)std::sqrt((double)cells * 8.0 / ((double)kx * ky * cb));
-      side &= ~3;
-      tc.tx = std::min<int>(side, ((int)d.nbx + 3) & ~3);
-      tc.ty = std::min<int>(side, ((int)d.nby + 3) & ~3);
-      if (tc.tx < 4) tc.tx = 4;
-      if (tc.ty < 4) tc.ty = 4;
-      // use the room a narrow domain leaves along one axis for the other
-      if (tc.tx < side) tc.ty = std::min<int>(((int)(cells * 8 / ((int64_t)kx * ky * cb * tc.tx))) & ~3,
-                                              ((int)d.nby + 3) & ~3);
-      if (tc.ty < side && tc.tx == side)
-        tc.tx = std::min<int>(((int)(cells * 8 / ((int64_t)kx * ky * cb * tc.ty))) & ~3,
-                              ((int)d.nbx + 3) & ~3);
-      tc.tx = std::max(tc.tx, 4);
-      tc.ty = std::max(tc.ty, 4);
-    }
+  const int64_t budget = di.smem_optin;
+  const int64_t sbin = (int64_t)sb * d.bin;
+  // velocity block: keep the union window within ~15% of the tile per axis
+  const int64_t step_x = spread_bound(std::llabs((int64_t)d.dvx), dT, tph) - 1;
+  const int64_t step_y = spread_bound(std::llabs((int64_t)d.dvy), dT, tph) - 1;
+  const double lam1 = (double)n / ((double)E * d.nbx * d.nby);  // per bin per epoch
+  // The shifts of one velocity tile may spread by at most 2^23 mpx over the
+  // time span, so that staged coordinates fit their 24-bit field.
+  if (spread_bound((int64_t)(kx - 1) * std::llabs((int64_t)d.dvx), dT, tph) >= (1 << 23) ||
+      spread_bound((int64_t)(ky - 1) * std::llabs((int64_t)d.dvy), dT, tph) >= (1 << 23))
+    return fail(SAS_ERR_RANGE, "lattice step x time span too large (shift spread >= 2^23 mpx)");
+  double cells_frac = 0.62;
+  int bv_cap = 8;
+  for (int iter = 0; iter < 200; ++iter) {
+    const int64_t cells_bytes = (int64_t)(budget * cells_frac);
+    int side = (int)std::sqrt((double)cells_bytes * 8.0 / ((double)kx * ky * cb));
+    side = std::max(4, side & ~3);
+    const int dom_x = (int)(((int64_t)d.nbx + sb - 1) / sb + 3) & ~3;
+    const int dom_y = (int)(((int64_t)d.nby + sb - 1) / sb + 3) & ~3;
+    tc.tx = o.tile_bx ? (int)o.tile_bx : std::min(side, dom_x);
+    tc.ty = o.tile_by ? (int)o.tile_by : std::min(side, dom_y);
+    if (!o.tile_bx && tc.ty < side)
+      tc.tx = std::min((int)(cells_bytes * 8 / ((int64_t)kx * ky * cb * tc.ty)) & ~3, dom_x);
+    if (!o.tile_by && tc.tx < side && tc.ty == side)
+      tc.ty = std::min((int)(cells_bytes * 8 / ((int64_t)kx * ky * cb * tc.tx)) & ~3, dom_y);
+    tc.tx = std::max(tc.tx, 4);
+    tc.ty = std::max(tc.ty, 4);
     if (((int64_t)tc.tx * tc.ty) % 4 != 0)
       return fail(SAS_ERR_ARG, "tile_bx * tile_by must be a multiple of 4");
-    while (!magic_exact(d.bin, (int64_t)std::max(tc.tx, tc.ty) * d.bin - 1) && tc.tx > 4 && tc.ty > 4) {
-      tc.tx = std::max(4, (tc.tx / 2) & ~3);
-      tc.ty = std::max(4, (tc.ty / 2) & ~3);
+    const int64_t tw = (int64_t)tc.tx * sbin, th = (int64_t)tc.ty * sbin;
+    int bvx = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (tw * 15 / 100) / std::max<int64_t>(1, step_x * kx)));
+    int bvy = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (th * 15 / 100) / std::max<int64_t>(1, step_y * ky)));
+    if (o.velocity_block) bvx = bvy = (int)std::min<uint32_t>(o.velocity_block, 8);
+    // enough work units to fill the GPU: shrink the velocity block, then the tile
+    const uint64_t units = (uint64_t)div_ceil_u32(d.nvx, kx * bvx) * div_ceil_u32(n_rows, ky * bvy) *
+                           div_ceil_u32(d.nbx, tc.tx * sb) * div_ceil_u32(d.nby, tc.ty * sb);
+    if (units < 2ull * di.sms && !o.velocity_block && std::max(bvx, bvy) > 1) {
+      bv_cap = std::max(bvx, bvy) / 2;
+      continue;
     }
-    if (!magic_exact(d.bin, (int64_t)std::max(tc.tx, tc.ty) * d.bin - 1))
-      return fail(SAS_ERR_RANGE, "bin %d too large for exact reciprocal division", d.bin);
-    // coarse bucket cell
+    if (units < 2ull * di.sms && !(o.tile_bx || o.tile_by) && std::min(tc.tx, tc.ty) > 16) {
+      cells_frac *= 0.7;
+      continue;
+    }
+    tc.bvx = bvx;
+    tc.bvy = bvy;
+    const int64_t spread_x = spread_bound((int64_t)(bvx * kx - 1) * std::llabs((int64_t)d.dvx), dT, tph);
+    const int64_t spread_y = spread_bound((int64_t)(bvy * ky - 1) * std::llabs((int64_t)d.dvy), dT, tph);
+    if (tw + spread_x >= (1 << 24) || th + spread_y >= ((int64_t)1 << 30)) {
+      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_ARG, "tile too wide for staged records");
+      cells_frac *= 0.8;
+      continue;
+    }
+    if (!magic_exact((int32_t)std::min<int64_t>(sbin, INT32_MAX), std::max(tw, th) - 1)) {
+      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_RANGE, "tile too large for exact division");
+      cells_frac *= 0.8;
+      continue;
+    }
+    // coarse bucket cell and rows per epoch window
     CoarseGeom cg{};
     if (fixed_cg) {
       cg = *fixed_cg;
     } else {
-      int cbins = o.coarse_bins > 0 ? (int)o.coarse_bins : std::max(1, tc.ty / 4);
-      int64_t cell = (int64_t)cbins * d.bin;
-      // by default a tile's source window spans at most about 8 bucket rows
-      if (o.coarse_bins == 0) cell = std::max<int64_t>(cell, ((int64_t)tc.ty * d.bin + spread_y + 7) / 8);
-      cg.cell = (int32_t)std::min<int64_t>(cell, kLimDomain);
+      int64_t cell = o.coarse_bins > 0 ? (int64_t)o.coarse_bins * d.bin : (th + spread_y + 5) / 6;
+      cg.cell = (int32_t)std::max<int64_t>(1, std::min<int64_t>(cell, kLimDomain));
     }
-    const int64_t rows = ((int64_t)tc.ty * d.bin + spread_y) / cg.cell + 2;
+    const int64_t rows = (th + spread_y) / cg.cell + 2;
     if (rows > kSegCap) {
       if (fixed_cg) return fail(SAS_ERR_INTERNAL, "segment rows exceed capacity");
       return fail(SAS_ERR_ARG, "coarse_bins too small for this tile (%lld rows)", (long long)rows);
     }
-    int new_ec = (int)std::min<int64_t>(std::min<int64_t>(E, kStackThreads), kSegCap / rows);
-    if (new_ec < 1) new_ec = 1;
-    tc.ec = new_ec;
+    tc.rows = (int)rows;
+    tc.ec = (int)std::min<int64_t>(std::min<int64_t>(E, kMaxEpochChunk), kSegCap / rows);
+    if (tc.ec < 1) tc.ec = 1;
+    // staged records: what the union window holds on average, with headroom
+    const double win = (double)(tw + spread_x) / d.bin * (double)(th + spread_y) / d.bin;
+    const double est = lam1 * std::min<uint32_t>(E, tc.ec) * win;
+    tc.scap = 0;
+    const int64_t rest = budget - (int64_t)stack_smem_bytes(tc);
+    const int64_t want = (int64_t)(1.5 * est) + 1024;
+    if (rest < 8 * 256) {
+      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_ARG, "tile does not fit in shared memory");
+      cells_frac *= 0.9;
+      continue;
+    }
+    if (rest / 8 < want && cells_frac > 0.15 && !(o.tile_bx || o.tile_by)) {
+      cells_frac *= 0.93;  // give the staging area more room
+      continue;
+    }
+    tc.scap = (int)std::min<int64_t>(rest / 8, std::max<int64_t>(want, 4096));
     tc.smem = stack_smem_bytes(tc);
     if ((int64_t)tc.smem > budget) {
-      if (tx > 0 && ty > 0) return fail(SAS_ERR_ARG, "tile does not fit in shared memory");
-      // shrink and retry
-      tx = tx > 0 ? tx : std::max(4, (tc.tx - 4) & ~3);
-      ty = ty > 0 ? ty : std::max(4, (tc.ty - 4) & ~3);
+      cells_frac *= 0.95;
       continue;
     }
     p->tc = tc;
@@ -243,6 +330,7 @@ int sas_create_grid(const sas_grid_desc* desc, sas_grid** out) {
   sas_grid* g = new (std::nothrow) sas_grid;
   if (!g) return fail(SAS_ERR_OOM, "host allocation");
   g->d = d;
+  g->emit_hint.store(0);
   *out = g;
   return SAS_OK;
 }
@@ -252,6 +340,7 @@ void sas_destroy_grid(sas_grid* grid) { delete grid; }
 int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* opts,
               void* stream, sas_result** out) {
   if (!grid || !cat || !out) return fail(SAS_ERR_ARG, "null argument");
+  const Tracer tr;
   const sas_grid_desc& d = grid->d;
   const uint32_t E = cat->n_epochs;
   const uint64_t n = cat->n;
@@ -283,14 +372,18 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   if (int rc = device_info(dev, &di)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
 
+  // A CB-bit counter holds thresholds up to 2^(CB-1) (it starts at 2^(CB-1) - n_min).
+  if (n_min > (1u << 31)) return fail(SAS_ERR_ARG, "n_min must be <= 2^31");
   int cb = (int)o.counter_bits;
-  if (cb == 0) cb = n_min <= 255 ? 8 : (n_min <= 65535 ? 16 : 32);
+  if (cb == 0) cb = n_min <= 128 ? 8 : (n_min <= 32768 ? 16 : 32);
   if (cb != 8 && cb != 16 && cb != 32) return fail(SAS_ERR_ARG, "counter_bits must be 8, 16 or 32");
-  if (cb == 8 && n_min > 255) cb = 16;
-  if (cb == 16 && n_min > 65535) cb = 32;
-  const int kx = o.tile_kx ? (int)o.tile_kx : 4;
+  if (cb == 8 && n_min > 128) cb = 16;
+  if (cb == 16 && n_min > 32768) cb = 32;
+  const int kx = o.tile_kx ? (int)o.tile_kx : 8;
   const int ky = o.tile_ky ? (int)o.tile_ky : 4;
-  const int ctas = o.ctas_per_sm ? (int)o.ctas_per_sm : 2;
+  if (o.superbin > 4) return fail(SAS_ERR_ARG, "superbin must be 0..4");
+  const uint64_t nv_search = v_end - v_begin;
+  const int sb = o.superbin ? (int)o.superbin : choose_superbin(d, n, n_min, nv_search);
 
   sas_result* res = new (std::nothrow) sas_result;
   if (!res) return fail(SAS_ERR_OOM, "host allocation");
@@ -304,7 +397,8 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   }
 
   Plan plan;
-  if (int rc = choose_tiles(d, E, dT, tph, kx, ky, cb, ctas, o, di, nullptr, &plan)) {
+  const int n_rows = (int)((v_end - 1) / d.nvx - v_begin / d.nvx + 1);
+  if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, nullptr, &plan)) {
     delete res;
     return rc;
   }
@@ -329,13 +423,14 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   }
   {  // the bucket cell may have grown: recompute the per-chunk epoch count
     Plan p2;
-    if (int rc = choose_tiles(d, E, dT, tph, kx, ky, cb, ctas, o, di, &cg, &p2)) {
+    if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, &cg, &p2)) {
       delete res;
       return rc;
     }
     plan.tc = p2.tc;
   }
   const uint64_t nb = (uint64_t)E * cg.ncx * cg.ncy;
+  tr.mark("planned");
 
   SearchGeom g{};
   g.vx0 = d.vx0; g.vy0 = d.vy0; g.dvx = d.dvx; g.dvy = d.dvy;
@@ -346,12 +441,13 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   g.E = E; g.tph = tph;
   g.v_begin = v_begin; g.v_end = v_end;
 
-  cudaEvent_t ev0, ev1, evs0, evs1;
+  cudaEvent_t ev0, ev1, evs0, evs1, evc0, evc1;
   cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&evs0); cudaEventCreate(&evs1);
+  cudaEventCreate(&evc0); cudaEventCreate(&evc1);
   struct EvGuard {
-    cudaEvent_t a, b, c, d;
-    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c); cudaEventDestroy(d); }
-  } evg{ev0, ev1, evs0, evs1};
+    cudaEvent_t e[6];
+    ~EvGuard() { for (cudaEvent_t x : e) cudaEventDestroy(x); }
+  } evg{{ev0, ev1, evs0, evs1, evc0, evc1}};
   cudaEventRecord(ev0, s);
 
   int rc = SAS_OK;
@@ -382,9 +478,11 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     uint32_t* d_raw = nullptr;
     unsigned long long *d_idoff = nullptr, *d_scan64 = nullptr;
     uint32_t* d_ids_tmp = nullptr;
-    uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1u << 14, n / 4), 1u << 26);
+    const uint32_t hint = grid->emit_hint.load(std::memory_order_relaxed);
+    uint32_t emit_cap = (uint32_t)std::min<uint64_t>(
+        std::max<uint64_t>({(uint64_t)1 << 16, 2 * n, (uint64_t)hint + hint / 4 + 1024}), (uint64_t)1 << 26);
     uint32_t h_small[3] = {0, 0, 0};
-    unsigned long long h_small64[3] = {0, 0, 0};
+    unsigned long long h_small64[4] = {0, 0, 0, 0};
     int64_t h_t0 = 0;
     uint32_t n_out = 0;
     unsigned long long n_ids = 0;
@@ -418,6 +516,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     CK(cudaMemsetAsync(d_bcount, 0, nb * 4, s), "memset");
     CK(cudaMemsetAsync(d_small, 0, 16, s), "memset");
     CK(cudaMemsetAsync(d_small64, 0, 32, s), "memset");
+    tr.mark("allocated");
 
     // a1-a3: ingest and validate, bucket, reference epoch, shift tables
     CK(launch_ingest(dx, dy, dep, n, E, cg, d_bcount, d_ecount, d_bof, &d_small[0], s), "ingest");
@@ -426,6 +525,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     CK(launch_scatter(dx, dy, dep, n, d_bof, d_cursor, d_dets, s), "scatter");
     CK(launch_epoch_setup(E, d_t, d_ecount, d_dt, d_t0, s), "epoch setup");
     CK(launch_shift_tables(g, d_dt, d_ecount, d_sxt, d_syt, &d_small[0], s), "shift tables");
+    tr.mark("prep launched");
 
     // a4-a6: the stack kernel; reruns (exact) with wider counters if one wrapped
     // or with a longer emission list if it overflowed.
@@ -436,17 +536,18 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       sa.g = g;
       sa.cg = cg;
       sa.tc = tc;
-      sa.magic = d.bin >= 2 ? magic_for(d.bin) : 0u;
-      sa.bin_is_one = d.bin == 1;
+      const int64_t sbin = (int64_t)tc.s * d.bin;
+      sa.magic = sbin >= 2 ? magic_for((int32_t)sbin) : 0u;
+      sa.bin_is_one = sbin == 1;
       sa.n_min = n_min;
       plan.ky_lo = (int)(v_begin / d.nvx);
       plan.ky_hi = (int)((v_end - 1) / d.nvx);
       sa.kx_lo = 0;
       sa.ky_lo = plan.ky_lo;
-      sa.nvt_x = (int)div_ceil_u32(d.nvx, tc.kx);
-      sa.nvt_y = (int)div_ceil_u32((uint32_t)(plan.ky_hi - plan.ky_lo + 1), tc.ky);
-      sa.nst_x = (int)div_ceil_u32(d.nbx, tc.tx);
-      sa.nst_y = (int)div_ceil_u32(d.nby, tc.ty);
+      sa.nvt_x = (int)div_ceil_u32(d.nvx, tc.kx * tc.bvx);
+      sa.nvt_y = (int)div_ceil_u32((uint32_t)(plan.ky_hi - plan.ky_lo + 1), tc.ky * tc.bvy);
+      sa.nst_x = (int)div_ceil_u32(d.nbx, tc.tx * tc.s);
+      sa.nst_y = (int)div_ceil_u32(d.nby, tc.ty * tc.s);
       sa.n_tiles = (uint64_t)sa.nvt_x * sa.nvt_y * sa.nst_x * sa.nst_y;
       sa.dets = d_dets;
       sa.boff = d_boff;
@@ -457,28 +558,34 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       sa.emit_cap = emit_cap;
       sa.n_emit = &d_small[1];
       sa.n_pairs = &d_small64[0];
+      sa.balance = &d_small64[3];
       sa.flags = &d_small[0];
       sa.tile_counter = &d_small64[1];
       CK(cudaMemsetAsync(&d_small[1], 0, 4, s), "memset");
       CK(cudaMemsetAsync(d_small64, 0, 16, s), "memset");
-      const int grid_sz = di.sms * tc.ctas_per_sm;
+      CK(cudaMemsetAsync(&d_small64[3], 0, 8, s), "memset");
+      const int grid_sz = (int)std::min<uint64_t>((uint64_t)di.sms, std::max<uint64_t>(sa.n_tiles, 1));
       cudaEventRecord(evs0, s);
+      tr.mark("stack configured");
       CK(launch_stack(sa, grid_sz, s), "stack kernel");
       cudaEventRecord(evs1, s);
+      tr.mark("stack launched");
       CK(cudaMemcpyAsync(h_small, d_small, 12, cudaMemcpyDeviceToHost, s), "read counters");
-      CK(cudaMemcpyAsync(h_small64, d_small64, 16, cudaMemcpyDeviceToHost, s), "read counters");
+      CK(cudaMemcpyAsync(h_small64, d_small64, 32, cudaMemcpyDeviceToHost, s), "read counters");
       CK(cudaMemcpyAsync(&h_t0, d_t0, 8, cudaMemcpyDeviceToHost, s), "read t0");
       CK(cudaStreamSynchronize(s), "stack sync");
+      tr.mark("stack done");
       if (h_small[0] & kFlagEpoch) { rc = fail(SAS_ERR_RANGE, "an epoch index is >= n_epochs"); goto done; }
       if (h_small[0] & kFlagPos) { rc = fail(SAS_ERR_RANGE, "a detection has |x| or |y| >= 2^29"); goto done; }
       if (h_small[0] & kFlagShift) { rc = fail(SAS_ERR_RANGE, "a shift |v*(t-t0)/TPH| >= 2^28"); goto done; }
       if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "stack kernel invariant"); goto done; }
       if (attempt >= 4) { rc = fail(SAS_ERR_INTERNAL, "stack kernel did not converge"); goto done; }
-      if (h_small[0] & kFlagCounter) {
+      if ((h_small[0] & kFlagCounter) || h_small64[3] != 0) {  // a counter wrapped
+        if (plan.tc.cb == 32) { rc = fail(SAS_ERR_INTERNAL, "32-bit counter wrapped"); goto done; }
         CK(cudaMemsetAsync(&d_small[0], 0, 4, s), "memset");
         const int wider = plan.tc.cb * 2;
         Plan p2;
-        if (int r2 = choose_tiles(d, E, dT, tph, kx, ky, wider, ctas, o, di, &cg, &p2)) { rc = r2; goto done; }
+        if (int r2 = choose_tiles(d, E, n, dT, tph, kx, ky, wider, sb, o, di, n_rows, &cg, &p2)) { rc = r2; goto done; }
         plan.tc = p2.tc;
         continue;
       }
@@ -495,16 +602,31 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     }
     {
       const uint32_t n_emit = h_small[1];
-      uint32_t n_pad = 1;
-      while (n_pad < n_emit) n_pad <<= 1;
-      CK(sc.alloc(&d_keys, n_pad), "alloc keys");
-      // a5/a7: exact distinct and raw counts of every emitted cell, then a8: order
-      CK(launch_cell_count(d_emits, n_emit, g, cg, d_dets, d_boff, d_ecount, d_sxt, d_syt, n_min,
-                           d_keys, &d_small[2], &d_small64[2], s), "cell count");
-      CK(launch_sort_keys(d_keys, n_emit, n_pad, s), "sort");
+      const_cast<sas_grid*>(grid)->emit_hint.store(n_emit, std::memory_order_relaxed);
+      const uint64_t n_keys = (uint64_t)n_emit * plan.tc.s * plan.tc.s;
+      if (n_keys >= (1ull << 31)) { rc = fail(SAS_ERR_OOM, "too many candidate bins; raise n_min"); goto done; }
+      CK(sc.alloc(&d_keys, n_keys), "alloc keys");
+      // a5/a7: exact distinct and raw counts of every bin of the emitted super-bins
+      cudaEventRecord(evc0, s);
+      CK(launch_cell_count(d_emits, n_emit, plan.tc.s, g, cg, d_dets, d_boff, d_ecount, d_sxt,
+                           d_syt, n_min, d_keys, &d_small[2], &d_small64[2], s), "cell count");
       CK(cudaMemcpyAsync(&h_small[2], &d_small[2], 4, cudaMemcpyDeviceToHost, s), "read n_valid");
       CK(cudaMemcpyAsync(&h_small64[2], &d_small64[2], 8, cudaMemcpyDeviceToHost, s), "read raw");
       CK(cudaStreamSynchronize(s), "count sync");
+      tr.mark("counts done");
+      {  // a8: total order of the valid keys
+        const uint32_t n_valid = h_small[2];
+        uint32_t n_pad = 1;
+        while (n_pad < n_valid) n_pad <<= 1;
+        Key* sort_buf = d_keys;
+        if (n_pad > n_keys) {
+          CK(sc.alloc(&sort_buf, n_pad), "alloc sort buffer");
+          CK(cudaMemcpyAsync(sort_buf, d_keys, (size_t)n_valid * sizeof(Key), cudaMemcpyDeviceToDevice, s), "copy keys");
+        }
+        CK(launch_sort_keys(sort_buf, n_valid, n_pad, s), "sort");
+        d_keys = sort_buf;
+      }
+      cudaEventRecord(evc1, s);
       n_out = h_small[2];
       if (o.max_candidates > 0 && n_out > o.max_candidates) n_out = (uint32_t)o.max_candidates;
       const uint64_t id_cap = std::max<uint64_t>(h_small64[2], 1);
@@ -525,6 +647,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       CK(cudaMemcpyAsync(&h_small[0], &d_small[0], 4, cudaMemcpyDeviceToHost, s), "read flags");
       cudaEventRecord(ev1, s);
       CK(cudaStreamSynchronize(s), "final sync");
+      tr.mark("ids done");
       if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "id gather invariant"); goto done; }
       res->info.n_candidates = n_out;
       res->info.n_ids = n_ids;
@@ -536,8 +659,15 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       res->info.tile_ky = (uint32_t)plan.tc.ky;
       res->info.tile_bx = (uint32_t)plan.tc.tx;
       res->info.tile_by = (uint32_t)plan.tc.ty;
+      res->info.superbin = (uint32_t)plan.tc.s;
+      res->info.vblock_x = (uint32_t)plan.tc.bvx;
+      res->info.vblock_y = (uint32_t)plan.tc.bvy;
+      res->info.staged_cap = (uint32_t)plan.tc.scap;
       cudaEventElapsedTime(&res->info.ms_stack, evs0, evs1);
       cudaEventElapsedTime(&res->info.ms_total, ev0, ev1);
+      cudaEventElapsedTime(&res->info.ms_count, evc0, evc1);
+      cudaEventElapsedTime(&res->info.ms_ids, evc1, ev1);
+      cudaEventElapsedTime(&res->info.ms_prep, ev0, evs0);
     }
   done:;
 #undef CK

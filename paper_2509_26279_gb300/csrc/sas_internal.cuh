@@ -67,15 +67,18 @@ struct __align__(8) Key {
   uint32_t c, pad;
 };
 
-// Stack kernel tile configuration.
+// Stack kernel configuration.
 struct TileCfg {
-  int kx, ky;        // velocities per tile (lattice block)
-  int tx, ty;        // bins per tile
+  int kx, ky;        // lattice points per velocity tile
+  int bvx, bvy;      // velocity tiles per velocity block (share one staged detection set)
+  int tx, ty;        // super-bins per spatial tile
+  int s;             // bins per super-bin side
   int cb;            // counter bits: 8, 16, 32
   int nt;            // threads per CTA
-  int ctas_per_sm;
-  int ec;            // epochs per segment chunk
-  int seg_cap;       // segment slots per chunk
+  int ec;            // epochs per chunk (<= 256)
+  int rows;          // bucket rows per epoch window (ec * rows <= seg_cap)
+  int seg_cap;       // segment slots per chunk (= nt)
+  int scap;          // staged detection records
   int emit_cap;      // per-CTA emission buffer entries
   size_t smem;       // dynamic shared memory bytes
 };
@@ -84,13 +87,13 @@ struct StackArgs {
   SearchGeom g;
   CoarseGeom cg;
   TileCfg tc;
-  uint32_t magic;      // umulhi(X, magic) = X / bin for 0 <= X < tile extent
-  int32_t bin_is_one;  // bin == 1: the quotient is X itself
+  uint32_t magic;      // umulhi(X, magic) = X / (s*bin) for 0 <= X < tile extent
+  int32_t bin_is_one;  // s*bin == 1: the quotient is X itself
   uint32_t n_min;
-  int32_t nvt_x, nvt_y;      // velocity tiles along kx, ky
-  int32_t kx_lo, ky_lo;      // first lattice column/row covered by the tiles
+  int32_t nvt_x, nvt_y;      // velocity blocks along kx, ky
+  int32_t kx_lo, ky_lo;      // first lattice column/row covered by the blocks
   int32_t nst_x, nst_y;      // spatial tiles
-  uint64_t n_tiles;
+  uint64_t n_tiles;          // work units = velocity blocks x spatial tiles
   const Det* dets;
   const uint32_t* boff;      // [E*ncy*ncx + 1]
   const uint32_t* ecount;    // [E] detections per epoch
@@ -100,6 +103,7 @@ struct StackArgs {
   uint32_t emit_cap;
   uint32_t* n_emit;
   unsigned long long* n_pairs;
+  unsigned long long* balance;  // sum over tiles of (counted - added); nonzero: a counter wrapped
   uint32_t* flags;
   unsigned long long* tile_counter;
 };
@@ -133,7 +137,9 @@ cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s);
 cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
 
 // sas_post.cu
-cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, const SearchGeom& g,
+// Appends one key per bin of an emitted super-bin that lies in the domain and
+// has >= n_min distinct epochs (keys needs room for s*s keys per emission).
+cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, const SearchGeom& g,
                               const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
                               const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
                               uint32_t n_min, Key* keys, uint32_t* n_valid,

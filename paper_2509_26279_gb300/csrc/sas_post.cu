@@ -43,11 +43,14 @@ __device__ __forceinline__ bool bin_window(const SearchGeom& g, const CoarseGeom
   return w.cxa <= w.cxb && w.cya <= w.cyb;
 }
 
-// One warp per emitted cell: lane l handles epochs l, l+32, ...  The epochs with
-// at least one detection in the cell form a bitmask per 32-epoch block
-// (__ballot_sync), whose popcount is the exact distinct-epoch count.
-__global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, SearchGeom g,
-                             CoarseGeom cg, const Det* __restrict__ dets,
+// One warp per emitted super-bin (s x s bins): lane l handles epochs l, l+32, ...
+// For every bin q of the super-bin, the epochs with at least one detection in it
+// form a bitmask per 32-epoch block (__ballot_sync) whose popcount adds up to the
+// exact distinct-epoch count; raw counts are summed over the warp.
+constexpr int kMaxS = 4;
+
+__global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, int sb,
+                             SearchGeom g, CoarseGeom cg, const Det* __restrict__ dets,
                              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ ecount,
                              const int32_t* __restrict__ sxt, const int32_t* __restrict__ syt,
                              uint32_t n_min, Key* __restrict__ keys, uint32_t* __restrict__ n_valid,
@@ -57,39 +60,56 @@ __global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, Se
   if (w >= n_emit) return;
   const Emit em = emits[w];
   const uint32_t kx = em.v_idx % (uint32_t)g.nvx, ky = em.v_idx / (uint32_t)g.nvx;
-  uint32_t distinct = 0, raw = 0;
+  const int nq = sb * sb;
+  const int32_t span = sb * g.bin;
+  uint32_t distinct[kMaxS * kMaxS], raw[kMaxS * kMaxS];
+#pragma unroll
+  for (int q = 0; q < kMaxS * kMaxS; ++q) distinct[q] = raw[q] = 0;
   for (uint32_t eb = 0; eb < g.E; eb += 32) {
     const uint32_t e = eb + lane;
-    uint32_t cnt = 0;
-    BinWindow bw;
-    if (e < g.E && ecount[e] > 0 && bin_window(g, cg, e, kx, ky, em.bx, em.by, sxt, syt, bw)) {
-      for (int cy = bw.cya; cy <= bw.cyb; ++cy) {
+    uint32_t hit = 0;
+    if (e < g.E && ecount[e] > 0) {
+      const int32_t ox = g.x_min + (int32_t)em.bx * g.bin + sxt[(size_t)kx * g.E + e];
+      const int32_t oy = g.y_min + (int32_t)em.by * g.bin + syt[(size_t)ky * g.E + e];
+      const int cxa = max(floor_div32(ox - cg.gx0, cg.cell), 0);
+      const int cxb = min(floor_div32(ox + span - 1 - cg.gx0, cg.cell), cg.ncx - 1);
+      const int cya = max(floor_div32(oy - cg.gy0, cg.cell), 0);
+      const int cyb = min(floor_div32(oy + span - 1 - cg.gy0, cg.cell), cg.ncy - 1);
+      for (int cy = cya; cy <= cyb && cxa <= cxb; ++cy) {
         const size_t b0 = ((size_t)e * cg.ncy + cy) * cg.ncx;
-        const uint32_t k1 = boff[b0 + bw.cxb + 1];
-        for (uint32_t k = boff[b0 + bw.cxa]; k < k1; ++k) {
+        const uint32_t k1 = boff[b0 + cxb + 1];
+        for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
           const Det d = dets[k];
-          cnt += ((uint32_t)(d.x - bw.ox) < (uint32_t)g.bin) &&
-                 ((uint32_t)(d.y - bw.oy) < (uint32_t)g.bin);
+          const uint32_t X = (uint32_t)(d.x - ox), Y = (uint32_t)(d.y - oy);
+          if (X < (uint32_t)span && Y < (uint32_t)span) {
+            const int q = (int)(Y / (uint32_t)g.bin) * sb + (int)(X / (uint32_t)g.bin);
+            hit |= 1u << q;
+#pragma unroll
+            for (int qq = 0; qq < kMaxS * kMaxS; ++qq) raw[qq] += (qq == q);
+          }
         }
       }
     }
-    const uint32_t mask = __ballot_sync(0xffffffffu, cnt > 0);
-    distinct += __popc(mask);
-    raw += cnt;
+#pragma unroll
+    for (int q = 0; q < kMaxS * kMaxS; ++q)
+      if (q < nq) distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
   }
-  for (int o = 16; o > 0; o >>= 1) raw += __shfl_xor_sync(0xffffffffu, raw, o);
-  if (lane == 0) {
-    if (distinct >= n_min) {
-      Key k;
-      k.a = ((uint64_t)(~distinct) << 32) | (uint64_t)(~raw);
-      k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)em.by;
-      k.c = em.bx;
-      k.pad = 0;
-      keys[w] = k;
-      atomicAdd(n_valid, 1u);
-      atomicAdd(raw_total, (unsigned long long)raw);
-    } else {
-      keys[w] = max_key();
+#pragma unroll
+  for (int q = 0; q < kMaxS * kMaxS; ++q) {
+    if (q >= nq) break;
+    uint32_t r = raw[q];
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) {
+      const uint32_t bx = em.bx + (uint32_t)(q % sb), by = em.by + (uint32_t)(q / sb);
+      if (bx < (uint32_t)g.nbx && by < (uint32_t)g.nby && distinct[q] >= n_min) {
+        Key k;
+        k.a = ((uint64_t)(~distinct[q]) << 32) | (uint64_t)(~r);
+        k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
+        k.c = bx;
+        k.pad = 0;
+        keys[atomicAdd(n_valid, 1u)] = k;  // compacted; the sort fixes the order
+        atomicAdd(raw_total, (unsigned long long)r);
+      }
     }
   }
 }
@@ -241,14 +261,15 @@ unsigned blocks_for(uint64_t n, unsigned per) { return (unsigned)((n + per - 1) 
 
 }  // namespace
 
-cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, const SearchGeom& g,
+cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, const SearchGeom& g,
                               const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
                               const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
                               uint32_t n_min, Key* keys, uint32_t* n_valid,
                               unsigned long long* raw_total, cudaStream_t s) {
   if (n_emit == 0) return cudaSuccess;
+  if (s_bins < 1 || s_bins > kMaxS) return cudaErrorInvalidValue;
   k_cell_count<<<blocks_for(n_emit, kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
-      emits, n_emit, g, cg, dets, boff, ecount, sxt, syt, n_min, keys, n_valid, raw_total);
+      emits, n_emit, s_bins, g, cg, dets, boff, ecount, sxt, syt, n_min, keys, n_valid, raw_total);
   note_launch();
   return cudaGetLastError();
 }

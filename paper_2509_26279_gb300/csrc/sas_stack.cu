@@ -1,363 +1,493 @@
-// The stack kernel: Sec. 2.1 steps 1-3 for one tile of the 3-D histogram at a time.
+// The stack kernel: Sec. 2.1 steps 1-3 for one block of the 3-D histogram at a time.
 //
-// A CTA owns a tile of KX x KY lattice velocities x TX x TY spatial bins and keeps
-// one narrow counter per cell in shared memory.  For every detection whose
-// projection can land in the tile (found through the (epoch, coarse cell)
-// buckets), it computes the projected bin at each of the tile's velocities --
-// the shift is separable, sx depends on kx only and sy on ky only, so a
-// detection costs KX + KY divisions -- and does one shared-memory atomicAdd per
-// (detection, velocity) pair that lands in the tile.  The counter counts
-// detections; a cell whose counter goes from N_min - 1 to N_min is emitted
-// exactly once (the crossing is a unique event).  Since distinct epochs <= raw
-// detections, the emitted set contains every cell with >= N_min distinct epochs;
-// the exact distinct-epoch count (bitmask + popcount) of each emitted cell is
-// taken afterwards (sas_post.cu), which also discards the rest.
+// Work unit = (spatial tile) x (velocity block).  A velocity block is BVX x BVY
+// velocity tiles of KX x KY lattice points.  For a unit, the detections whose
+// projection can land in the tile at any velocity of the block are found through
+// the (epoch, coarse cell) buckets, filtered to the exact union window of each
+// epoch and staged ONCE in shared memory as 8-byte records.  Then every velocity
+// tile of the block runs against shared memory only: per record, KX + KY
+// projections (the shift is separable: sx depends on kx, sy on ky) and one
+// shared-memory atomicAdd per (detection, velocity) pair that lands in the tile.
 //
-// Counters are packed CB bits wide, 32/CB per 32-bit word, and the packing runs
-// along kx so the byte lane and increment of every pair are compile-time
-// constants.  A counter that would wrap sets kFlagCounter and the host reruns
-// with wider counters, so results stay exact for any input.
+// Counters: one narrow counter (CB = 8/16/32 bits, packed along kx so lane and
+// increment are compile-time constants) per S x S block of bins ("super-bin")
+// per velocity, counting raw detections.  Distinct epochs <= raw detections of a
+// bin <= raw detections of its super-bin, so the super-bins whose count reaches
+// N_min contain every bin that can reach N_min distinct epochs; the exact
+// per-bin distinct-epoch counts (epoch bitmasks + popcount) are taken afterwards
+// in sas_post.cu, which also discards the rest.
+//
+// A counter starts at 2^(CB-1) - N_min, so its top bit is set exactly when its
+// count reaches N_min.  The hot loop therefore only adds (the atomics' old
+// values are never read).  The pass that resets a tile's counters after its
+// velocity tile is done reads them first: every counter with the top bit set is
+// emitted once, and the counters' excess over their start value is summed.  A
+// counter that wrapped (more than 2^(CB-1) - 1 + N_min detections) makes that sum
+// fall short of the number of pairs added, by 255 or 256 per wrap; the kernel
+// accumulates (sum - pairs) into a global balance and the host reruns with wider
+// counters when it is not zero, so the result is exact for any input.
 #include "sas_internal.cuh"
 
 namespace sas {
 
 namespace {
 
-constexpr int kNT = 512;
+constexpr int kNT = 1024;
 constexpr int32_t kOutside = -(1 << 30);  // table entry of a lattice column that does not exist
 
 struct SmemLayout {
-  size_t cells, ox, oy, seg_pos, seg_src, emit, misc, total;
+  size_t cells, staged, ox, oy, win, seg_pos, seg_src, emit, misc, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
-__host__ __device__ inline SmemLayout layout(int kx, int ky, int tx, int ty, int cb, int ec,
-                                             int seg_cap, int emit_cap) {
+__host__ __device__ inline SmemLayout layout(const TileCfg& tc) {
   SmemLayout L;
-  const int per_word = 32 / cb;
+  const int per_word = 32 / tc.cb;
   size_t off = 0;
   L.cells = off;
-  off += align16((size_t)ky * (kx / per_word) * tx * ty * 4);
+  off += align16((size_t)tc.ky * (tc.kx / per_word) * tc.tx * tc.ty * 4);
+  L.staged = off;
+  off += align16((size_t)tc.scap * 8);
   L.ox = off;
-  off += align16((size_t)ec * kx * 4);
+  off += align16((size_t)tc.ec * tc.bvx * tc.kx * 4);
   L.oy = off;
-  off += align16((size_t)ec * ky * 4);
+  off += align16((size_t)tc.ec * tc.bvy * tc.ky * 4);
+  L.win = off;
+  off += align16((size_t)tc.ec * 4 * 4);
   L.seg_pos = off;
-  off += align16((size_t)(seg_cap + 1) * 4);
+  off += align16((size_t)(tc.seg_cap + 1) * 4);
   L.seg_src = off;
-  off += align16((size_t)seg_cap * 4);
+  off += align16((size_t)tc.seg_cap * 4);
   L.emit = off;
-  off += align16((size_t)emit_cap * sizeof(Emit));
+  off += align16((size_t)tc.emit_cap * sizeof(Emit));
   L.misc = off;
   off += 512;
   L.total = off;
   return L;
 }
 
-// Block-wide exclusive scan of two values at once (kNT threads).
-__device__ inline void scan2(uint32_t a, uint32_t b, uint32_t* s_tmp, uint32_t& ea, uint32_t& eb,
-                             uint32_t& ta, uint32_t& tb) {
+// Block-wide exclusive scan of one value per thread (kNT threads).
+__device__ inline uint32_t block_scan(uint32_t v, uint32_t* s_tmp, uint32_t& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t ia = a, ib = b;
+  uint32_t inc = v;
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t na = __shfl_up_sync(0xffffffffu, ia, o);
-    const uint32_t nb = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) { ia += na; ib += nb; }
+    const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += n;
   }
-  if (lane == 31) { s_tmp[w] = ia; s_tmp[32 + w] = ib; }
+  if (lane == 31) s_tmp[w] = inc;
   __syncthreads();
   if (w == 0) {
     constexpr int nw = kNT / 32;
-    const uint32_t va = lane < nw ? s_tmp[lane] : 0u;
-    const uint32_t vb = lane < nw ? s_tmp[32 + lane] : 0u;
-    uint32_t sa = va, sb = vb;
+    const uint32_t x = lane < nw ? s_tmp[lane] : 0u;
+    uint32_t s = x;
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t na = __shfl_up_sync(0xffffffffu, sa, o);
-      const uint32_t nb = __shfl_up_sync(0xffffffffu, sb, o);
-      if (lane >= o) { sa += na; sb += nb; }
+      const uint32_t n = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += n;
     }
-    if (lane < nw) { s_tmp[lane] = sa - va; s_tmp[32 + lane] = sb - vb; }
-    if (lane == nw - 1) { s_tmp[64] = sa; s_tmp[65] = sb; }
+    if (lane < nw) s_tmp[lane] = s - x;
+    if (lane == nw - 1) s_tmp[32] = s;
   }
   __syncthreads();
-  ea = s_tmp[w] + ia - a;
-  eb = s_tmp[32 + w] + ib - b;
-  ta = s_tmp[64];
-  tb = s_tmp[65];
+  const uint32_t r = s_tmp[w] + inc - v;
+  total = s_tmp[32];
   __syncthreads();
+  return r;
 }
 
-template <int KX, int KY, int CB>
-struct Tile {
-  static constexpr int P = 32 / CB;            // counters per word
+template <int CB>
+struct Counter {
+  static constexpr int P = 32 / CB;  // counters per word
   static constexpr uint32_t CMASK = CB == 32 ? 0xffffffffu : ((1u << CB) - 1u);
 };
 
-// Where a threshold crossing is recorded: the CTA's buffer, else the global list.
-struct EmitCtx {
-  Emit* s_emit;
-  uint32_t* s_count;
-  uint32_t s_cap;
-  Emit* g_emit;
-  uint32_t* g_count;
-  uint32_t g_cap;
-  uint32_t v_base;  // v_idx of the tile's (kx0, ky0)
-  uint32_t nvx;
-  uint32_t bx0, by0;
-  uint32_t flags;
-};
-
-__device__ __noinline__ void emit_cell(EmitCtx& ec, uint32_t dv, uint32_t bxl, uint32_t byl) {
-  Emit em;
-  em.v_idx = ec.v_base + dv;
-  em.bx = ec.bx0 + bxl;
-  em.by = ec.by0 + byl;
-  em.pad = 0;
-  const uint32_t p = atomicAdd(ec.s_count, 1u);
-  if (p < ec.s_cap) {
-    ec.s_emit[p] = em;
-  } else {
-    const uint32_t gp = atomicAdd(ec.g_count, 1u);
-    if (gp < ec.g_cap) ec.g_emit[gp] = em; else ec.flags |= kFlagEmitCap;
-  }
-}
-
-// One detection against every velocity of the tile (Sec. 2.1 steps 1-2).
+// One staged detection against every velocity of the tile (Sec. 2.1 steps 1-2).
+// ox/oy hold the tile origin plus the shift of each lattice column/row, relative
+// to the same window origin as the staged coordinates, so X = xr - ox[k] is the
+// projected position relative to the tile origin.  Returns the number of
+// (detection, velocity) pairs that landed in the tile.
 template <int KX, int KY, int CB, bool MASKED>
-__device__ __forceinline__ void process_det(const Det& d, int el, const int32_t* __restrict__ s_ox,
-                                            const int32_t* __restrict__ s_oy,
-                                            uint32_t* __restrict__ cells, uint32_t tw_x,
-                                            uint32_t tw_y, uint32_t magic, bool bin_one, int tx,
-                                            int txty, uint32_t act, uint32_t nmin1,
-                                            uint64_t& pairs, EmitCtx& ec) {
-  using T = Tile<KX, KY, CB>;
-  uint32_t col[KX];
-  bool okx[KX];
+__device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
+                                                const int32_t* __restrict__ ox,
+                                                const int32_t* __restrict__ oy,
+                                                uint32_t* __restrict__ cells, uint32_t tw_x,
+                                                uint32_t tw_y, uint32_t magic, bool one, int tx,
+                                                int txty, uint32_t act) {
+  using C = Counter<CB>;
+  int32_t oxv[KX], oyv[KY];
+  if constexpr (KX % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < KX; k += 4) {
+      const int4 q = *reinterpret_cast<const int4*>(ox + k);
+      oxv[k] = q.x; oxv[k + 1] = q.y; oxv[k + 2] = q.z; oxv[k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < KX; ++k) oxv[k] = ox[k];
+  }
+  if constexpr (KY % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < KY; k += 4) {
+      const int4 q = *reinterpret_cast<const int4*>(oy + k);
+      oyv[k] = q.x; oyv[k + 1] = q.y; oyv[k + 2] = q.z; oyv[k + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < KY; ++k) oyv[k] = oy[k];
+  }
+  uint32_t col[KX], okxb = 0;
 #pragma unroll
   for (int k = 0; k < KX; ++k) {
-    const uint32_t X = (uint32_t)(d.x - s_ox[el * KX + k]);
-    okx[k] = X < tw_x;
-    col[k] = bin_one ? X : __umulhi(X, magic);
+    const uint32_t X = xr - (uint32_t)oxv[k];
+    okxb |= (uint32_t)(X < tw_x) << k;
+    col[k] = one ? X : __umulhi(X, magic);
   }
-  uint32_t row[KY];
-  bool oky[KY];
+  uint32_t rbase[KY], okyb = 0;
 #pragma unroll
   for (int k = 0; k < KY; ++k) {
-    const uint32_t Y = (uint32_t)(d.y - s_oy[el * KY + k]);
-    oky[k] = Y < tw_y;
-    row[k] = bin_one ? Y : __umulhi(Y, magic);
+    const uint32_t Y = yr - (uint32_t)oyv[k];
+    okyb |= (uint32_t)(Y < tw_y) << k;
+    rbase[k] = (one ? Y : __umulhi(Y, magic)) * (uint32_t)tx;
   }
+  uint32_t m = 0;
+#pragma unroll
+  for (int ky = 0; ky < KY; ++ky)
+    if ((okyb >> ky) & 1u) m |= okxb << (ky * KX);
+  if (MASKED) m &= act;
 #pragma unroll
   for (int ky = 0; ky < KY; ++ky) {
-    const uint32_t rbase = row[ky] * (uint32_t)tx;
 #pragma unroll
     for (int kx = 0; kx < KX; ++kx) {
-      bool ok = okx[kx] && oky[ky];
-      if (MASKED) ok = ok && ((act >> (ky * KX + kx)) & 1u);
-      if (ok) {
-        const uint32_t widx = (uint32_t)((ky * (KX / T::P) + kx / T::P) * txty) + rbase + col[kx];
-        const int sh = CB * (kx % T::P);  // folds to a constant once unrolled
-        const uint32_t old = atomicAdd(&cells[widx], 1u << sh);
-        const uint32_t c = (old >> sh) & T::CMASK;
-        ++pairs;
-        if (c >= nmin1) {
-          if (c == nmin1) emit_cell(ec, (uint32_t)ky * ec.nvx + kx, col[kx], row[ky]);
-          if (c == T::CMASK) ec.flags |= kFlagCounter;  // counter wrapped: rerun wider
-        }
+      if ((m >> (ky * KX + kx)) & 1u) {
+        const uint32_t widx = (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty) + rbase[ky] + col[kx];
+        atomicAdd(&cells[widx], 1u << (CB * (kx % C::P)));  // old value unused: a reduction
       }
     }
   }
+  return (uint32_t)__popc(m);
+}
+
+// Sum of the counters packed in one word.
+template <int CB>
+__device__ __forceinline__ uint32_t word_sum(uint32_t w) {
+  if constexpr (CB == 8) return __dp4a(w, 0x01010101u, 0u);
+  else if constexpr (CB == 16) return (w & 0xffffu) + (w >> 16);
+  else return w;
 }
 
 template <int KX, int KY, int CB>
-__global__ void __launch_bounds__(kNT, 2) k_stack(StackArgs a) {
+__global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
   static_assert(KX % (32 / CB) == 0, "kx must be a multiple of the counters per word");
-  static_assert(KX * KY <= 31, "at most 31 velocities per tile");
+  static_assert(KX * KY <= 32, "at most 32 velocities per tile");
+  using C = Counter<CB>;
   extern __shared__ __align__(16) unsigned char smem[];
   const TileCfg& tc = a.tc;
-  const SmemLayout L = layout(KX, KY, tc.tx, tc.ty, CB, tc.ec, tc.seg_cap, tc.emit_cap);
+  const SmemLayout L = layout(tc);
   uint32_t* cells = reinterpret_cast<uint32_t*>(smem + L.cells);
+  uint2* staged = reinterpret_cast<uint2*>(smem + L.staged);
   int32_t* s_ox = reinterpret_cast<int32_t*>(smem + L.ox);
   int32_t* s_oy = reinterpret_cast<int32_t*>(smem + L.oy);
+  int32_t* s_win = reinterpret_cast<int32_t*>(smem + L.win);  // [ec][4]: xlo, xw, ylo, yw
   uint32_t* s_seg_pos = reinterpret_cast<uint32_t*>(smem + L.seg_pos);
   uint32_t* s_seg_src = reinterpret_cast<uint32_t*>(smem + L.seg_src);
   Emit* s_emit = reinterpret_cast<Emit*>(smem + L.emit);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
-  // s_misc: [0..66) scan scratch, [70] tile lo, [71] tile hi, [72] active mask,
-  //         [73] emission count, [74] flags
+  // s_misc: [0..33) scan scratch, [40] unit lo, [41] unit hi, [42] active mask,
+  //         [43] emission count, [44] flush base, [45] staged count
   const int tid = threadIdx.x;
-  const int P = 32 / CB;
+  constexpr int P = C::P;
   const uint32_t n_words = (uint32_t)KY * (KX / P) * tc.tx * tc.ty;
   const int txty = tc.tx * tc.ty;
   const SearchGeom& g = a.g;
   const CoarseGeom& cg = a.cg;
   const uint32_t E = g.E;
-  const uint32_t nmin1 = a.n_min - 1u;
   const int n_st = a.nst_x * a.nst_y;
+  const int bxk = tc.bvx * KX, byk = tc.bvy * KY;  // lattice columns / rows of a block
+  const int sbins = tc.s;                          // bins per super-bin side
+  const int rows_per_epoch = tc.rows;
+  const bool single_chunk = E <= (uint32_t)tc.ec;
+  // counter start value: the top bit turns on when the count reaches n_min
+  const uint32_t start = (1u << (CB - 1)) - a.n_min;
+  uint32_t start_word = 0;
+#pragma unroll
+  for (int q = 0; q < P; ++q) start_word |= start << (CB * q);
+  uint32_t tmask = 0;  // the top bit of every counter in a word
+#pragma unroll
+  for (int q = 0; q < P; ++q) tmask |= (1u << (CB - 1)) << (CB * q);
+  const uint4 start4 = make_uint4(start_word, start_word, start_word, start_word);
 
-  for (uint32_t i = tid; i < n_words / 4; i += kNT)
-    reinterpret_cast<uint4*>(cells)[i] = make_uint4(0, 0, 0, 0);
-  uint64_t pairs = 0;
+  for (uint32_t i = tid; i < n_words / 4; i += kNT) reinterpret_cast<uint4*>(cells)[i] = start4;
+  if (tid == 0) s_misc[43] = 0;
+  int64_t balance = 0;  // (counted excess over the start values) - (pairs added)
+  uint64_t pairs64 = 0;
   uint32_t my_flags = 0;
 
   while (true) {
     if (tid == 0) {
       const unsigned long long t = atomicAdd(a.tile_counter, 1ull);
-      s_misc[70] = (uint32_t)t;
-      s_misc[71] = (uint32_t)(t >> 32);
-      s_misc[73] = 0;
+      s_misc[40] = (uint32_t)t;
+      s_misc[41] = (uint32_t)(t >> 32);
     }
     __syncthreads();
-    const uint64_t tile = (uint64_t)s_misc[70] | ((uint64_t)s_misc[71] << 32);
-    if (tile >= a.n_tiles) break;
-    const int vt = (int)(tile / n_st), st = (int)(tile % n_st);
-    const int kx0 = a.kx_lo + (vt % a.nvt_x) * KX;
-    const int ky0 = a.ky_lo + (vt / a.nvt_x) * KY;
-    const int bx0 = (st % a.nst_x) * tc.tx;
-    const int by0 = (st / a.nst_x) * tc.ty;
-    const int txe = min(tc.tx, g.nbx - bx0), tye = min(tc.ty, g.nby - by0);
-    const uint32_t tw_x = (uint32_t)txe * (uint32_t)g.bin, tw_y = (uint32_t)tye * (uint32_t)g.bin;
+    const uint64_t unit = (uint64_t)s_misc[40] | ((uint64_t)s_misc[41] << 32);
+    if (unit >= a.n_tiles) break;
+    const int vb = (int)(unit / n_st), st = (int)(unit % n_st);
+    const int kxa = a.kx_lo + (vb % a.nvt_x) * bxk;   // nvt_x/nvt_y count velocity BLOCKS
+    const int kya = a.ky_lo + (vb / a.nvt_x) * byk;
+    const int kxb = min(kxa + bxk, g.nvx) - 1;
+    const int kyb = min(kya + byk, g.nvy) - 1;
+    const int bx0 = (st % a.nst_x) * tc.tx * sbins;
+    const int by0 = (st / a.nst_x) * tc.ty * sbins;
+    const uint32_t tw_x = (uint32_t)min(tc.tx * sbins, g.nbx - bx0) * (uint32_t)g.bin;
+    const uint32_t tw_y = (uint32_t)min(tc.ty * sbins, g.nby - by0) * (uint32_t)g.bin;
     const int32_t X0 = g.x_min + bx0 * g.bin, Y0 = g.y_min + by0 * g.bin;
 
-    // Which (kx, ky) of the tile are searched: inside the lattice, inside the
-    // requested index range and inside the speed annulus.
-    if (tid < 32) {
-      bool act = false;
-      if (tid < KX * KY) {
-        const int kx = kx0 + tid % KX, ky = ky0 + tid / KX;
-        if (kx < g.nvx && ky < g.nvy) {
-          const uint64_t v = (uint64_t)ky * g.nvx + kx;
-          act = v >= g.v_begin && v < g.v_end;
-          if (act && (g.smin != 0 || g.smax != 0)) {
-            const int64_t vx = (int64_t)g.vx0 + (int64_t)kx * g.dvx;
-            const int64_t vy = (int64_t)g.vy0 + (int64_t)ky * g.dvy;
-            const int64_t s2 = vx * vx + vy * vy;
-            act = s2 >= (int64_t)g.smin * g.smin && s2 <= (int64_t)g.smax * g.smax;
-          }
-        }
-      }
-      const uint32_t m = __ballot_sync(0xffffffffu, act);
-      if (tid == 0) s_misc[72] = m;
-    }
-    __syncthreads();
-    const uint32_t act = s_misc[72];
-    if (act == 0) continue;  // nothing searched here; every thread sees the same value
-    const uint32_t full = (KX * KY == 32) ? 0xffffffffu : ((1u << (KX * KY)) - 1u);
-    const bool masked = act != full;
-    const int kxl = min(kx0 + KX, g.nvx) - 1;  // last lattice column of the tile
-    const int kyl = min(ky0 + KY, g.nvy) - 1;
-
-    for (uint32_t e_base = 0; e_base < E; e_base += tc.ec) {
+    // --- prepare one epoch chunk: windows, shift tables, bucket segments -----
+    auto prepare_chunk = [&](uint32_t e_base) -> uint32_t {
       const int ne = (int)min((uint32_t)tc.ec, E - e_base);
-      // Shift table of this chunk, offset by the tile origin.
-      for (int i = tid; i < ne * (KX + KY); i += kNT) {
-        if (i < ne * KX) {
-          const int el = i / KX, k = i % KX;
-          const int kx = kx0 + k;
-          s_ox[el * KX + k] = kx < g.nvx ? X0 + a.sxt[(size_t)kx * E + e_base + el] : kOutside;
+      if (tid < ne) {
+        const uint32_t e = e_base + tid;
+        int32_t xlo = 0, xw = 0, ylo = 0, yw = 0;
+        if (a.ecount[e] > 0) {
+          const int32_t s0 = a.sxt[(size_t)kxa * E + e], s1 = a.sxt[(size_t)kxb * E + e];
+          const int32_t t0 = a.syt[(size_t)kya * E + e], t1 = a.syt[(size_t)kyb * E + e];
+          xlo = X0 + min(s0, s1);
+          xw = max(s0, s1) - min(s0, s1) + (int32_t)tw_x;
+          ylo = Y0 + min(t0, t1);
+          yw = max(t0, t1) - min(t0, t1) + (int32_t)tw_y;
+          if (xw >= (1 << 24)) my_flags |= kFlagInternal;  // staged x must fit 24 bits
+        }
+        s_win[tid * 4 + 0] = xlo;
+        s_win[tid * 4 + 1] = xw;
+        s_win[tid * 4 + 2] = ylo;
+        s_win[tid * 4 + 3] = yw;
+      }
+      __syncthreads();
+      for (int i = tid; i < ne * (bxk + byk); i += kNT) {
+        if (i < ne * bxk) {
+          const int el = i / bxk, k = i % bxk, kx = kxa + k;
+          s_ox[el * bxk + k] = (kx < g.nvx && s_win[el * 4 + 1] > 0)
+                                   ? X0 + a.sxt[(size_t)kx * E + e_base + el] - s_win[el * 4]
+                                   : kOutside;
         } else {
-          const int j = i - ne * KX;
-          const int el = j / KY, k = j % KY;
-          const int ky = ky0 + k;
-          s_oy[el * KY + k] = ky < g.nvy ? Y0 + a.syt[(size_t)ky * E + e_base + el] : kOutside;
+          const int j = i - ne * bxk;
+          const int el = j / byk, k = j % byk, ky = kya + k;
+          s_oy[el * byk + k] = (ky < g.nvy && s_win[el * 4 + 3] > 0)
+                                   ? Y0 + a.syt[(size_t)ky * E + e_base + el] - s_win[el * 4 + 2]
+                                   : kOutside;
         }
       }
-      // Source window of the tile at this epoch -> bucket rows.
-      uint32_t nrows = 0, ndet = 0;
-      int cxa = 0, cxb = -1, cya = 0, cyb = -1;
-      const uint32_t e = e_base + tid;
-      if (tid < ne && a.ecount[e] > 0) {
-        const int32_t s0 = a.sxt[(size_t)kx0 * E + e], s1 = a.sxt[(size_t)kxl * E + e];
-        const int32_t t0 = a.syt[(size_t)ky0 * E + e], t1 = a.syt[(size_t)kyl * E + e];
-        const int32_t xa = X0 + min(s0, s1), xb = X0 + max(s0, s1) + (int32_t)tw_x;  // [xa, xb)
-        const int32_t ya = Y0 + min(t0, t1), yb = Y0 + max(t0, t1) + (int32_t)tw_y;
-        cxa = max(floor_div32(xa - cg.gx0, cg.cell), 0);
-        cxb = min(floor_div32(xb - 1 - cg.gx0, cg.cell), cg.ncx - 1);
-        cya = max(floor_div32(ya - cg.gy0, cg.cell), 0);
-        cyb = min(floor_div32(yb - 1 - cg.gy0, cg.cell), cg.ncy - 1);
-        if (cxa <= cxb && cya <= cyb) {
-          for (int cy = cya; cy <= cyb; ++cy) {  // rows holding at least one detection
-            const size_t b0 = ((size_t)e * cg.ncy + cy) * cg.ncx;
-            const uint32_t len = a.boff[b0 + cxb + 1] - a.boff[b0 + cxa];
-            if (len) { ++nrows; ndet += len; }
+      // One segment per (epoch, bucket row): thread t owns item t.
+      uint32_t len = 0, src = 0;
+      {
+        const int el = tid / rows_per_epoch, r = tid % rows_per_epoch;
+        if (el < ne && s_win[el * 4 + 1] > 0) {
+          const int32_t xlo = s_win[el * 4], ylo = s_win[el * 4 + 2];
+          const int cxa = max(floor_div32(xlo - cg.gx0, cg.cell), 0);
+          const int cxb = min(floor_div32(xlo + s_win[el * 4 + 1] - 1 - cg.gx0, cg.cell), cg.ncx - 1);
+          const int cya = max(floor_div32(ylo - cg.gy0, cg.cell), 0);
+          const int cyb = min(floor_div32(ylo + s_win[el * 4 + 3] - 1 - cg.gy0, cg.cell), cg.ncy - 1);
+          const int cy = cya + r;
+          if (cxa <= cxb && cy <= cyb) {
+            const size_t b0 = ((size_t)(e_base + el) * cg.ncy + cy) * cg.ncx;
+            src = a.boff[b0 + cxa];
+            len = a.boff[b0 + cxb + 1] - src;
+          }
+          if (r == rows_per_epoch - 1 && cyb - cya + 1 > rows_per_epoch) my_flags |= kFlagInternal;
+        }
+      }
+      uint32_t total;
+      const uint32_t pos = block_scan(len, s_misc, total);
+      s_seg_pos[tid] = pos;
+      s_seg_src[tid] = src;
+      __syncthreads();
+      return total;
+    };
+
+    // --- stage detections [p0, p1) of the chunk, keeping those in the window --
+    auto stage = [&](uint32_t e_base, uint32_t p0, uint32_t p1) -> uint32_t {
+      if (tid == 0) s_misc[45] = 0;
+      __syncthreads();
+      for (uint32_t j0 = p0; j0 < p1; j0 += kNT) {
+        const uint32_t j = j0 + tid;
+        bool keep = false;
+        uint2 rec = make_uint2(0, 0);
+        if (j < p1) {
+          uint32_t lo = 0, hi = kNT;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_seg_pos[mid] <= j) lo = mid; else hi = mid;
+          }
+          const Det d = a.dets[s_seg_src[lo] + (j - s_seg_pos[lo])];
+          const int el = (int)(d.e - e_base);
+          const uint32_t xr = (uint32_t)(d.x - s_win[el * 4]);
+          const uint32_t yr = (uint32_t)(d.y - s_win[el * 4 + 2]);
+          keep = xr < (uint32_t)s_win[el * 4 + 1] && yr < (uint32_t)s_win[el * 4 + 3];
+          rec = make_uint2(xr | ((uint32_t)el << 24), yr);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+        uint32_t base = 0;
+        if ((tid & 31) == 0 && m) base = atomicAdd(&s_misc[45], (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) staged[base + __popc(m & ((1u << (tid & 31)) - 1u))] = rec;
+      }
+      __syncthreads();
+      const uint32_t ns = s_misc[45];
+      __syncthreads();
+      return ns;
+    };
+
+    // --- which lattice points of a velocity tile are searched ----------------
+    auto active_mask = [&](int kx0, int ky0) -> uint32_t {
+      if (tid < 32) {
+        bool act = false;
+        if (tid < KX * KY) {
+          const int kx = kx0 + tid % KX, ky = ky0 + tid / KX;
+          if (kx < g.nvx && ky <= kyb) {
+            const uint64_t v = (uint64_t)ky * g.nvx + kx;
+            act = v >= g.v_begin && v < g.v_end;
+            if (act && (g.smin != 0 || g.smax != 0)) {
+              const int64_t vx = (int64_t)g.vx0 + (int64_t)kx * g.dvx;
+              const int64_t vy = (int64_t)g.vy0 + (int64_t)ky * g.dvy;
+              const int64_t s2 = vx * vx + vy * vy;
+              act = s2 >= (int64_t)g.smin * g.smin && s2 <= (int64_t)g.smax * g.smax;
+            }
           }
         }
+        const uint32_t m = __ballot_sync(0xffffffffu, act);
+        if (tid == 0) s_misc[42] = m;
       }
-      uint32_t seg_off, det_off, nseg, D;
-      scan2(nrows, ndet, s_misc, seg_off, det_off, nseg, D);
-      if (nseg > (uint32_t)tc.seg_cap) {  // cannot happen with host-chosen sizes
-        my_flags |= kFlagInternal;
-        nseg = 0;
-        D = 0;
-      } else if (nrows) {
-        uint32_t si = seg_off, pos = det_off;
-        for (int cy = cya; cy <= cyb; ++cy) {
-          const size_t b0 = ((size_t)e * cg.ncy + cy) * cg.ncx;
-          const uint32_t st0 = a.boff[b0 + cxa];
-          const uint32_t len = a.boff[b0 + cxb + 1] - st0;
-          if (!len) continue;
-          s_seg_pos[si] = pos;
-          s_seg_src[si] = st0;
-          ++si;
-          pos += len;
+      __syncthreads();
+      const uint32_t act = s_misc[42];
+      __syncthreads();
+      return act;
+    };
+
+    // --- run one velocity tile of the block against the staged records -------
+    auto compute = [&](int vtx, int vty, uint32_t act, uint32_t n_staged) {
+      const uint32_t full = (KX * KY == 32) ? 0xffffffffu : ((1u << (KX * KY)) - 1u);
+      const int oxo = vtx * KX, oyo = vty * KY;
+      uint32_t pairs = 0;
+      if (act == full) {
+        for (uint32_t j = tid; j < n_staged; j += kNT) {
+          const uint2 r = staged[j];
+          const int el = (int)(r.x >> 24);
+          pairs += process_rec<KX, KY, CB, false>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
+                                                  s_oy + el * byk + oyo, cells, tw_x, tw_y,
+                                                  a.magic, a.bin_is_one, tc.tx, txty, act);
+        }
+      } else {
+        for (uint32_t j = tid; j < n_staged; j += kNT) {
+          const uint2 r = staged[j];
+          const int el = (int)(r.x >> 24);
+          pairs += process_rec<KX, KY, CB, true>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
+                                                 s_oy + el * byk + oyo, cells, tw_x, tw_y,
+                                                 a.magic, a.bin_is_one, tc.tx, txty, act);
         }
       }
-      __syncthreads();
+      pairs64 += pairs;
+      balance -= pairs;
+    };
 
-      EmitCtx ecx;
-      ecx.s_emit = s_emit;
-      ecx.s_count = &s_misc[73];
-      ecx.s_cap = (uint32_t)tc.emit_cap;
-      ecx.g_emit = a.emits;
-      ecx.g_count = a.n_emit;
-      ecx.g_cap = a.emit_cap;
-      ecx.v_base = (uint32_t)ky0 * (uint32_t)g.nvx + (uint32_t)kx0;
-      ecx.nvx = (uint32_t)g.nvx;
-      ecx.bx0 = (uint32_t)bx0;
-      ecx.by0 = (uint32_t)by0;
-      ecx.flags = 0;
-      for (uint32_t j = tid; j < D; j += kNT) {
-        uint32_t lo = 0, hi = nseg;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (s_seg_pos[mid] <= j) lo = mid; else hi = mid;
+    // --- read every counter of the tile: emit those at or over n_min, add up
+    //     the counts, and reset them to the start value -----------------------
+    auto finish = [&](int kx0, int ky0) {
+      __syncthreads();
+      for (uint32_t i = tid; i < n_words / 4; i += kNT) {
+        const uint4 v = reinterpret_cast<const uint4*>(cells)[i];
+        balance += (int64_t)word_sum<CB>(v.x) + (int64_t)word_sum<CB>(v.y) +
+                   (int64_t)word_sum<CB>(v.z) + (int64_t)word_sum<CB>(v.w) - (int64_t)4 * P * start;
+        if ((v.x | v.y | v.z | v.w) & tmask) {
+          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+          for (int q = 0; q < 4; ++q) {
+            for (int lane = 0; lane < P; ++lane) {
+              if (!((wv[q] >> (CB * lane + CB - 1)) & 1u)) continue;
+              const uint32_t widx = 4 * i + q;
+              const uint32_t r = widx / (uint32_t)txty, rem = widx % (uint32_t)txty;
+              const uint32_t row = rem / (uint32_t)tc.tx, col = rem % (uint32_t)tc.tx;
+              const uint32_t ky = r / (KX / P), kx = (r % (KX / P)) * P + lane;
+              Emit em;
+              em.v_idx = (uint32_t)(ky0 + ky) * (uint32_t)g.nvx + (uint32_t)(kx0 + kx);
+              em.bx = (uint32_t)bx0 + col * sbins;
+              em.by = (uint32_t)by0 + row * sbins;
+              em.pad = 0;
+              const uint32_t p = atomicAdd(&s_misc[43], 1u);
+              if (p < (uint32_t)tc.emit_cap) {
+                s_emit[p] = em;
+              } else {
+                const uint32_t gp = atomicAdd(a.n_emit, 1u);
+                if (gp < a.emit_cap) a.emits[gp] = em; else my_flags |= kFlagEmitCap;
+              }
+            }
+          }
         }
-        const Det d = a.dets[s_seg_src[lo] + (j - s_seg_pos[lo])];
-        const int el = (int)(d.e - e_base);
-        if (masked)
-          process_det<KX, KY, CB, true>(d, el, s_ox, s_oy, cells, tw_x, tw_y, a.magic,
-                                        a.bin_is_one, tc.tx, txty, act, nmin1, pairs, ecx);
-        else
-          process_det<KX, KY, CB, false>(d, el, s_ox, s_oy, cells, tw_x, tw_y, a.magic,
-                                         a.bin_is_one, tc.tx, txty, act, nmin1, pairs, ecx);
+        reinterpret_cast<uint4*>(cells)[i] = start4;
       }
-      my_flags |= ecx.flags;
       __syncthreads();
-    }
+      const uint32_t ne_tile = min(s_misc[43], (uint32_t)tc.emit_cap);
+      if (ne_tile) {
+        if (tid == 0) s_misc[44] = atomicAdd(a.n_emit, ne_tile);
+        __syncthreads();
+        const uint32_t base = s_misc[44];
+        for (uint32_t i = tid; i < ne_tile; i += kNT) {
+          if (base + i < a.emit_cap) a.emits[base + i] = s_emit[i]; else my_flags |= kFlagEmitCap;
+        }
+        __syncthreads();
+      }
+      if (tid == 0) s_misc[43] = 0;
+    };
 
-    // Flush this tile's emissions with one global atomic, then clear the tile.
-    const uint32_t ne_tile = min(s_misc[73], (uint32_t)tc.emit_cap);
-    if (ne_tile) {
-      if (tid == 0) s_misc[74] = atomicAdd(a.n_emit, ne_tile);
-      __syncthreads();
-      const uint32_t base = s_misc[74];
-      for (uint32_t i = tid; i < ne_tile; i += kNT) {
-        if (base + i < a.emit_cap) a.emits[base + i] = s_emit[i]; else my_flags |= kFlagEmitCap;
-      }
+    const int nvt_bx = min(tc.bvx, (kxb - kxa) / KX + 1);
+    const int nvt_by = min(tc.bvy, (kyb - kya) / KY + 1);
+    if (single_chunk) {
+      const uint32_t D = prepare_chunk(0);
+      const bool once = D <= (uint32_t)tc.scap;
+      const uint32_t ns_once = once ? stage(0, 0, D) : 0u;  // staged once for the whole block
+      for (int vty = 0; vty < nvt_by; ++vty)
+        for (int vtx = 0; vtx < nvt_bx; ++vtx) {
+          const int kx0 = kxa + vtx * KX, ky0 = kya + vty * KY;
+          const uint32_t act = active_mask(kx0, ky0);
+          if (act == 0) continue;
+          if (once) {
+            compute(vtx, vty, act, ns_once);
+          } else {
+            for (uint32_t p0 = 0; p0 < D; p0 += tc.scap) {
+              const uint32_t ns = stage(0, p0, min(D, p0 + (uint32_t)tc.scap));
+              compute(vtx, vty, act, ns);
+              __syncthreads();
+            }
+          }
+          finish(kx0, ky0);
+        }
+    } else {
+      for (int vty = 0; vty < nvt_by; ++vty)
+        for (int vtx = 0; vtx < nvt_bx; ++vtx) {
+          const int kx0 = kxa + vtx * KX, ky0 = kya + vty * KY;
+          const uint32_t act = active_mask(kx0, ky0);
+          if (act == 0) continue;
+          for (uint32_t e_base = 0; e_base < E; e_base += tc.ec) {
+            const uint32_t D = prepare_chunk(e_base);
+            for (uint32_t p0 = 0; p0 < D; p0 += tc.scap) {
+              const uint32_t ns = stage(e_base, p0, min(D, p0 + (uint32_t)tc.scap));
+              compute(vtx, vty, act, ns);
+              __syncthreads();
+            }
+          }
+          finish(kx0, ky0);
+        }
     }
-    for (uint32_t i = tid; i < n_words / 4; i += kNT)
-      reinterpret_cast<uint4*>(cells)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
   }
 
-  // Pair count and flags: one global atomic per warp.
+  // Pair count, balance and flags: one global atomic each per warp.
   for (int o = 16; o > 0; o >>= 1) {
-    pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    pairs64 += __shfl_xor_sync(0xffffffffu, pairs64, o);
+    balance += __shfl_xor_sync(0xffffffffu, balance, o);
     my_flags |= __shfl_xor_sync(0xffffffffu, my_flags, o);
   }
   if ((tid & 31) == 0) {
-    if (pairs) atomicAdd(a.n_pairs, (unsigned long long)pairs);
+    if (pairs64) atomicAdd(a.n_pairs, (unsigned long long)pairs64);
+    if (balance) atomicAdd(a.balance, (unsigned long long)balance);
     if (my_flags) atomicOr(a.flags, my_flags);
   }
 }
@@ -377,9 +507,9 @@ cudaError_t attr_t(size_t smem) {
 
 // Supported (KX, KY, CB) instantiations.
 #define SAS_STACK_CONFIGS(X) \
-  X(4, 1, 8) X(4, 2, 8) X(4, 4, 8) X(8, 2, 8) X(8, 3, 8) \
-  X(4, 1, 16) X(4, 2, 16) X(4, 4, 16) X(8, 2, 16) X(8, 3, 16) \
-  X(4, 1, 32) X(4, 2, 32) X(4, 4, 32) X(8, 2, 32) X(8, 3, 32)
+  X(4, 1, 8) X(4, 2, 8) X(4, 4, 8) X(8, 2, 8) X(8, 4, 8) \
+  X(4, 1, 16) X(4, 2, 16) X(4, 4, 16) X(8, 2, 16) X(8, 4, 16) \
+  X(4, 1, 32) X(4, 2, 32) X(4, 4, 32) X(8, 2, 32) X(8, 4, 32)
 
 }  // namespace
 
@@ -390,9 +520,7 @@ bool stack_config_supported(int kx, int ky, int cb) {
   return false;
 }
 
-size_t stack_smem_bytes(const TileCfg& tc) {
-  return layout(tc.kx, tc.ky, tc.tx, tc.ty, tc.cb, tc.ec, tc.seg_cap, tc.emit_cap).total;
-}
+size_t stack_smem_bytes(const TileCfg& tc) { return layout(tc).total; }
 
 int stack_threads() { return kNT; }
 

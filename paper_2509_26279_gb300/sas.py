@@ -54,8 +54,8 @@ class sas_opts(ctypes.Structure):
                 ("max_candidates", ctypes.c_uint64), ("tile_kx", ctypes.c_uint32),
                 ("tile_ky", ctypes.c_uint32), ("tile_bx", ctypes.c_uint32),
                 ("tile_by", ctypes.c_uint32), ("counter_bits", ctypes.c_uint32),
-                ("coarse_bins", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("coarse_bins", ctypes.c_uint32), ("superbin", ctypes.c_uint32),
+                ("velocity_block", ctypes.c_uint32)]
 
 
 class sas_result_info(ctypes.Structure):
@@ -64,8 +64,12 @@ class sas_result_info(ctypes.Structure):
                 ("t0", ctypes.c_int64), ("counter_bits", ctypes.c_uint32),
                 ("tile_kx", ctypes.c_uint32), ("tile_ky", ctypes.c_uint32),
                 ("tile_bx", ctypes.c_uint32), ("tile_by", ctypes.c_uint32),
+                ("superbin", ctypes.c_uint32), ("vblock_x", ctypes.c_uint32),
+                ("vblock_y", ctypes.c_uint32), ("staged_cap", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("ms_stack", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("ms_prep", ctypes.c_float),
+                ("ms_count", ctypes.c_float), ("ms_ids", ctypes.c_float),
+                ("reserved_f", ctypes.c_float)]
 
 
 # sas_candidate as a NumPy record (32 bytes, same layout as the C struct)
@@ -161,7 +165,7 @@ class Result:
     def info(self) -> dict:
         inf = sas_result_info()
         _check(_lib.sas_result_get_info(self._h, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in sas_result_info._fields_ if k != "reserved"}
+        return {k: getattr(inf, k) for k, _ in sas_result_info._fields_}
 
     def candidates(self):
         """(candidates: structured array of CANDIDATE_DTYPE, ids: uint32 array)."""

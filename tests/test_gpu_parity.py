@@ -82,10 +82,10 @@ def test_tiny_workload():
 
 @pytest.mark.parametrize("cfg", [
     dict(tile_kx=4, tile_ky=1), dict(tile_kx=4, tile_ky=2), dict(tile_kx=8, tile_ky=2),
-    dict(tile_kx=8, tile_ky=3), dict(counter_bits=16), dict(counter_bits=32),
+    dict(counter_bits=16), dict(counter_bits=32),
     dict(tile_bx=12, tile_by=8), dict(tile_bx=36, tile_by=20, coarse_bins=3),
-    dict(coarse_bins=1), dict(coarse_bins=50), dict(ctas_per_sm=1), dict(ctas_per_sm=3),
-    dict(tile_kx=8, tile_ky=3, counter_bits=16, tile_bx=20, tile_by=28),
+    dict(coarse_bins=1), dict(coarse_bins=50), dict(tile_kx=8, tile_ky=4),
+    dict(tile_kx=8, tile_ky=4, counter_bits=16, tile_bx=20, tile_by=28),
 ])
 def test_tile_configurations_agree(cfg):
     """Every tile shape, counter width and bucket size gives the same bytes."""
@@ -274,3 +274,31 @@ def test_full_decam_tno():
 def test_full_fast_movers():
     info = _full_size_check(W.fast_movers(), n_ranges=2, n_cells_sample=30, seed=2)
     assert info["n_pairs"] > 1e11
+
+
+def test_dense_catalog_multi_pass_staging():
+    """More detections in one work unit than the staging area holds: the kernel
+    stages and runs the unit in several passes per velocity tile."""
+    rng = np.random.default_rng(5)
+    E, n = 20, 60_000
+    x = rng.integers(0, 120_000, n)
+    y = rng.integers(0, 120_000, n)
+    ep = rng.integers(0, E, n)
+    cat = cases.catalog(x, y, ep, np.arange(E) * 720, 3600)
+    grid = W.GridSpec(vx0=-2000, vy0=-2000, dvx=1000, dvy=1000, nvx=5, nvy=5, x_min=0,
+                      y_min=0, nbx=60, nby=60, bin=2000)
+    res, ref = run_both(cat, grid, 30)
+    assert_same(res, ref)
+    res, ref = run_both(cat, grid, 30, opts=sas.make_opts(superbin=1, velocity_block=1))
+    assert_same(res, ref)
+
+
+@pytest.mark.parametrize("sb,vb", [(1, 1), (2, 1), (3, 2), (4, 8), (2, 3)])
+def test_superbin_and_velocity_block_agree(sb, vb):
+    w = W.scaled(W.decam_tno(), frac_noise=0.03, width_px=700, height_px=500, n_movers=40,
+                 grid_half=12, seed=21)
+    cat = W.load(w)
+    res, ref = run_both(cat, w.grid, 10, opts=sas.make_opts(superbin=sb, velocity_block=vb))
+    assert len(ref.cands) > 0
+    assert_same(res, ref)
+    assert res.info()["superbin"] == sb
