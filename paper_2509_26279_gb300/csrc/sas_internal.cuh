@@ -133,6 +133,7 @@ size_t scan_scratch_elems(uint64_t n);
 // sas_stack.cu
 bool stack_config_supported(int kx, int ky, int cb);
 size_t stack_smem_bytes(const TileCfg& tc);
+size_t stack_counter_bytes(const TileCfg& tc);
 cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s);
 cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
 

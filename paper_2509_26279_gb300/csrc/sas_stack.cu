@@ -106,11 +106,19 @@ struct Counter {
 // to the same window origin as the staged coordinates, so X = xr - ox[k] is the
 // projected position relative to the tile origin.  Returns the number of
 // (detection, velocity) pairs that landed in the tile.
+// Predicated shared-memory reduction: adds inc to the word at shared address
+// addr when pred is nonzero, without a branch.
+__device__ __forceinline__ void red_shared_if(uint32_t pred, uint32_t addr, uint32_t inc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t@p red.shared.add.u32 [%1], %2;\n\t}" ::"r"(pred),
+      "r"(addr), "r"(inc));
+}
+
 template <int KX, int KY, int CB, bool MASKED>
 __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 const int32_t* __restrict__ ox,
                                                 const int32_t* __restrict__ oy,
-                                                uint32_t* __restrict__ cells, uint32_t tw_x,
+                                                uint32_t cells_s, uint32_t tw_x,
                                                 uint32_t tw_y, uint32_t magic, bool one, int tx,
                                                 int txty, uint32_t act) {
   using C = Counter<CB>;
@@ -135,19 +143,19 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
 #pragma unroll
     for (int k = 0; k < KY; ++k) oyv[k] = oy[k];
   }
-  uint32_t col[KX], okxb = 0;
+  uint32_t col4[KX], okxb = 0;  // byte offset of the counter word in its row
 #pragma unroll
   for (int k = 0; k < KX; ++k) {
     const uint32_t X = xr - (uint32_t)oxv[k];
     okxb |= (uint32_t)(X < tw_x) << k;
-    col[k] = one ? X : __umulhi(X, magic);
+    col4[k] = (one ? X : __umulhi(X, magic)) * 4u;
   }
-  uint32_t rbase[KY], okyb = 0;
+  uint32_t rbase4[KY], okyb = 0;  // shared address of the counter row
 #pragma unroll
   for (int k = 0; k < KY; ++k) {
     const uint32_t Y = yr - (uint32_t)oyv[k];
     okyb |= (uint32_t)(Y < tw_y) << k;
-    rbase[k] = (one ? Y : __umulhi(Y, magic)) * (uint32_t)tx;
+    rbase4[k] = cells_s + (one ? Y : __umulhi(Y, magic)) * (uint32_t)(4 * tx);
   }
   uint32_t m = 0;
 #pragma unroll
@@ -158,10 +166,8 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
   for (int ky = 0; ky < KY; ++ky) {
 #pragma unroll
     for (int kx = 0; kx < KX; ++kx) {
-      if ((m >> (ky * KX + kx)) & 1u) {
-        const uint32_t widx = (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty) + rbase[ky] + col[kx];
-        atomicAdd(&cells[widx], 1u << (CB * (kx % C::P)));  // old value unused: a reduction
-      }
+      const uint32_t addr = rbase4[ky] + col4[kx] + (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty * 4);
+      red_shared_if(m & (1u << (ky * KX + kx)), addr, 1u << (CB * (kx % C::P)));
     }
   }
   return (uint32_t)__popc(m);
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
   const TileCfg& tc = a.tc;
   const SmemLayout L = layout(tc);
   uint32_t* cells = reinterpret_cast<uint32_t*>(smem + L.cells);
+  const uint32_t cells_s = (uint32_t)__cvta_generic_to_shared(cells);
   uint2* staged = reinterpret_cast<uint2*>(smem + L.staged);
   int32_t* s_ox = reinterpret_cast<int32_t*>(smem + L.ox);
   int32_t* s_oy = reinterpret_cast<int32_t*>(smem + L.oy);
@@ -304,13 +311,14 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
       return total;
     };
 
-    // --- stage detections [p0, p1) of the chunk, keeping those in the window --
+    // --- stage detections [p0, p1) of the chunk that lie in the window, in
+    //     bucket order (records of one epoch stay together, so the shift-table
+    //     loads of a warp are broadcasts) ----------------------------------------
     auto stage = [&](uint32_t e_base, uint32_t p0, uint32_t p1) -> uint32_t {
-      if (tid == 0) s_misc[45] = 0;
-      __syncthreads();
+      uint32_t n_kept = 0;
       for (uint32_t j0 = p0; j0 < p1; j0 += kNT) {
         const uint32_t j = j0 + tid;
-        bool keep = false;
+        uint32_t keep = 0;
         uint2 rec = make_uint2(0, 0);
         if (j < p1) {
           uint32_t lo = 0, hi = kNT;
@@ -325,16 +333,13 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
           keep = xr < (uint32_t)s_win[el * 4 + 1] && yr < (uint32_t)s_win[el * 4 + 3];
           rec = make_uint2(xr | ((uint32_t)el << 24), yr);
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, keep);
-        uint32_t base = 0;
-        if ((tid & 31) == 0 && m) base = atomicAdd(&s_misc[45], (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) staged[base + __popc(m & ((1u << (tid & 31)) - 1u))] = rec;
+        uint32_t total;
+        const uint32_t pos = block_scan(keep, s_misc, total);
+        if (keep) staged[n_kept + pos] = rec;
+        n_kept += total;
       }
       __syncthreads();
-      const uint32_t ns = s_misc[45];
-      __syncthreads();
-      return ns;
+      return n_kept;
     };
 
     // --- which lattice points of a velocity tile are searched ----------------
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
           const uint2 r = staged[j];
           const int el = (int)(r.x >> 24);
           pairs += process_rec<KX, KY, CB, false>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
-                                                  s_oy + el * byk + oyo, cells, tw_x, tw_y,
+                                                  s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
                                                   a.magic, a.bin_is_one, tc.tx, txty, act);
         }
       } else {
@@ -381,12 +386,13 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
           const uint2 r = staged[j];
           const int el = (int)(r.x >> 24);
           pairs += process_rec<KX, KY, CB, true>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
-                                                 s_oy + el * byk + oyo, cells, tw_x, tw_y,
+                                                 s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
                                                  a.magic, a.bin_is_one, tc.tx, txty, act);
         }
       }
       pairs64 += pairs;
       balance -= pairs;
+      __syncthreads();  // the reductions above are asm: order them before any reader
     };
 
     // --- read every counter of the tile: emit those at or over n_min, add up
@@ -521,6 +527,8 @@ bool stack_config_supported(int kx, int ky, int cb) {
 }
 
 size_t stack_smem_bytes(const TileCfg& tc) { return layout(tc).total; }
+
+size_t stack_counter_bytes(const TileCfg& tc) { return layout(tc).staged - layout(tc).cells; }
 
 int stack_threads() { return kNT; }
 
