@@ -192,6 +192,38 @@ int sas_candidates(const sas_result* result, sas_candidate* out, uint64_t cap,
 
 void sas_result_free(sas_result* result);
 
+/* Exact counts of chosen cells without allocating device memory.
+ *
+ * The paper has no counterpart; this is a service for callers that cannot
+ * allocate device memory while they run -- a process that has handed all of
+ * its device memory to its own pool under a fixed budget, or code issuing work
+ * from a loop that must never wait on the CUDA allocator.  For each cell
+ * (v_idx, bx, by) it returns the same numbers as the exact-count step of
+ * sas_stack: distinct[i] = number of distinct epochs and raw[i] = number of
+ * detections of the catalog that project into the cell (Sec. 2.1 steps 1-2,
+ * reference epoch t0 = earliest detection time).
+ *
+ * cells: device array of n_cells triples (v_idx, bx, by) as uint32.
+ * distinct, raw: device arrays of n_cells uint32, owned by the caller.
+ * cat: x, y and epoch must be device arrays (on_device = 1); t is host memory.
+ * The call writes only distinct and raw; it allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call).  Its working state (epoch times and
+ * flags) lives in one fixed 16 KiB array inside the library, which every GPU
+ * that loads the library holds until the process exits; so n_epochs may not
+ * exceed 1024 (SAS_ERR_RANGE otherwise).  The first call on a device looks up
+ * that array's device address, so make it before capturing a stream into a
+ * graph.  All calls on a device share the array: calls whose GPU work overlaps
+ * (other streams, other host threads) race, and must be serialized by the
+ * caller.  Each call resets the parts that must start at zero.  The call
+ * synchronizes the stream.  Counting is exact in 64-bit arithmetic; the cost is
+ * O(n_cells * n) (it scans the whole catalog per cell), meant for modest
+ * numbers of cells.
+ * Errors: SAS_ERR_ARG (nulls, host catalog, a cell outside the lattice or the
+ * domain: its outputs are set to 0xffffffff), SAS_ERR_RANGE (n_epochs, an epoch
+ * index >= n_epochs, |x| or |y| >= 2^29), SAS_ERR_CUDA. */
+int sas_cell_counts_noalloc(const sas_grid* grid, const sas_catalog* cat, const uint32_t* cells,
+                            uint64_t n_cells, uint32_t* distinct, uint32_t* raw, void* stream);
+
 /* Measurement utility: throughput of conflict-free 32-bit shared-memory
  * atomicAdd on every SM of the current device, in operations per second,
  * measured with CUDA events over `iters` operations per thread; this is the

@@ -720,6 +720,15 @@ void sas_result_free(sas_result* r) {
   delete r;
 }
 
+int sas_cell_counts_noalloc(const sas_grid* grid, const sas_catalog* cat, const uint32_t* cells,
+                            uint64_t n_cells, uint32_t* distinct, uint32_t* raw, void* stream) {
+  if (!grid || !cat) return fail(SAS_ERR_ARG, "null argument");
+  std::string err;
+  const int rc = noalloc_cell_counts(grid->d, cat, cells, n_cells, distinct, raw, stream, &err);
+  if (rc != SAS_OK) return fail(rc, "%s", err.c_str());
+  return SAS_OK;
+}
+
 int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s, double* sm_mhz) {
   if (!ops_per_s || !sm_mhz || iters == 0) return fail(SAS_ERR_ARG, "bad argument");
   cudaError_t e = run_atomic_probe(iters, (cudaStream_t)stream, ops_per_s, sm_mhz);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <string>
 
 #include "../../include/sas.h"
 
@@ -157,6 +158,11 @@ cudaError_t launch_write_candidates(const Key* keys, uint32_t n, const unsigned 
 
 // sas_probe.cu
 cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
+
+// sas_noalloc.cu (returns a sas_status; *err gets the message on failure)
+int noalloc_cell_counts(const sas_grid_desc& d, const sas_catalog* cat, const uint32_t* cells,
+                        uint64_t n_cells, uint32_t* distinct, uint32_t* raw, void* stream,
+                        std::string* err);
 
 // ---- small device helpers ---------------------------------------------------
 

@@ -94,10 +94,12 @@ _lib.sas_result_free.argtypes = [_p]
 _lib.sas_result_free.restype = None
 _lib.sas_probe_shared_atomic_peak.argtypes = [ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_double)]
+_lib.sas_cell_counts_noalloc.argtypes = [_p, ctypes.POINTER(sas_catalog), _p, ctypes.c_uint64, _p, _p,
+                                         _p]
 
 EXPORTED = ["sas_version", "sas_abi_version", "sas_kernel_launches", "sas_last_error", "sas_create_grid",
             "sas_destroy_grid", "sas_stack", "sas_result_get_info", "sas_candidates",
-            "sas_result_free", "sas_probe_shared_atomic_peak"]
+            "sas_result_free", "sas_probe_shared_atomic_peak", "sas_cell_counts_noalloc"]
 
 
 def _check(status: int):
@@ -235,6 +237,21 @@ def sas_stack(grid: Grid, x, y, epoch, t, ticks_per_hour: int, n_min: int, *,
 def stack_catalog(grid: Grid, cat, n_min: int, **kw) -> Result:
     """sas_stack on a workloads.Catalog held in host memory."""
     return sas_stack(grid, cat.x, cat.y, cat.epoch, cat.t, cat.ticks_per_hour, n_min, **kw)
+
+
+def sas_cell_counts_noalloc(grid: Grid, x, y, epoch, t, ticks_per_hour: int, cells, n_cells: int,
+                            distinct, raw, stream=None) -> None:
+    """Exact (distinct, raw) counts of n_cells cells without any device
+    allocation by the library.  x, y, epoch, cells (n_cells x 3 uint32:
+    v_idx, bx, by), distinct and raw are device arrays owned by the caller."""
+    t = np.ascontiguousarray(t, np.int64)
+    n = int(x.numel() if hasattr(x, "numel") else len(x))
+    cat = sas_catalog(n=n, x=_dev_ptr(x), y=_dev_ptr(y), epoch=_dev_ptr(epoch),
+                      n_epochs=int(t.shape[0]), t=t.ctypes.data,
+                      ticks_per_hour=int(ticks_per_hour), on_device=1)
+    _check(_lib.sas_cell_counts_noalloc(grid.handle, ctypes.byref(cat), _dev_ptr(cells),
+                                        int(n_cells), _dev_ptr(distinct), _dev_ptr(raw),
+                                        _stream_handle(stream)))
 
 
 def sas_probe_shared_atomic_peak(iters: int = 4096, stream=None):
