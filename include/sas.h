@@ -167,6 +167,7 @@ const char* sas_last_error(void);
  * SAS_ERR_RANGE (limits above).  *out is untouched on error. */
 int sas_create_grid(const sas_grid_desc* desc, sas_grid** out);
 void sas_destroy_grid(sas_grid* grid);
+int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc);
 
 /* Run the search (Sec. 2.1 steps 1-3) on the current CUDA device.
  * grid, cat: see above.  n_min >= 1.  opts may be NULL.  stream: a
@@ -191,6 +192,48 @@ int sas_candidates(const sas_result* result, sas_candidate* out, uint64_t cap,
                    uint64_t* n_ids_total, int on_device);
 
 void sas_result_free(sas_result* result);
+
+/* ---- Batched search: many fields in one graph-captured pass ---------------
+ *
+ * Many fields (CCDs) with uneven detection and epoch counts are searched by
+ * one pass of every kernel -- one persistent stack launch over the work units
+ * of all fields -- recorded once as a CUDA graph by sas_batch_create and
+ * replayed by sas_batch_run.  (The paper searches each CCD independently,
+ * Sec. 3.3; batching is an implementation pattern with the same results.)
+ *
+ * grids[f], cats[f], n_min[f]: field f (catalogs in device memory, on_device
+ * = 1, n >= 1; 1 <= n_min <= 128).  opts: NULL or an array of n_fields option
+ * sets (tile_kx and tile_ky must agree across fields; v_begin/v_end and
+ * counter_bits are ignored).  The batch keeps the catalogs' device pointers:
+ * the caller may rewrite their contents between runs (same sizes, same
+ * epoch times) and must keep them alive until sas_batch_destroy.
+ * sas_batch_run replays the pass on `stream` and synchronizes; a field that
+ * exceeded the batch's fixed capacities (emissions, 8192 candidates, ids) or
+ * whose counters wrapped is recomputed by sas_stack, so every field's result
+ * equals sas_stack's.  Results stay valid until the next run.
+ * Errors: as sas_stack; SAS_ERR_ARG for fields that cannot share a launch. */
+typedef struct sas_batch sas_batch;
+int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, const uint32_t* n_min,
+                     uint32_t n_fields, const sas_opts* opts, void* stream, sas_batch** out);
+int sas_batch_run(sas_batch* batch, void* stream);
+int sas_batch_field_info(const sas_batch* batch, uint32_t field, sas_result_info* info);
+int sas_batch_candidates(const sas_batch* batch, uint32_t field, sas_candidate* out,
+                         uint64_t cap, uint64_t* n_total, uint32_t* ids, uint64_t ids_cap,
+                         uint64_t* n_ids_total, int on_device);
+/* Device time (ms, CUDA events) of the last replayed pass and the number of
+ * field fallbacks so far. */
+int sas_batch_stats(const sas_batch* batch, float* ms_last, uint64_t* fallbacks);
+void sas_batch_destroy(sas_batch* batch);
+
+/* Autotuner: times sas_stack on (grid, cat, n_min) for each candidate pair of
+ * superbin in {1, 2, 3} and velocity_block in {1, 2, 4, 8} (other fields of
+ * *base kept; tile sizes chosen by the planner), `reps` timed runs each after
+ * one warm-up, and returns in *best the options with the lowest median device
+ * time of the whole search (*best_ms).  Every candidate gives the same
+ * candidates; only the speed differs. */
+int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
+                 const sas_opts* base, uint32_t reps, void* stream, sas_opts* best,
+                 float* best_ms);
 
 /* Exact counts of chosen cells without allocating device memory.
  *

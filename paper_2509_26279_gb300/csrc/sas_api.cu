@@ -30,16 +30,15 @@ struct sas_result {
   sas_result_info info;
 };
 
+namespace {
+thread_local std::string g_err;
+}  // namespace
+
 namespace sas {
 std::atomic<unsigned long long> g_launches{0};
 void note_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
-}  // namespace sas
 
-namespace {
-
-thread_local std::string g_err;
-
-int fail(int code, const char* fmt, ...) {
+int set_errorf(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -48,42 +47,18 @@ int fail(int code, const char* fmt, ...) {
   g_err = buf;
   return code;
 }
+}  // namespace sas
+
+namespace {
+
+template <typename... Args>
+int fail(int code, const char* fmt, Args... args) {
+  return set_errorf(code, fmt, args...);
+}
 
 int cuda_fail(cudaError_t e, const char* where) {
   return fail(e == cudaErrorMemoryAllocation ? SAS_ERR_OOM : SAS_ERR_CUDA, "%s: %s", where,
               cudaGetErrorString(e));
-}
-
-struct DevInfo {
-  int sms = 0;
-  int smem_optin = 0;
-  int smem_per_sm = 0;
-  bool ready = false;
-};
-
-std::mutex g_dev_mu;
-DevInfo g_dev[64];
-
-int device_info(int dev, DevInfo* out) {
-  std::lock_guard<std::mutex> lk(g_dev_mu);
-  if (dev < 0 || dev >= 64) return fail(SAS_ERR_ARG, "device ordinal %d out of range", dev);
-  DevInfo& d = g_dev[dev];
-  if (!d.ready) {
-    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    // Keep freed stream-ordered allocations cached in the pool between calls.
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t thr = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "device query");
-    d.ready = true;
-  }
-  *out = d;
-  return SAS_OK;
 }
 
 // Stream-ordered scratch, released when the search returns.
@@ -120,188 +95,6 @@ struct Tracer {
   }
 };
 
-uint32_t magic_for(int32_t bin) {  // ceil(2^32 / bin) for bin >= 2
-  return (uint32_t)(((uint64_t)1 << 32) / (uint64_t)bin + 1);
-}
-
-// (X_max) * (magic * bin - 2^32) < 2^32 makes umulhi(X, magic) == X / bin for X <= X_max.
-bool magic_exact(int32_t bin, int64_t x_max) {
-  if (bin == 1) return true;
-  const uint64_t m = magic_for(bin);
-  const uint64_t err = m * (uint64_t)bin - ((uint64_t)1 << 32);
-  return (unsigned __int128)x_max * err < ((unsigned __int128)1 << 32);
-}
-
-constexpr int kStackThreads = 1024;
-constexpr int kSegCap = kStackThreads;  // one (epoch, bucket row) segment per thread
-constexpr int kEmitCap = 256;
-constexpr int kMaxEpochChunk = 256;     // staged records carry the epoch in 8 bits
-
-struct Plan {
-  TileCfg tc;
-  CoarseGeom cg;
-  int ky_lo, ky_hi;
-};
-
-// Upper bound of |floor(v*dt/TPH) - floor(v'*dt/TPH)| over dt in [0, dT] for
-// |v - v'| <= dv_span.
-int64_t spread_bound(int64_t dv_span, int64_t dT, int64_t tph) {
-  const long double s = (long double)dv_span * (long double)dT / (long double)tph + 2.0L;
-  return s > (long double)kLimDomain ? kLimDomain : (int64_t)s;
-}
-
-// log P(Poisson(lam) >= k), summed in log space.
-double log_poisson_tail(double lam, int k) {
-  if (k <= 0) return 0.0;
-  if (lam <= 0) return -1e300;
-  double lt = -lam + k * std::log(lam) - std::lgamma(k + 1.0), acc = lt, term = lt;
-  for (int i = k + 1; i < k + 200; ++i) {
-    term += std::log(lam) - std::log((double)i);
-    acc = std::max(acc, term) + std::log1p(std::exp(-std::fabs(acc - term)));
-    if (term < acc - 40) break;
-  }
-  return acc;
-}
-
-// Super-bin size: the largest s in 1..3 for which uniform noise of the
-// catalog's mean density is expected to push few super-bins over n_min across
-// the searched lattice -- at most max(4000, pairs / 1e5), each emission costing
-// one exact recount.  Larger super-bins mean fewer counters to reset per
-// detection-shift but more cells near true movers reach the threshold; measured
-// on the DECam-like fields, s = 3 balances the two and s = 4 does not pay.
-int choose_superbin(const sas_grid_desc& d, uint64_t n, uint32_t n_min, uint64_t nv) {
-  if (n_min < 2) return 1;
-  const double bins = (double)d.nbx * d.nby;
-  const double lam_bin = (double)n / bins;  // detections per bin over all epochs
-  const double pairs = (double)n * (double)nv;  // upper bound of detection-shifts
-  const double budget = std::max(4000.0, pairs / 1e5);
-  int best = 1;
-  for (int s = 2; s <= 3; ++s) {
-    if ((int64_t)s * d.bin >= kLimDomain / 4) break;
-    const double cells = (double)nv * bins / (s * s);
-    const double lt = log_poisson_tail(lam_bin * s * s, (int)n_min);
-    if (std::log(cells) + lt < std::log(budget)) best = s;
-  }
-  return best;
-}
-
-int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int64_t tph, int kx,
-                 int ky, int cb, int sb, const sas_opts& o, const DevInfo& di, int n_rows,
-                 const CoarseGeom* fixed_cg, Plan* p) {
-  if (!stack_config_supported(kx, ky, cb))
-    return fail(SAS_ERR_ARG, "unsupported tile (kx=%d, ky=%d, counter_bits=%d)", kx, ky, cb);
-  TileCfg tc{};
-  tc.kx = kx;
-  tc.ky = ky;
-  tc.cb = cb;
-  tc.s = sb;
-  tc.nt = kStackThreads;
-  tc.seg_cap = kSegCap;
-  tc.emit_cap = kEmitCap;
-  const int64_t budget = di.smem_optin;
-  const int64_t sbin = (int64_t)sb * d.bin;
-  // velocity block: keep the union window within ~15% of the tile per axis
-  const int64_t step_x = spread_bound(std::llabs((int64_t)d.dvx), dT, tph) - 1;
-  const int64_t step_y = spread_bound(std::llabs((int64_t)d.dvy), dT, tph) - 1;
-  const double lam1 = (double)n / ((double)E * d.nbx * d.nby);  // per bin per epoch
-  // The shifts of one velocity tile may spread by at most 2^23 mpx over the
-  // time span, so that staged coordinates fit their 24-bit field.
-  if (spread_bound((int64_t)(kx - 1) * std::llabs((int64_t)d.dvx), dT, tph) >= (1 << 23) ||
-      spread_bound((int64_t)(ky - 1) * std::llabs((int64_t)d.dvy), dT, tph) >= (1 << 23))
-    return fail(SAS_ERR_RANGE, "lattice step x time span too large (shift spread >= 2^23 mpx)");
-  double cells_frac = 0.62;
-  int bv_cap = 8;
-  for (int iter = 0; iter < 200; ++iter) {
-    const int64_t cells_bytes = (int64_t)(budget * cells_frac);
-    int side = (int)std::sqrt((double)cells_bytes * 8.0 / ((double)kx * ky * cb));
-    side = std::max(4, side & ~3);
-    const int dom_x = (int)(((int64_t)d.nbx + sb - 1) / sb + 3) & ~3;
-    const int dom_y = (int)(((int64_t)d.nby + sb - 1) / sb + 3) & ~3;
-    tc.tx = o.tile_bx ? (int)o.tile_bx : std::min(side, dom_x);
-    tc.ty = o.tile_by ? (int)o.tile_by : std::min(side, dom_y);
-    if (!o.tile_bx && tc.ty < side)
-      tc.tx = std::min((int)(cells_bytes * 8 / ((int64_t)kx * ky * cb * tc.ty)) & ~3, dom_x);
-    if (!o.tile_by && tc.tx < side && tc.ty == side)
-      tc.ty = std::min((int)(cells_bytes * 8 / ((int64_t)kx * ky * cb * tc.tx)) & ~3, dom_y);
-    tc.tx = std::max(tc.tx, 4);
-    tc.ty = std::max(tc.ty, 4);
-    if (((int64_t)tc.tx * tc.ty) % 4 != 0)
-      return fail(SAS_ERR_ARG, "tile_bx * tile_by must be a multiple of 4");
-    const int64_t tw = (int64_t)tc.tx * sbin, th = (int64_t)tc.ty * sbin;
-    int bvx = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (tw * 15 / 100) / std::max<int64_t>(1, step_x * kx)));
-    int bvy = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (th * 15 / 100) / std::max<int64_t>(1, step_y * ky)));
-    if (o.velocity_block) bvx = bvy = (int)std::min<uint32_t>(o.velocity_block, 8);
-    // enough work units to fill the GPU: shrink the velocity block, then the tile
-    const uint64_t units = (uint64_t)div_ceil_u32(d.nvx, kx * bvx) * div_ceil_u32(n_rows, ky * bvy) *
-                           div_ceil_u32(d.nbx, tc.tx * sb) * div_ceil_u32(d.nby, tc.ty * sb);
-    if (units < 2ull * di.sms && !o.velocity_block && std::max(bvx, bvy) > 1) {
-      bv_cap = std::max(bvx, bvy) / 2;
-      continue;
-    }
-    if (units < 2ull * di.sms && !(o.tile_bx || o.tile_by) && std::min(tc.tx, tc.ty) > 16) {
-      cells_frac *= 0.7;
-      continue;
-    }
-    tc.bvx = bvx;
-    tc.bvy = bvy;
-    const int64_t spread_x = spread_bound((int64_t)(bvx * kx - 1) * std::llabs((int64_t)d.dvx), dT, tph);
-    const int64_t spread_y = spread_bound((int64_t)(bvy * ky - 1) * std::llabs((int64_t)d.dvy), dT, tph);
-    if (tw + spread_x >= (1 << 24) || th + spread_y >= ((int64_t)1 << 30)) {
-      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_ARG, "tile too wide for staged records");
-      cells_frac *= 0.8;
-      continue;
-    }
-    if (!magic_exact((int32_t)std::min<int64_t>(sbin, INT32_MAX), std::max(tw, th) - 1)) {
-      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_RANGE, "tile too large for exact division");
-      cells_frac *= 0.8;
-      continue;
-    }
-    // coarse bucket cell and rows per epoch window
-    CoarseGeom cg{};
-    if (fixed_cg) {
-      cg = *fixed_cg;
-    } else {
-      int64_t cell = o.coarse_bins > 0 ? (int64_t)o.coarse_bins * d.bin : (th + spread_y + 5) / 6;
-      cg.cell = (int32_t)std::max<int64_t>(1, std::min<int64_t>(cell, kLimDomain));
-    }
-    const int64_t rows = (th + spread_y) / cg.cell + 2;
-    if (rows > kSegCap) {
-      if (fixed_cg) return fail(SAS_ERR_INTERNAL, "segment rows exceed capacity");
-      return fail(SAS_ERR_ARG, "coarse_bins too small for this tile (%lld rows)", (long long)rows);
-    }
-    tc.rows = (int)rows;
-    tc.ec = (int)std::min<int64_t>(std::min<int64_t>(E, kMaxEpochChunk), kSegCap / rows);
-    if (tc.ec < 1) tc.ec = 1;
-    // staged records: what the union window holds on average, with headroom
-    const double win = (double)(tw + spread_x) / d.bin * (double)(th + spread_y) / d.bin;
-    const double est = lam1 * std::min<uint32_t>(E, tc.ec) * win;
-    tc.scap = 0;
-    const int64_t rest = budget - (int64_t)stack_smem_bytes(tc);
-    const int64_t want = (int64_t)(1.5 * est) + 1024;
-    if (rest < 8 * 256) {
-      if (o.tile_bx || o.tile_by) return fail(SAS_ERR_ARG, "tile does not fit in shared memory");
-      cells_frac *= 0.9;
-      continue;
-    }
-    if (rest / 8 < want && cells_frac > 0.15 && !(o.tile_bx || o.tile_by)) {
-      cells_frac *= 0.93;  // give the staging area more room
-      continue;
-    }
-    tc.scap = (int)std::min<int64_t>(rest / 8, std::max<int64_t>(want, 4096));
-    tc.smem = stack_smem_bytes(tc);
-    if ((int64_t)tc.smem > budget) {
-      cells_frac *= 0.95;
-      continue;
-    }
-    p->tc = tc;
-    p->cg = cg;
-    return SAS_OK;
-  }
-  return fail(SAS_ERR_INTERNAL, "could not size the stack tile");
-}
-
-int64_t ceil_div64(int64_t a, int64_t b) { return -floor_div64(-a, b); }
-
 }  // namespace
 
 extern "C" {
@@ -337,6 +130,12 @@ int sas_create_grid(const sas_grid_desc* desc, sas_grid** out) {
 
 void sas_destroy_grid(sas_grid* grid) { delete grid; }
 
+int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc) {
+  if (!grid || !desc) return fail(SAS_ERR_ARG, "null argument");
+  *desc = grid->d;
+  return SAS_OK;
+}
+
 int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* opts,
               void* stream, sas_result** out) {
   if (!grid || !cat || !out) return fail(SAS_ERR_ARG, "null argument");
@@ -362,7 +161,6 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     tmax = std::max(tmax, cat->t[e]);
   }
   if ((__int128)tmax - tmin >= ((__int128)1 << 32)) return fail(SAS_ERR_RANGE, "time span must be < 2^32 ticks");
-  const int64_t dT = tmax - tmin;
   const int64_t tph = cat->ticks_per_hour;
 
   int dev = 0;
@@ -371,19 +169,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   DevInfo di;
   if (int rc = device_info(dev, &di)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-
-  // A CB-bit counter holds thresholds up to 2^(CB-1) (it starts at 2^(CB-1) - n_min).
   if (n_min > (1u << 31)) return fail(SAS_ERR_ARG, "n_min must be <= 2^31");
-  int cb = (int)o.counter_bits;
-  if (cb == 0) cb = n_min <= 128 ? 8 : (n_min <= 32768 ? 16 : 32);
-  if (cb != 8 && cb != 16 && cb != 32) return fail(SAS_ERR_ARG, "counter_bits must be 8, 16 or 32");
-  if (cb == 8 && n_min > 128) cb = 16;
-  if (cb == 16 && n_min > 32768) cb = 32;
-  const int kx = o.tile_kx ? (int)o.tile_kx : 8;
-  const int ky = o.tile_ky ? (int)o.tile_ky : 4;
-  if (o.superbin > 4) return fail(SAS_ERR_ARG, "superbin must be 0..4");
-  const uint64_t nv_search = v_end - v_begin;
-  const int sb = o.superbin ? (int)o.superbin : choose_superbin(d, n, n_min, nv_search);
 
   sas_result* res = new (std::nothrow) sas_result;
   if (!res) return fail(SAS_ERR_OOM, "host allocation");
@@ -396,50 +182,15 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     return SAS_OK;
   }
 
-  Plan plan;
-  const int n_rows = (int)((v_end - 1) / d.nvx - v_begin / d.nvx + 1);
-  if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, nullptr, &plan)) {
+  FieldPlan plan;
+  if (int rc = plan_field(d, n, E, cat->t, tph, n_min, v_begin, v_end, o, di, &plan)) {
     delete res;
     return rc;
   }
-  // Bucket grid: every detection that can project into the domain for some
-  // lattice velocity and some dt in [0, dT] lies inside it.
-  const int64_t vxa = d.vx0, vxb = (int64_t)d.vx0 + (int64_t)(d.nvx - 1) * d.dvx;
-  const int64_t vya = d.vy0, vyb = (int64_t)d.vy0 + (int64_t)(d.nvy - 1) * d.dvy;
-  auto clampd = [](int64_t v) { return std::max(-kLimDomain, std::min(kLimDomain, v)); };
-  const int64_t sx_lo = clampd(floor_div64(std::min<int64_t>(std::min(vxa, vxb), 0) * dT, tph));
-  const int64_t sx_hi = clampd(ceil_div64(std::max<int64_t>(std::max(vxa, vxb), 0) * dT, tph));
-  const int64_t sy_lo = clampd(floor_div64(std::min<int64_t>(std::min(vya, vyb), 0) * dT, tph));
-  const int64_t sy_hi = clampd(ceil_div64(std::max<int64_t>(std::max(vya, vyb), 0) * dT, tph));
-  CoarseGeom& cg = plan.cg;
-  for (;;) {
-    cg.gx0 = (int32_t)(d.x_min + sx_lo);
-    cg.gy0 = (int32_t)(d.y_min + sy_lo);
-    cg.ncx = (int32_t)ceil_div64((int64_t)d.nbx * d.bin + (sx_hi - sx_lo) + 1, cg.cell);
-    cg.ncy = (int32_t)ceil_div64((int64_t)d.nby * d.bin + (sy_hi - sy_lo) + 1, cg.cell);
-    if ((uint64_t)E * cg.ncx * cg.ncy <= ((uint64_t)1 << 27)) break;
-    if (cg.cell >= kLimDomain / 2) break;
-    cg.cell *= 2;  // fewer, larger buckets
-  }
-  {  // the bucket cell may have grown: recompute the per-chunk epoch count
-    Plan p2;
-    if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, &cg, &p2)) {
-      delete res;
-      return rc;
-    }
-    plan.tc = p2.tc;
-  }
-  const uint64_t nb = (uint64_t)E * cg.ncx * cg.ncy;
+  const CoarseGeom& cg = plan.cg;
+  const uint64_t nb = plan.nb;
+  const SearchGeom& g = plan.g;
   tr.mark("planned");
-
-  SearchGeom g{};
-  g.vx0 = d.vx0; g.vy0 = d.vy0; g.dvx = d.dvx; g.dvy = d.dvy;
-  g.nvx = (int32_t)d.nvx; g.nvy = (int32_t)d.nvy;
-  g.smin = d.speed_min; g.smax = d.speed_max;
-  g.x_min = d.x_min; g.y_min = d.y_min;
-  g.nbx = (int32_t)d.nbx; g.nby = (int32_t)d.nby; g.bin = d.bin;
-  g.E = E; g.tph = tph;
-  g.v_begin = v_begin; g.v_end = v_end;
 
   cudaEvent_t ev0, ev1, evs0, evs1, evc0, evc1;
   cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&evs0); cudaEventCreate(&evs1);
@@ -533,22 +284,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       const TileCfg& tc = plan.tc;
       CK(sc.alloc(&d_emits, emit_cap), "alloc emissions");
       CK(stack_set_smem_attr(tc.kx, tc.ky, tc.cb, tc.smem), "smem attribute");
-      sa.g = g;
-      sa.cg = cg;
-      sa.tc = tc;
-      const int64_t sbin = (int64_t)tc.s * d.bin;
-      sa.magic = sbin >= 2 ? magic_for((int32_t)sbin) : 0u;
-      sa.bin_is_one = sbin == 1;
-      sa.n_min = n_min;
-      plan.ky_lo = (int)(v_begin / d.nvx);
-      plan.ky_hi = (int)((v_end - 1) / d.nvx);
-      sa.kx_lo = 0;
-      sa.ky_lo = plan.ky_lo;
-      sa.nvt_x = (int)div_ceil_u32(d.nvx, tc.kx * tc.bvx);
-      sa.nvt_y = (int)div_ceil_u32((uint32_t)(plan.ky_hi - plan.ky_lo + 1), tc.ky * tc.bvy);
-      sa.nst_x = (int)div_ceil_u32(d.nbx, tc.tx * tc.s);
-      sa.nst_y = (int)div_ceil_u32(d.nby, tc.ty * tc.s);
-      sa.n_tiles = (uint64_t)sa.nvt_x * sa.nvt_y * sa.nst_x * sa.nst_y;
+      fill_stack_args(plan, n_min, &sa);
       sa.dets = d_dets;
       sa.boff = d_boff;
       sa.ecount = d_ecount;
@@ -581,12 +317,8 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "stack kernel invariant"); goto done; }
       if (attempt >= 4) { rc = fail(SAS_ERR_INTERNAL, "stack kernel did not converge"); goto done; }
       if ((h_small[0] & kFlagCounter) || h_small64[3] != 0) {  // a counter wrapped
-        if (plan.tc.cb == 32) { rc = fail(SAS_ERR_INTERNAL, "32-bit counter wrapped"); goto done; }
         CK(cudaMemsetAsync(&d_small[0], 0, 4, s), "memset");
-        const int wider = plan.tc.cb * 2;
-        Plan p2;
-        if (int r2 = choose_tiles(d, E, n, dT, tph, kx, ky, wider, sb, o, di, n_rows, &cg, &p2)) { rc = r2; goto done; }
-        plan.tc = p2.tc;
+        if (int r2 = replan_wider(d, n, n_min, o, di, &plan)) { rc = r2; goto done; }
         continue;
       }
       if (h_small[1] > emit_cap || (h_small[0] & kFlagEmitCap)) {

@@ -1,0 +1,460 @@
+// Batched search: many fields (CCDs) with uneven detection and epoch counts in
+// one pass of every kernel -- one persistent stack launch over the work units of
+// all fields -- recorded once as a CUDA graph and replayed.
+//
+// sas_batch_create plans every field (tile shape from its own opts, e.g. the
+// autotuner's pick for its size class), lays out one device arena for all of
+// them with fixed capacities, and captures the whole device pipeline into a
+// graph.  sas_batch_run replays the graph; a field whose capacities were not
+// enough, or whose counters wrapped, is recomputed exactly on the single-field
+// path, so the results always equal sas_stack's.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sas_batch.cuh"
+
+using namespace sas;
+
+struct sas_batch {
+  int device = 0;
+  uint32_t n_fields = 0;
+  std::vector<sas_grid*> grids;            // private copies (own descriptors)
+  std::vector<sas_catalog> cats;
+  std::vector<std::vector<int64_t>> times;
+  std::vector<uint32_t> n_min;
+  std::vector<sas_opts> opts;
+  std::vector<FieldPlan> plans;
+  std::vector<BatchField> hf;              // host copy of the field descriptors
+  std::vector<uint32_t> key_cap;
+  std::vector<uint64_t> ids_cap;
+  BatchDev dev{};
+  void* arena = nullptr;
+  uint32_t* h_ctr = nullptr;               // pinned [n_fields][kCtrN]
+  unsigned long long* h_c64 = nullptr;     // pinned [n_fields][kC64N]
+  uint32_t* d_ctr = nullptr;
+  unsigned long long* d_c64 = nullptr;
+  unsigned long long* d_work = nullptr;
+  StackArgs* d_args = nullptr;
+  unsigned long long* d_unit_base = nullptr;
+  uint32_t* d_ecount_all = nullptr;
+  size_t ecount_words = 0;
+  int kx = 0, ky = 0, cb = 0;
+  size_t stack_smem = 0;
+  int stack_grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<sas_result*> fallback;       // per field, after a run that needed it
+  float ms_last = 0.f;
+  uint64_t fallback_count = 0;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e, const char* where) {
+  return set_errorf(e == cudaErrorMemoryAllocation ? SAS_ERR_OOM : SAS_ERR_CUDA, "%s: %s", where,
+                    cudaGetErrorString(e));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Records the device work of one batch pass on stream s (used under capture).
+cudaError_t record_pass(sas_batch* b, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(b->d_ctr, 0, (size_t)b->n_fields * kCtrN * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b->d_c64, 0, (size_t)b->n_fields * kC64N * 8, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b->d_work, 0, 8, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b->d_ecount_all, 0, b->ecount_words * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b->dev.bucket_count, 0, b->dev.total_buckets * 4, s)) != cudaSuccess) return e;
+  if ((e = batch_launch_prep(b->dev, s)) != cudaSuccess) return e;
+  if ((e = launch_stack_multi(b->kx, b->ky, b->cb, b->d_args, b->d_unit_base, (int)b->n_fields,
+                              b->d_work, b->stack_smem, b->stack_grid, s)) != cudaSuccess)
+    return e;
+  if ((e = batch_launch_post(b->dev, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(b->h_ctr, b->d_ctr, (size_t)b->n_fields * kCtrN * 4,
+                           cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(b->h_c64, b->d_c64, (size_t)b->n_fields * kC64N * 8,
+                         cudaMemcpyDeviceToHost, s);
+}
+
+void free_batch(sas_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->arena) cudaFree(b->arena);
+  if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->h_c64) cudaFreeHost(b->h_c64);
+  for (sas_result* r : b->fallback) sas_result_free(r);
+  for (sas_grid* g : b->grids) sas_destroy_grid(g);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, const uint32_t* n_min,
+                     uint32_t n_fields, const sas_opts* opts, void* stream, sas_batch** out) {
+  if (!grids || !cats || !n_min || !out || n_fields == 0) return set_error(SAS_ERR_ARG, "null argument or no fields");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return cuda_err(ce, "cudaGetDevice");
+  DevInfo di;
+  if (int rc = device_info(dev, &di)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  sas_batch* b = new (std::nothrow) sas_batch;
+  if (!b) return set_error(SAS_ERR_OOM, "host allocation");
+  b->device = dev;
+  b->n_fields = n_fields;
+  int rc = SAS_OK;
+  // --- plan every field --------------------------------------------------------
+  for (uint32_t f = 0; f < n_fields && rc == SAS_OK; ++f) {
+    const sas_catalog& c = cats[f];
+    if (!grids[f]) { rc = set_error(SAS_ERR_ARG, "null grid"); break; }
+    if (!c.on_device) { rc = set_error(SAS_ERR_ARG, "batch catalogs must be in device memory"); break; }
+    if (c.n_epochs < 1 || c.n_epochs > SAS_MAX_EPOCHS) { rc = set_error(SAS_ERR_RANGE, "n_epochs out of range"); break; }
+    if (!c.t || c.ticks_per_hour <= 0) { rc = set_error(SAS_ERR_ARG, "bad epoch times"); break; }
+    if (c.n == 0 || c.n >= ((uint64_t)1 << 31)) { rc = set_error(SAS_ERR_RANGE, "each field needs 1 <= n < 2^31 detections"); break; }
+    if (!c.x || !c.y || !c.epoch) { rc = set_error(SAS_ERR_ARG, "null catalog array"); break; }
+    if (n_min[f] < 1 || n_min[f] > 128) { rc = set_error(SAS_ERR_ARG, "batch fields need 1 <= n_min <= 128"); break; }
+    int64_t tmin = c.t[0], tmax = c.t[0];
+    for (uint32_t e = 1; e < c.n_epochs; ++e) { tmin = std::min(tmin, c.t[e]); tmax = std::max(tmax, c.t[e]); }
+    if ((__int128)tmax - tmin >= ((__int128)1 << 32)) { rc = set_error(SAS_ERR_RANGE, "time span must be < 2^32 ticks"); break; }
+    sas_grid* gcopy = nullptr;
+    sas_grid_desc desc;
+    // copy the grid through its public descriptor
+    rc = sas_grid_get_desc(grids[f], &desc);
+    if (rc == SAS_OK) rc = sas_create_grid(&desc, &gcopy);
+    if (rc != SAS_OK) break;
+    b->grids.push_back(gcopy);
+    b->times.emplace_back(c.t, c.t + c.n_epochs);
+    sas_catalog cc = c;
+    cc.t = b->times.back().data();
+    b->cats.push_back(cc);
+    b->n_min.push_back(n_min[f]);
+    sas_opts o{};
+    if (opts) o = opts[f];
+    o.counter_bits = 8;  // every field in one launch shares one counter width
+    o.v_begin = o.v_end = 0;
+    b->opts.push_back(o);
+    FieldPlan fp;
+    rc = plan_field(desc, c.n, c.n_epochs, c.t, c.ticks_per_hour, n_min[f], 0,
+                    (uint64_t)desc.nvx * desc.nvy, o, di, &fp);
+    if (rc != SAS_OK) break;
+    b->plans.push_back(fp);
+  }
+  if (rc != SAS_OK) { free_batch(b); return rc; }
+  b->kx = b->plans[0].tc.kx;
+  b->ky = b->plans[0].tc.ky;
+  b->cb = 8;
+  for (const FieldPlan& fp : b->plans) {
+    if (fp.tc.kx != b->kx || fp.tc.ky != b->ky) {
+      free_batch(b);
+      return set_error(SAS_ERR_ARG, "all fields of a batch need the same tile_kx and tile_ky");
+    }
+    b->stack_smem = std::max(b->stack_smem, fp.tc.smem);
+  }
+  // --- sizes and arena layout --------------------------------------------------
+  std::vector<unsigned long long> det_off(n_fields + 1, 0), tab_off(n_fields + 1, 0),
+      emit_off(n_fields + 1, 0), cand_off(n_fields + 1, 0), unit_base(n_fields + 1, 0);
+  std::vector<uint64_t> bucket_base(n_fields + 1, 0), ecount_base(n_fields + 1, 0);
+  std::vector<StackArgs> hargs(n_fields);
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    const sas_catalog& c = b->cats[f];
+    det_off[f + 1] = det_off[f] + c.n;
+    tab_off[f + 1] = tab_off[f] + (unsigned long long)(fp.g.nvx + fp.g.nvy) * fp.g.E;
+    const uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * c.n, 1u << 16), 1u << 24);
+    const uint32_t key_cap = kBatchSortMax;
+    emit_off[f + 1] = emit_off[f] + emit_cap;
+    cand_off[f + 1] = cand_off[f] + key_cap;
+    bucket_base[f + 1] = bucket_base[f] + fp.nb;
+    ecount_base[f + 1] = ecount_base[f] + fp.g.E;
+    fill_stack_args(fp, b->n_min[f], &hargs[f]);
+    unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
+    b->key_cap.push_back(key_cap);
+    b->ids_cap.push_back((uint64_t)key_cap * (fp.g.E + 8));
+  }
+  BatchDev& B = b->dev;
+  B.n_fields = (int)n_fields;
+  B.total_dets = det_off[n_fields];
+  B.total_buckets = bucket_base[n_fields];
+  B.total_tab = tab_off[n_fields];
+  B.total_emit = emit_off[n_fields];
+  B.total_cand = cand_off[n_fields];
+  b->ecount_words = ecount_base[n_fields];
+  // one arena: [region sizes computed here]
+  struct Reg { void** p; size_t bytes; };
+  std::vector<Reg> regs;
+  std::vector<Emit*> f_emits(n_fields);
+  std::vector<Key*> f_keys(n_fields);
+  std::vector<unsigned long long*> f_idoff(n_fields);
+  std::vector<uint32_t*> f_ids(n_fields), f_idt(n_fields);
+  std::vector<sas_candidate*> f_cands(n_fields);
+  std::vector<int32_t*> f_sxt(n_fields), f_syt(n_fields);
+  std::vector<int64_t*> f_t(n_fields), f_dt(n_fields);
+  regs.push_back({(void**)&B.fields, n_fields * sizeof(BatchField)});
+  regs.push_back({(void**)&b->d_args, n_fields * sizeof(StackArgs)});
+  regs.push_back({(void**)&b->d_unit_base, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.det_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.tab_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.emit_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.cand_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&b->d_ctr, (size_t)n_fields * kCtrN * 4});
+  regs.push_back({(void**)&b->d_c64, (size_t)n_fields * kC64N * 8});
+  regs.push_back({(void**)&b->d_work, 8});
+  regs.push_back({(void**)&b->d_ecount_all, b->ecount_words * 4});
+  regs.push_back({(void**)&B.bucket_count, B.total_buckets * 4});
+  regs.push_back({(void**)&B.boff, (B.total_buckets + 1) * 4});
+  regs.push_back({(void**)&B.cursor, B.total_buckets * 4});
+  regs.push_back({(void**)&B.scan_scratch, scan_scratch_elems(B.total_buckets) * 4});
+  regs.push_back({(void**)&B.bucket_of, B.total_dets * 4});
+  regs.push_back({(void**)&B.dets, B.total_dets * sizeof(Det)});
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    regs.push_back({(void**)&f_t[f], fp.g.E * 8});
+    regs.push_back({(void**)&f_dt[f], fp.g.E * 8});
+    regs.push_back({(void**)&f_sxt[f], (size_t)fp.g.nvx * fp.g.E * 4});
+    regs.push_back({(void**)&f_syt[f], (size_t)fp.g.nvy * fp.g.E * 4});
+    regs.push_back({(void**)&f_emits[f], (emit_off[f + 1] - emit_off[f]) * sizeof(Emit)});
+    regs.push_back({(void**)&f_keys[f], (size_t)b->key_cap[f] * sizeof(Key)});
+    regs.push_back({(void**)&f_idoff[f], ((size_t)b->key_cap[f] + 1) * 8});
+    regs.push_back({(void**)&f_ids[f], b->ids_cap[f] * 4});
+    regs.push_back({(void**)&f_idt[f], b->ids_cap[f] * 4});
+    regs.push_back({(void**)&f_cands[f], (size_t)b->key_cap[f] * sizeof(sas_candidate)});
+  }
+  size_t total = 0;
+  for (const Reg& r : regs) total += align256(std::max<size_t>(r.bytes, 1));
+  if ((ce = cudaMalloc(&b->arena, total)) != cudaSuccess) { rc = cuda_err(ce, "batch arena"); free_batch(b); return rc; }
+  {
+    size_t off = 0;
+    for (const Reg& r : regs) {
+      *r.p = static_cast<char*>(b->arena) + off;
+      off += align256(std::max<size_t>(r.bytes, 1));
+    }
+  }
+  if ((ce = cudaMallocHost((void**)&b->h_ctr, (size_t)n_fields * kCtrN * 4)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_c64, (size_t)n_fields * kC64N * 8)) != cudaSuccess) {
+    rc = cuda_err(ce, "pinned counters");
+    free_batch(b);
+    return rc;
+  }
+  // --- field descriptors ---------------------------------------------------------
+  b->hf.resize(n_fields);
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    const sas_catalog& c = b->cats[f];
+    StackArgs& sa = hargs[f];
+    uint32_t* ctr = b->d_ctr + (size_t)f * kCtrN;
+    unsigned long long* c64 = b->d_c64 + (size_t)f * kC64N;
+    sa.dets = B.dets;
+    sa.boff = B.boff + bucket_base[f];
+    sa.ecount = b->d_ecount_all + ecount_base[f];
+    sa.sxt = f_sxt[f];
+    sa.syt = f_syt[f];
+    sa.emits = f_emits[f];
+    sa.emit_cap = (uint32_t)(emit_off[f + 1] - emit_off[f]);
+    sa.n_emit = ctr + kCtrEmit;
+    sa.n_pairs = c64 + kC64Pairs;
+    sa.balance = c64 + kC64Balance;
+    sa.flags = ctr + kCtrFlags;
+    sa.tile_counter = b->d_work;
+    BatchField& bf = b->hf[f];
+    memset(&bf, 0, sizeof(bf));
+    bf.args = sa;
+    bf.x = c.x;
+    bf.y = c.y;
+    bf.epoch = c.epoch;
+    bf.t = f_t[f];
+    bf.E = fp.g.E;
+    bf.emit_cap = sa.emit_cap;
+    bf.ecount = const_cast<uint32_t*>(sa.ecount);
+    bf.dt = f_dt[f];
+    bf.t0 = reinterpret_cast<long long*>(c64 + kC64T0);
+    bf.sxt = f_sxt[f];
+    bf.syt = f_syt[f];
+    bf.bucket_base = bucket_base[f];
+    bf.counters = ctr;
+    bf.keys = f_keys[f];
+    bf.key_cap = b->key_cap[f];
+    bf.max_out = b->opts[f].max_candidates ? (uint32_t)std::min<uint64_t>(b->opts[f].max_candidates, b->key_cap[f]) : b->key_cap[f];
+    bf.id_off = f_idoff[f];
+    bf.ids = f_ids[f];
+    bf.ids_tmp = f_idt[f];
+    bf.ids_cap = b->ids_cap[f];
+    bf.cands = f_cands[f];
+    if ((ce = cudaMemcpyAsync(f_t[f], c.t, fp.g.E * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.fields, b->hf.data(), n_fields * sizeof(BatchField), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_args, hargs.data(), n_fields * sizeof(StackArgs), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_unit_base, unit_base.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.det_off, det_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.tab_off, tab_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.emit_off, emit_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.cand_off, cand_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess) ce = stack_set_smem_attr(b->kx, b->ky, b->cb, b->stack_smem);
+  if (ce == cudaSuccess) ce = batch_set_attrs();
+  if (ce != cudaSuccess) { rc = cuda_err(ce, "batch setup"); free_batch(b); return rc; }
+  b->stack_grid = (int)std::min<unsigned long long>((unsigned long long)di.sms, std::max<unsigned long long>(unit_base[n_fields], 1));
+  // --- record the pass as a graph ---------------------------------------------
+  cudaStream_t cs;
+  if ((ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_err(ce, "stream"); free_batch(b); return rc; }
+  ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t ce2 = ce == cudaSuccess ? record_pass(b, cs) : ce;
+  cudaGraph_t g = nullptr;
+  if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &g);
+  if (ce == cudaSuccess) ce = ce2;
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, g, 0);
+  b->graph = g;
+  cudaStreamDestroy(cs);
+  if (ce != cudaSuccess) { rc = cuda_err(ce, "graph capture"); free_batch(b); return rc; }
+  cudaEventCreate(&b->ev0);
+  cudaEventCreate(&b->ev1);
+  b->fallback.assign(n_fields, nullptr);
+  *out = b;
+  return SAS_OK;
+}
+
+int sas_batch_run(sas_batch* b, void* stream) {
+  if (!b) return set_error(SAS_ERR_ARG, "null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (sas_result*& r : b->fallback) {
+    if (r) sas_result_free(r);
+    r = nullptr;
+  }
+  cudaEventRecord(b->ev0, s);
+  cudaError_t ce = cudaGraphLaunch(b->exec, s);
+  cudaEventRecord(b->ev1, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_err(ce, "batch graph");
+  cudaEventElapsedTime(&b->ms_last, b->ev0, b->ev1);
+  // exact fallback for fields that did not fit their capacities
+  for (uint32_t f = 0; f < b->n_fields; ++f) {
+    const uint32_t* ctr = b->h_ctr + (size_t)f * kCtrN;
+    const unsigned long long* c64 = b->h_c64 + (size_t)f * kC64N;
+    const uint32_t fl = ctr[kCtrFlags];
+    if (fl & kFlagEpoch) return set_errorf(SAS_ERR_RANGE, "field %u: an epoch index is >= n_epochs", f);
+    if (fl & kFlagPos) return set_errorf(SAS_ERR_RANGE, "field %u: a detection has |x| or |y| >= 2^29", f);
+    if (fl & kFlagShift) return set_errorf(SAS_ERR_RANGE, "field %u: a shift |v*(t-t0)/TPH| >= 2^28", f);
+    const bool redo = (fl & (kFlagEmitCap | kFlagCounter | kFlagInternal)) || c64[kC64Balance] != 0 ||
+                      ctr[kCtrEmit] > b->hf[f].emit_cap;
+    if (!redo) continue;
+    sas_opts o = b->opts[f];
+    o.counter_bits = 0;
+    const int rc = sas_stack(b->grids[f], &b->cats[f], b->n_min[f], &o, stream, &b->fallback[f]);
+    if (rc != SAS_OK) return rc;
+    ++b->fallback_count;
+  }
+  return SAS_OK;
+}
+
+int sas_batch_field_info(const sas_batch* b, uint32_t field, sas_result_info* info) {
+  if (!b || !info || field >= b->n_fields) return set_error(SAS_ERR_ARG, "bad argument");
+  if (b->fallback[field]) return sas_result_get_info(b->fallback[field], info);
+  const uint32_t* ctr = b->h_ctr + (size_t)field * kCtrN;
+  const unsigned long long* c64 = b->h_c64 + (size_t)field * kC64N;
+  memset(info, 0, sizeof(*info));
+  info->n_candidates = ctr[kCtrOut];
+  info->n_ids = (uint64_t)ctr[kCtrIdsLo] | ((uint64_t)ctr[kCtrIdsHi] << 32);
+  info->n_pairs = c64[kC64Pairs];
+  info->n_emitted = ctr[kCtrEmit];
+  info->t0 = (int64_t)c64[kC64T0];
+  const TileCfg& tc = b->plans[field].tc;
+  info->counter_bits = (uint32_t)tc.cb;
+  info->tile_kx = (uint32_t)tc.kx;
+  info->tile_ky = (uint32_t)tc.ky;
+  info->tile_bx = (uint32_t)tc.tx;
+  info->tile_by = (uint32_t)tc.ty;
+  info->superbin = (uint32_t)tc.s;
+  info->vblock_x = (uint32_t)tc.bvx;
+  info->vblock_y = (uint32_t)tc.bvy;
+  info->staged_cap = (uint32_t)tc.scap;
+  info->ms_total = b->ms_last;
+  return SAS_OK;
+}
+
+int sas_batch_candidates(const sas_batch* b, uint32_t field, sas_candidate* out, uint64_t cap,
+                         uint64_t* n_total, uint32_t* ids, uint64_t ids_cap, uint64_t* n_ids_total,
+                         int on_device) {
+  if (!b || field >= b->n_fields) return set_error(SAS_ERR_ARG, "bad argument");
+  if (b->fallback[field])
+    return sas_candidates(b->fallback[field], out, cap, n_total, ids, ids_cap, n_ids_total, on_device);
+  sas_result_info info;
+  sas_batch_field_info(b, field, &info);
+  const uint64_t nc = info.n_candidates, ni = info.n_ids;
+  if (n_total) *n_total = nc;
+  if (n_ids_total) *n_ids_total = ni;
+  const uint64_t c1 = std::min(cap, nc), i1 = std::min(ids_cap, ni);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c1) {
+    if (!out) return set_error(SAS_ERR_ARG, "null candidate buffer");
+    cudaError_t e = cudaMemcpy(out, b->hf[field].cands, c1 * sizeof(sas_candidate), kind);
+    if (e != cudaSuccess) return cuda_err(e, "copy candidates");
+  }
+  if (i1) {
+    if (!ids) return set_error(SAS_ERR_ARG, "null id buffer");
+    cudaError_t e = cudaMemcpy(ids, b->hf[field].ids, i1 * sizeof(uint32_t), kind);
+    if (e != cudaSuccess) return cuda_err(e, "copy ids");
+  }
+  if (cap < nc || ids_cap < ni)
+    return set_errorf(SAS_ERR_OVERFLOW, "buffers too small: need %llu candidates and %llu ids",
+                      (unsigned long long)nc, (unsigned long long)ni);
+  return SAS_OK;
+}
+
+int sas_batch_stats(const sas_batch* b, float* ms_last, uint64_t* fallbacks) {
+  if (!b) return set_error(SAS_ERR_ARG, "null batch");
+  if (ms_last) *ms_last = b->ms_last;
+  if (fallbacks) *fallbacks = b->fallback_count;
+  return SAS_OK;
+}
+
+void sas_batch_destroy(sas_batch* b) { free_batch(b); }
+
+int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* base,
+                 uint32_t reps, void* stream, sas_opts* best, float* best_ms) {
+  if (!grid || !cat || !best) return set_error(SAS_ERR_ARG, "null argument");
+  if (reps == 0) reps = 3;
+  sas_opts o0{};
+  if (base) o0 = *base;
+  float best_t = 1e30f;
+  sas_opts best_o = o0;
+  bool any = false;
+  for (uint32_t sb : {1u, 2u, 3u}) {
+    for (uint32_t vb : {1u, 2u, 4u, 8u}) {
+      sas_opts o = o0;
+      o.superbin = sb;
+      o.velocity_block = vb;
+      std::vector<float> ts;
+      int rc = SAS_OK;
+      for (uint32_t r = 0; r <= reps && rc == SAS_OK; ++r) {
+        sas_result* res = nullptr;
+        rc = sas_stack(grid, cat, n_min, &o, stream, &res);
+        if (rc != SAS_OK) break;
+        sas_result_info inf;
+        sas_result_get_info(res, &inf);
+        if (r > 0) ts.push_back(inf.ms_total);
+        sas_result_free(res);
+      }
+      if (rc != SAS_OK) continue;  // a configuration the planner rejects for this field
+      std::sort(ts.begin(), ts.end());
+      const float med = ts[ts.size() / 2];
+      if (med < best_t) {
+        best_t = med;
+        best_o = o;
+        any = true;
+      }
+    }
+  }
+  if (!any) return set_error(SAS_ERR_ARG, "no tile configuration fits this field");
+  *best = best_o;
+  if (best_ms) *best_ms = best_t;
+  return SAS_OK;
+}
+
+}  // extern "C"

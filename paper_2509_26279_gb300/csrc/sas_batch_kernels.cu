@@ -1,0 +1,405 @@
+// Device side of the batched search: many fields in one pass of each kernel.
+//
+// Every kernel here covers all fields of a batch in one launch; a thread, warp
+// or block finds its field from prefix offsets (binary search over n_fields + 1
+// entries).  The arithmetic per field is the same as in sas_prep.cu,
+// sas_stack.cu and sas_post.cu.
+#include <climits>
+
+#include "sas_batch.cuh"
+
+namespace sas {
+
+namespace {
+
+__device__ __forceinline__ int find_field(const unsigned long long* off, int n_fields,
+                                          unsigned long long i) {
+  int lo = 0, hi = n_fields;  // largest f with off[f] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ Key max_key_b() {
+  Key k;
+  k.a = ~0ull;
+  k.b = ~0ull;
+  k.c = ~0u;
+  k.pad = 0;
+  return k;
+}
+
+__device__ __forceinline__ bool key_less_b(const Key& p, const Key& q) {
+  if (p.a != q.a) return p.a < q.a;
+  if (p.b != q.b) return p.b < q.b;
+  return p.c < q.c;
+}
+
+// Validation, per-epoch counts and per-bucket counts of every detection.
+__global__ void k_batch_ingest(const BatchField* __restrict__ F, int n_fields,
+                               const unsigned long long* __restrict__ det_off,
+                               uint32_t* __restrict__ bucket_count, uint32_t* __restrict__ bucket_of) {
+  const unsigned long long total = det_off[n_fields];
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int f = find_field(det_off, n_fields, i);
+    const BatchField& bf = F[f];
+    const unsigned long long k = i - det_off[f];
+    const uint32_t e = bf.epoch[k];
+    const int32_t xi = bf.x[k], yi = bf.y[k];
+    uint32_t b = kInvalidBucket;
+    if (e >= bf.E) {
+      atomicOr(bf.counters + kCtrFlags, kFlagEpoch);
+    } else {
+      atomicAdd(&bf.ecount[e], 1u);
+      if (xi <= -kLimPos || xi >= kLimPos || yi <= -kLimPos || yi >= kLimPos) {
+        atomicOr(bf.counters + kCtrFlags, kFlagPos);
+      } else {
+        const CoarseGeom& cg = bf.args.cg;
+        const int64_t cx = floor_div64((int64_t)xi - cg.gx0, cg.cell);
+        const int64_t cy = floor_div64((int64_t)yi - cg.gy0, cg.cell);
+        if (cx >= 0 && cx < cg.ncx && cy >= 0 && cy < cg.ncy) {
+          b = (uint32_t)(bf.bucket_base +
+                         ((uint64_t)e * cg.ncy + (uint64_t)cy) * cg.ncx + (uint64_t)cx);
+          atomicAdd(&bucket_count[b], 1u);
+        }
+      }
+    }
+    bucket_of[i] = b;
+  }
+}
+
+__global__ void k_batch_scatter(const BatchField* __restrict__ F, int n_fields,
+                                const unsigned long long* __restrict__ det_off,
+                                const uint32_t* __restrict__ bucket_of, uint32_t* __restrict__ cursor,
+                                Det* __restrict__ dets) {
+  const unsigned long long total = det_off[n_fields];
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t b = bucket_of[i];
+    if (b == kInvalidBucket) continue;
+    const int f = find_field(det_off, n_fields, i);
+    const BatchField& bf = F[f];
+    const unsigned long long k = i - det_off[f];
+    Det d;
+    d.x = bf.x[k];
+    d.y = bf.y[k];
+    d.e = bf.epoch[k];
+    d.id = (uint32_t)k;
+    dets[atomicAdd(&cursor[b], 1u)] = d;
+  }
+}
+
+// Sec. 2.1 step 1 per field: t0 = earliest time with a detection, dt = t - t0.
+__global__ void k_batch_epoch_setup(const BatchField* __restrict__ F) {
+  const BatchField& bf = F[blockIdx.x];
+  __shared__ long long s_min[32];
+  long long m = LLONG_MAX;
+  for (uint32_t e = threadIdx.x; e < bf.E; e += blockDim.x)
+    if (bf.ecount[e] > 0 && bf.t[e] < m) m = bf.t[e];
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long other = __shfl_xor_sync(0xffffffffu, m, o);
+    m = other < m ? other : m;
+  }
+  if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t0 = s_min[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t0 = s_min[w] < t0 ? s_min[w] : t0;
+    s_min[0] = t0;
+    bf.t0[0] = t0;
+  }
+  __syncthreads();
+  const long long t0 = s_min[0];
+  for (uint32_t e = threadIdx.x; e < bf.E; e += blockDim.x)
+    bf.dt[e] = bf.ecount[e] > 0 ? (int64_t)(bf.t[e] - t0) : 0;
+}
+
+// Sec. 2 Eq. 1-2 per field: x and y shift tables, one thread per entry.
+__global__ void k_batch_shift(const BatchField* __restrict__ F, int n_fields,
+                              const unsigned long long* __restrict__ tab_off) {
+  const unsigned long long total = tab_off[n_fields];
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int f = find_field(tab_off, n_fields, i);
+    const BatchField& bf = F[f];
+    const SearchGeom& g = bf.args.g;
+    unsigned long long k = i - tab_off[f];
+    const unsigned long long nx = (unsigned long long)g.nvx * g.E;
+    const bool is_x = k < nx;
+    if (!is_x) k -= nx;
+    const uint32_t c = (uint32_t)(k / g.E), e = (uint32_t)(k % g.E);
+    const int64_t v = is_x ? (int64_t)g.vx0 + (int64_t)c * g.dvx : (int64_t)g.vy0 + (int64_t)c * g.dvy;
+    const int64_t s = floor_div64(v * bf.dt[e], g.tph);
+    int32_t sv = 0;
+    if (s <= -kLimDomain || s >= kLimDomain) {
+      if (bf.ecount[e] > 0) atomicOr(bf.counters + kCtrFlags, kFlagShift);
+    } else {
+      sv = (int32_t)s;
+    }
+    (is_x ? bf.sxt : bf.syt)[k] = sv;
+  }
+}
+
+constexpr int kWarps = 8;
+
+// Exact counts of every bin of every emitted super-bin of every field; one warp
+// per emission slot (slots beyond a field's emission count exit).
+__global__ void k_batch_cell_count(const BatchField* __restrict__ F, int n_fields,
+                                   const unsigned long long* __restrict__ emit_off,
+                                   const Det* __restrict__ dets, const uint32_t* __restrict__ boff) {
+  const unsigned long long w = blockIdx.x * (unsigned long long)kWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= emit_off[n_fields]) return;
+  const int f = find_field(emit_off, n_fields, w);
+  const BatchField& bf = F[f];
+  const unsigned long long j = w - emit_off[f];
+  const uint32_t n_emit = min(bf.counters[kCtrEmit], bf.emit_cap);
+  if (j >= n_emit) return;
+  const SearchGeom& g = bf.args.g;
+  const CoarseGeom& cg = bf.args.cg;
+  const Emit em = bf.args.emits[j];
+  const int sb = bf.args.tc.s;
+  const uint32_t kx = em.v_idx % (uint32_t)g.nvx, ky = em.v_idx / (uint32_t)g.nvx;
+  const int nq = sb * sb;
+  const int32_t span = sb * g.bin;
+  uint32_t distinct[16], raw[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) distinct[q] = raw[q] = 0;
+  for (uint32_t eb = 0; eb < g.E; eb += 32) {
+    const uint32_t e = eb + lane;
+    uint32_t hit = 0;
+    if (e < g.E && bf.ecount[e] > 0) {
+      const int32_t ox = g.x_min + (int32_t)em.bx * g.bin + bf.sxt[(size_t)kx * g.E + e];
+      const int32_t oy = g.y_min + (int32_t)em.by * g.bin + bf.syt[(size_t)ky * g.E + e];
+      const int cxa = max(floor_div32(ox - cg.gx0, cg.cell), 0);
+      const int cxb = min(floor_div32(ox + span - 1 - cg.gx0, cg.cell), cg.ncx - 1);
+      const int cya = max(floor_div32(oy - cg.gy0, cg.cell), 0);
+      const int cyb = min(floor_div32(oy + span - 1 - cg.gy0, cg.cell), cg.ncy - 1);
+      for (int cy = cya; cy <= cyb && cxa <= cxb; ++cy) {
+        const size_t b0 = bf.bucket_base + ((size_t)e * cg.ncy + cy) * cg.ncx;
+        const uint32_t k1 = boff[b0 + cxb + 1];
+        for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
+          const Det d = dets[k];
+          const uint32_t X = (uint32_t)(d.x - ox), Y = (uint32_t)(d.y - oy);
+          if (X < (uint32_t)span && Y < (uint32_t)span) {
+            const int q = (int)(Y / (uint32_t)g.bin) * sb + (int)(X / (uint32_t)g.bin);
+            hit |= 1u << q;
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) raw[qq] += (qq == q);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (q < nq) distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q >= nq) break;
+    uint32_t r = raw[q];
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) {
+      const uint32_t bx = em.bx + (uint32_t)(q % sb), by = em.by + (uint32_t)(q / sb);
+      if (bx < (uint32_t)g.nbx && by < (uint32_t)g.nby && distinct[q] >= bf.args.n_min) {
+        Key k;
+        k.a = ((uint64_t)(~distinct[q]) << 32) | (uint64_t)(~r);
+        k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
+        k.c = bx;
+        k.pad = 0;
+        const uint32_t p = atomicAdd(bf.counters + kCtrValid, 1u);
+        if (p < bf.key_cap) bf.keys[p] = k; else atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+      }
+    }
+  }
+}
+
+// One block per field: bitonic sort of the field's valid keys in shared memory
+// (up to kBatchSortMax keys; more sets the field's capacity flag), then the
+// exclusive scan of the raw counts of the first n_out keys into id offsets.
+__global__ void __launch_bounds__(1024) k_batch_sort_offsets(const BatchField* __restrict__ F) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Key* s = reinterpret_cast<Key*>(smem);
+  __shared__ unsigned long long s_warp[33];
+  const BatchField& bf = F[blockIdx.x];
+  const uint32_t n_valid = bf.counters[kCtrValid];
+  if (n_valid > kBatchSortMax || n_valid > bf.key_cap) {
+    if (threadIdx.x == 0) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+    return;
+  }
+  uint32_t n_pad = 1;
+  while (n_pad < n_valid) n_pad <<= 1;
+  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) s[i] = i < n_valid ? bf.keys[i] : max_key_b();
+  __syncthreads();
+  for (uint32_t k = 2; k <= n_pad; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const bool asc = (i & k) == 0;
+          if (key_less_b(s[ixj], s[i]) == asc) {
+            const Key t = s[i];
+            s[i] = s[ixj];
+            s[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const uint32_t n_out = min(n_valid, bf.max_out);
+  unsigned long long carry = 0;
+  for (uint32_t base = 0; base < n_out; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const unsigned long long r = i < n_out ? (unsigned long long)(~(uint32_t)s[i].a) : 0ull;
+    // block exclusive scan of r
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = r;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long n = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += n;
+    }
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      const int nw = blockDim.x >> 5;
+      const unsigned long long x = lane < nw ? s_warp[lane] : 0ull;
+      unsigned long long sc = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += n;
+      }
+      if (lane < nw) s_warp[lane] = sc - x;
+      if (lane == nw - 1) s_warp[32] = sc;
+    }
+    __syncthreads();
+    if (i < n_out) {
+      bf.keys[i] = s[i];
+      bf.id_off[i] = carry + s_warp[w] + inc - r;
+    }
+    carry += s_warp[32];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    bf.counters[kCtrOut] = n_out;
+    bf.id_off[n_out] = carry;
+    bf.counters[kCtrIdsLo] = (uint32_t)carry;
+    bf.counters[kCtrIdsHi] = (uint32_t)(carry >> 32);
+    if (carry > bf.ids_cap) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+  }
+}
+
+// Contributing ids (ascending) and the candidate records of every field; one
+// warp per candidate slot.
+__global__ void k_batch_ids(const BatchField* __restrict__ F, int n_fields,
+                            const unsigned long long* __restrict__ cand_off,
+                            const Det* __restrict__ dets, const uint32_t* __restrict__ boff) {
+  __shared__ uint32_t s_cursor[kWarps];
+  const int wl = threadIdx.x >> 5;
+  const unsigned long long w = blockIdx.x * (unsigned long long)kWarps + wl;
+  const int lane = threadIdx.x & 31;
+  if (w >= cand_off[n_fields]) return;
+  const int f = find_field(cand_off, n_fields, w);
+  const BatchField& bf = F[f];
+  const unsigned long long c = w - cand_off[f];
+  const uint32_t n_out = bf.counters[kCtrOut];
+  if (c >= n_out || (bf.counters[kCtrFlags] & kFlagEmitCap)) return;
+  const SearchGeom& g = bf.args.g;
+  const CoarseGeom& cg = bf.args.cg;
+  const Key key = bf.keys[c];
+  const uint32_t v_idx = (uint32_t)(key.b >> 32), by = (uint32_t)key.b, bx = key.c;
+  const uint32_t raw = ~(uint32_t)key.a;
+  const uint32_t kx = v_idx % (uint32_t)g.nvx, ky = v_idx / (uint32_t)g.nvx;
+  const unsigned long long off = bf.id_off[c];
+  if (lane == 0) {
+    sas_candidate rec;
+    rec.v_idx = v_idx;
+    rec.bx = bx;
+    rec.by = by;
+    rec.count = ~(uint32_t)(key.a >> 32);
+    rec.raw = raw;
+    rec.id_len = raw;
+    rec.id_off = off;
+    bf.cands[c] = rec;
+    s_cursor[wl] = 0;
+  }
+  __syncwarp();
+  for (uint32_t eb = 0; eb < g.E; eb += 32) {
+    const uint32_t e = eb + lane;
+    if (e >= g.E || bf.ecount[e] == 0) continue;
+    const int32_t ox = g.x_min + (int32_t)bx * g.bin + bf.sxt[(size_t)kx * g.E + e];
+    const int32_t oy = g.y_min + (int32_t)by * g.bin + bf.syt[(size_t)ky * g.E + e];
+    const int cxa = max(floor_div32(ox - cg.gx0, cg.cell), 0);
+    const int cxb = min(floor_div32(ox + g.bin - 1 - cg.gx0, cg.cell), cg.ncx - 1);
+    const int cya = max(floor_div32(oy - cg.gy0, cg.cell), 0);
+    const int cyb = min(floor_div32(oy + g.bin - 1 - cg.gy0, cg.cell), cg.ncy - 1);
+    for (int cy = cya; cy <= cyb && cxa <= cxb; ++cy) {
+      const size_t b0 = bf.bucket_base + ((size_t)e * cg.ncy + cy) * cg.ncx;
+      const uint32_t k1 = boff[b0 + cxb + 1];
+      for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
+        const Det d = dets[k];
+        if (((uint32_t)(d.x - ox) < (uint32_t)g.bin) && ((uint32_t)(d.y - oy) < (uint32_t)g.bin)) {
+          const uint32_t p = atomicAdd(&s_cursor[wl], 1u);
+          if (p < raw) bf.ids_tmp[off + p] = d.id;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (s_cursor[wl] != raw) {
+    if (lane == 0) atomicOr(bf.counters + kCtrFlags, kFlagInternal);
+    return;
+  }
+  for (uint32_t i = lane; i < raw; i += 32) {
+    const uint32_t v = bf.ids_tmp[off + i];
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < raw; ++j) r += bf.ids_tmp[off + j] < v;
+    bf.ids[off + r] = v;
+  }
+}
+
+unsigned grid_for(unsigned long long n, int threads) {
+  unsigned long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152ull * 64) b = 152ull * 64;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t batch_launch_prep(const BatchDev& B, cudaStream_t s) {
+  k_batch_ingest<<<grid_for(B.total_dets, 256), 256, 0, s>>>(B.fields, B.n_fields, B.det_off,
+                                                              B.bucket_count, B.bucket_of);
+  note_launch();
+  cudaError_t e = launch_scan_u32(B.bucket_count, B.boff, B.total_buckets, B.scan_scratch, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(B.cursor, B.boff, B.total_buckets * sizeof(uint32_t),
+                      cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  k_batch_scatter<<<grid_for(B.total_dets, 256), 256, 0, s>>>(B.fields, B.n_fields, B.det_off,
+                                                               B.bucket_of, B.cursor, B.dets);
+  k_batch_epoch_setup<<<B.n_fields, 1024, 0, s>>>(B.fields);
+  k_batch_shift<<<grid_for(B.total_tab, 256), 256, 0, s>>>(B.fields, B.n_fields, B.tab_off);
+  note_launch(3);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_post(const BatchDev& B, cudaStream_t s) {
+  k_batch_cell_count<<<(unsigned)((B.total_emit + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
+      B.fields, B.n_fields, B.emit_off, B.dets, B.boff);
+  k_batch_sort_offsets<<<B.n_fields, 1024, kBatchSortMax * sizeof(Key), s>>>(B.fields);
+  k_batch_ids<<<(unsigned)((B.total_cand + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
+      B.fields, B.n_fields, B.cand_off, B.dets, B.boff);
+  note_launch(3);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_set_attrs() {
+  return cudaFuncSetAttribute(k_batch_sort_offsets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kBatchSortMax * sizeof(Key)));
+}
+
+}  // namespace sas

@@ -112,6 +112,42 @@ struct StackArgs {
 // Process-wide count of kernels launched by the library (sas_kernel_launches).
 void note_launch(uint32_t k = 1);
 
+// Records the message of a failed call for sas_last_error() (printf-style) and
+// returns code.
+int set_errorf(int code, const char* fmt, ...);
+inline int set_error(int code, const char* msg) { return set_errorf(code, "%s", msg); }
+
+// ---- planning (sas_plan.cu) -------------------------------------------------
+
+struct DevInfo {
+  int sms = 0;
+  int smem_optin = 0;
+  int smem_per_sm = 0;
+  bool ready = false;
+};
+int device_info(int dev, DevInfo* out);
+uint32_t magic_for(int32_t bin);  // ceil(2^32 / bin)
+
+// The plan of one field's search (sizes only; no device work).
+struct FieldPlan {
+  TileCfg tc;
+  CoarseGeom cg;
+  SearchGeom g;
+  int kx, ky, cb, sb;
+  int ky_lo, ky_hi, n_rows;
+  uint64_t nb;  // buckets: E * ncy * ncx
+  int64_t dT;   // max(t) - min(t)
+};
+int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t, int64_t tph,
+               uint32_t n_min, uint64_t v_begin, uint64_t v_end, const sas_opts& o,
+               const DevInfo& di, FieldPlan* fp);
+// Same plan with counters twice as wide (after a counter wrapped).
+int replan_wider(const sas_grid_desc& d, uint64_t n, uint32_t n_min, const sas_opts& o,
+                 const DevInfo& di, FieldPlan* fp);
+// Geometry, tiling and division parts of the stack kernel's arguments.
+struct StackArgs;
+void fill_stack_args(const FieldPlan& fp, uint32_t n_min, StackArgs* sa);
+
 // ---- launchers (defined in the .cu files) ----------------------------------
 
 // sas_prep.cu
@@ -136,6 +172,11 @@ bool stack_config_supported(int kx, int ky, int cb);
 size_t stack_smem_bytes(const TileCfg& tc);
 size_t stack_counter_bytes(const TileCfg& tc);
 cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s);
+// One persistent launch over the units of several fields (per-field StackArgs in
+// device memory; field f owns units [unit_base[f], unit_base[f+1]) of counter).
+cudaError_t launch_stack_multi(int kx, int ky, int cb, const StackArgs* fargs,
+                               const unsigned long long* unit_base, int n_fields,
+                               unsigned long long* counter, size_t smem, int grid, cudaStream_t s);
 cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
 
 // sas_post.cu

@@ -181,12 +181,13 @@ __device__ __forceinline__ uint32_t word_sum(uint32_t w) {
   else return w;
 }
 
+// Everything one work unit needs lives in shared memory: the counter tile, the
+// staged records, the shift tables, the windows and the bucket segments.
 template <int KX, int KY, int CB>
-__global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
-  static_assert(KX % (32 / CB) == 0, "kx must be a multiple of the counters per word");
-  static_assert(KX * KY <= 32, "at most 32 velocities per tile");
+__device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsigned char* smem,
+                                         bool init_cells, int64_t& balance, uint64_t& pairs64,
+                                         uint32_t& my_flags) {
   using C = Counter<CB>;
-  extern __shared__ __align__(16) unsigned char smem[];
   const TileCfg& tc = a.tc;
   const SmemLayout L = layout(tc);
   uint32_t* cells = reinterpret_cast<uint32_t*>(smem + L.cells);
@@ -199,8 +200,8 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
   uint32_t* s_seg_src = reinterpret_cast<uint32_t*>(smem + L.seg_src);
   Emit* s_emit = reinterpret_cast<Emit*>(smem + L.emit);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
-  // s_misc: [0..33) scan scratch, [40] unit lo, [41] unit hi, [42] active mask,
-  //         [43] emission count, [44] flush base, [45] staged count
+  // s_misc: [0..33) scan scratch, [42] active mask, [43] emission count,
+  //         [44] flush base
   const int tid = threadIdx.x;
   constexpr int P = C::P;
   const uint32_t n_words = (uint32_t)KY * (KX / P) * tc.tx * tc.ty;
@@ -222,22 +223,12 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
 #pragma unroll
   for (int q = 0; q < P; ++q) tmask |= (1u << (CB - 1)) << (CB * q);
   const uint4 start4 = make_uint4(start_word, start_word, start_word, start_word);
-
-  for (uint32_t i = tid; i < n_words / 4; i += kNT) reinterpret_cast<uint4*>(cells)[i] = start4;
-  if (tid == 0) s_misc[43] = 0;
-  int64_t balance = 0;  // (counted excess over the start values) - (pairs added)
-  uint64_t pairs64 = 0;
-  uint32_t my_flags = 0;
-
-  while (true) {
-    if (tid == 0) {
-      const unsigned long long t = atomicAdd(a.tile_counter, 1ull);
-      s_misc[40] = (uint32_t)t;
-      s_misc[41] = (uint32_t)(t >> 32);
-    }
+  if (init_cells) {  // first unit of this block, or of another field
+    for (uint32_t i = tid; i < n_words / 4; i += kNT) reinterpret_cast<uint4*>(cells)[i] = start4;
+    if (tid == 0) s_misc[43] = 0;
     __syncthreads();
-    const uint64_t unit = (uint64_t)s_misc[40] | ((uint64_t)s_misc[41] << 32);
-    if (unit >= a.n_tiles) break;
+  }
+
     const int vb = (int)(unit / n_st), st = (int)(unit % n_st);
     const int kxa = a.kx_lo + (vb % a.nvt_x) * bxk;   // nvt_x/nvt_y count velocity BLOCKS
     const int kya = a.ky_lo + (vb / a.nvt_x) * byk;
@@ -482,33 +473,106 @@ __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a) {
           finish(kx0, ky0);
         }
     }
-    __syncthreads();
-  }
+}
 
-  // Pair count, balance and flags: one global atomic each per warp.
-  for (int o = 16; o > 0; o >>= 1) {
-    pairs64 += __shfl_xor_sync(0xffffffffu, pairs64, o);
-    balance += __shfl_xor_sync(0xffffffffu, balance, o);
-    my_flags |= __shfl_xor_sync(0xffffffffu, my_flags, o);
-  }
-  if ((tid & 31) == 0) {
-    if (pairs64) atomicAdd(a.n_pairs, (unsigned long long)pairs64);
-    if (balance) atomicAdd(a.balance, (unsigned long long)balance);
-    if (my_flags) atomicOr(a.flags, my_flags);
+// Single field: StackArgs as the kernel parameter.  Several fields (one
+// persistent launch over all their units): fargs[f] for field f, whose units
+// are [unit_base[f], unit_base[f + 1]) of one global work counter.
+struct MultiArgs {
+  const StackArgs* fargs;
+  const unsigned long long* unit_base;  // [n_fields + 1]
+  int n_fields;
+  unsigned long long* counter;
+};
+
+template <int KX, int KY, int CB, bool MULTI>
+__global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a0, MultiArgs m) {
+  static_assert(KX % (32 / CB) == 0, "kx must be a multiple of the counters per word");
+  static_assert(KX * KY <= 32, "at most 32 velocities per tile");
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ StackArgs s_args;
+  __shared__ unsigned long long s_unit, s_local;
+  __shared__ int s_field;
+  const int tid = threadIdx.x;
+  int cur_field = -1;
+  while (true) {
+    if (tid == 0) {
+      const unsigned long long t = atomicAdd(MULTI ? m.counter : a0.tile_counter, 1ull);
+      s_unit = t;
+      if (MULTI) {
+        const unsigned long long total = m.unit_base[m.n_fields];
+        int f = 0;
+        if (t < total) {
+          int lo = 0, hi = m.n_fields;  // largest f with unit_base[f] <= t
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (m.unit_base[mid] <= t) lo = mid; else hi = mid;
+          }
+          f = lo;
+        }
+        s_field = f;
+        s_local = t < total ? t - m.unit_base[f] : ~0ull;
+      } else {
+        s_field = 0;
+        s_local = t < a0.n_tiles ? t : ~0ull;
+      }
+    }
+    __syncthreads();
+    const unsigned long long local = s_local;
+    const int field = s_field;
+    if (local == ~0ull) break;
+    if (MULTI && field != cur_field) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&m.fargs[field]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_args);
+      for (int i = tid; i < (int)(sizeof(StackArgs) / 4); i += kNT) dst[i] = src[i];
+      __syncthreads();
+    }
+    const StackArgs& a = MULTI ? s_args : a0;
+    int64_t balance = 0;  // (counted excess over the start values) - (pairs added)
+    uint64_t pairs64 = 0;
+    uint32_t my_flags = 0;
+    run_unit<KX, KY, CB>(a, local, smem, field != cur_field, balance, pairs64, my_flags);
+    cur_field = field;
+    // Per-unit statistics of this field: one global atomic each per warp.
+    for (int o = 16; o > 0; o >>= 1) {
+      pairs64 += __shfl_xor_sync(0xffffffffu, pairs64, o);
+      balance += __shfl_xor_sync(0xffffffffu, balance, o);
+      my_flags |= __shfl_xor_sync(0xffffffffu, my_flags, o);
+    }
+    if ((tid & 31) == 0) {
+      if (pairs64) atomicAdd(a.n_pairs, (unsigned long long)pairs64);
+      if (balance) atomicAdd(a.balance, (unsigned long long)balance);
+      if (my_flags) atomicOr(a.flags, my_flags);
+    }
+    __syncthreads();
   }
 }
 
 template <int KX, int KY, int CB>
 cudaError_t launch_t(const StackArgs& a, int grid, cudaStream_t s) {
-  k_stack<KX, KY, CB><<<grid, kNT, a.tc.smem, s>>>(a);
+  MultiArgs m{};
+  k_stack<KX, KY, CB, false><<<grid, kNT, a.tc.smem, s>>>(a, m);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int KX, int KY, int CB>
+cudaError_t launch_multi_t(const StackArgs& proto, const StackArgs* fargs,
+                           const unsigned long long* unit_base, int n_fields,
+                           unsigned long long* counter, size_t smem, int grid, cudaStream_t s) {
+  MultiArgs m{fargs, unit_base, n_fields, counter};
+  k_stack<KX, KY, CB, true><<<grid, kNT, smem, s>>>(proto, m);
   note_launch();
   return cudaGetLastError();
 }
 
 template <int KX, int KY, int CB>
 cudaError_t attr_t(size_t smem) {
-  return cudaFuncSetAttribute(k_stack<KX, KY, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_stack<KX, KY, CB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stack<KX, KY, CB, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 // Supported (KX, KY, CB) instantiations.
@@ -537,6 +601,18 @@ cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s) {
   if (a.tc.kx == KX && a.tc.ky == KY && a.tc.cb == CB) return launch_t<KX, KY, CB>(a, grid, s);
   SAS_STACK_CONFIGS(SAS_LAUNCH)
 #undef SAS_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stack_multi(int kx, int ky, int cb, const StackArgs* fargs,
+                               const unsigned long long* unit_base, int n_fields,
+                               unsigned long long* counter, size_t smem, int grid, cudaStream_t s) {
+  StackArgs proto{};
+#define SAS_LAUNCH_M(KX, KY, CB)                                                            \
+  if (kx == KX && ky == KY && cb == CB)                                                     \
+    return launch_multi_t<KX, KY, CB>(proto, fargs, unit_base, n_fields, counter, smem, grid, s);
+  SAS_STACK_CONFIGS(SAS_LAUNCH_M)
+#undef SAS_LAUNCH_M
   return cudaErrorInvalidValue;
 }
 

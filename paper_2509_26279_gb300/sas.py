@@ -264,3 +264,109 @@ def sas_probe_shared_atomic_peak(iters: int = 4096, stream=None):
 
 def library():
     return _lib
+
+
+# ---- batched search and autotuner ------------------------------------------------
+
+_lib.sas_grid_get_desc.argtypes = [_p, ctypes.POINTER(sas_grid_desc)]
+_lib.sas_batch_create.argtypes = [ctypes.POINTER(_p), ctypes.POINTER(sas_catalog),
+                                  ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                  ctypes.POINTER(sas_opts), _p, ctypes.POINTER(_p)]
+_lib.sas_batch_run.argtypes = [_p, _p]
+_lib.sas_batch_field_info.argtypes = [_p, ctypes.c_uint32, ctypes.POINTER(sas_result_info)]
+_lib.sas_batch_candidates.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint64), _p, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+_lib.sas_batch_stats.argtypes = [_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)]
+_lib.sas_batch_destroy.argtypes = [_p]
+_lib.sas_batch_destroy.restype = None
+_lib.sas_autotune.argtypes = [_p, ctypes.POINTER(sas_catalog), ctypes.c_uint32,
+                              ctypes.POINTER(sas_opts), ctypes.c_uint32, _p,
+                              ctypes.POINTER(sas_opts), ctypes.POINTER(ctypes.c_float)]
+EXPORTED += ["sas_grid_get_desc", "sas_batch_create", "sas_batch_run", "sas_batch_field_info",
+             "sas_batch_candidates", "sas_batch_stats", "sas_batch_destroy", "sas_autotune"]
+
+
+def _device_catalog(x, y, epoch, t, tph):
+    t = np.ascontiguousarray(t, np.int64)
+    n = int(x.numel() if hasattr(x, "numel") else len(x))
+    return sas_catalog(n=n, x=_dev_ptr(x), y=_dev_ptr(y), epoch=_dev_ptr(epoch),
+                       n_epochs=int(t.shape[0]), t=t.ctypes.data, ticks_per_hour=int(tph),
+                       on_device=1), t
+
+
+class Batch:
+    """sas_batch_create / sas_batch_run / sas_batch_destroy.
+
+    fields: list of (grid, x, y, epoch, t, ticks_per_hour, n_min) with x, y,
+    epoch device arrays that stay alive (and keep their sizes) for the life of
+    the batch.  opts: None or one sas_opts per field."""
+
+    def __init__(self, fields, opts=None, stream=None):
+        n = len(fields)
+        self._keep = []
+        cats = (sas_catalog * n)()
+        grids = (_p * n)()
+        nmin = (ctypes.c_uint32 * n)()
+        for i, (g, x, y, e, t, tph, n_min) in enumerate(fields):
+            c, tt = _device_catalog(x, y, e, t, tph)
+            self._keep += [tt, g, x, y, e]
+            cats[i] = c
+            grids[i] = g.handle
+            nmin[i] = int(n_min)
+        op = None
+        if opts is not None:
+            arr = (sas_opts * n)(*opts)
+            self._keep.append(arr)
+            op = arr
+        h = _p()
+        _check(_lib.sas_batch_create(grids, cats, nmin, n, op, _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_fields = n
+
+    def run(self, stream=None):
+        _check(_lib.sas_batch_run(self._h, _stream_handle(stream)))
+
+    def field_info(self, f: int) -> dict:
+        inf = sas_result_info()
+        _check(_lib.sas_batch_field_info(self._h, int(f), ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in sas_result_info._fields_}
+
+    def candidates(self, f: int):
+        inf = self.field_info(f)
+        nc_v, ni_v = inf["n_candidates"], inf["n_ids"]
+        cands = np.zeros(nc_v, CANDIDATE_DTYPE)
+        ids = np.zeros(ni_v, np.uint32)
+        nc, ni = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.sas_batch_candidates(self._h, int(f), cands.ctypes.data if nc_v else None, nc_v,
+                                         ctypes.byref(nc), ids.ctypes.data if ni_v else None, ni_v,
+                                         ctypes.byref(ni), 0))
+        return cands, ids
+
+    def stats(self):
+        ms, fb = ctypes.c_float(), ctypes.c_uint64()
+        _check(_lib.sas_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(fb)))
+        return ms.value, fb.value
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.sas_batch_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def sas_autotune(grid: Grid, x, y, epoch, t, ticks_per_hour: int, n_min: int,
+                 base: sas_opts | None = None, reps: int = 3, stream=None):
+    """Fastest (superbin, velocity_block) options for this field and their
+    median device time in ms (device arrays x, y, epoch)."""
+    cat, tt = _device_catalog(x, y, epoch, t, ticks_per_hour)
+    best, ms = sas_opts(), ctypes.c_float()
+    _check(_lib.sas_autotune(grid.handle, ctypes.byref(cat), int(n_min),
+                             ctypes.byref(base) if base is not None else None, int(reps),
+                             _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value

@@ -1,0 +1,102 @@
+"""The batched, graph-replayed search gives every field exactly what sas_stack
+gives it, including fields that need the exact fallback."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_26279_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2509_26279_gb300 import sas  # noqa: E402
+
+
+def _dev(cat):
+    d = torch.device("cuda")
+    return (torch.from_numpy(cat.x).to(d), torch.from_numpy(cat.y).to(d),
+            torch.from_numpy(cat.epoch.view(np.int16)).to(d))
+
+
+def _fields(n, seed):
+    """Uneven small fields: epochs 20..150, noise 2%..8% of the full density."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        E = int(rng.integers(20, 151))
+        w = W.scaled(W.decam_tno(), frac_noise=float(rng.uniform(0.02, 0.08)), width_px=int(rng.integers(300, 900)),
+                     height_px=int(rng.integers(300, 900)), n_epochs=E, n_movers=int(rng.integers(10, 40)),
+                     grid_half=int(rng.integers(6, 14)), seed=seed * 100 + i)
+        out.append((w, max(3, -(-E // 4))))
+    return out
+
+
+def _single(grid, cat, n_min):
+    r = sas.stack_catalog(grid, cat, n_min)
+    c, ids = r.candidates()
+    return c, ids, r.info()["n_pairs"]
+
+
+def test_batch_equals_single_field_search():
+    specs = _fields(7, 3)
+    fields, refs = [], []
+    for w, n_min in specs:
+        cat = W.load(w)
+        g = sas.Grid(w.grid)
+        x, y, e = _dev(cat)
+        fields.append((g, x, y, e, cat.t, cat.ticks_per_hour, n_min))
+        refs.append(_single(g, cat, n_min))
+    b = sas.Batch(fields)
+    for rep in range(2):  # two replays of the same graph
+        b.run()
+        for f, (c_ref, ids_ref, pairs_ref) in enumerate(refs):
+            c, ids = b.candidates(f)
+            assert np.array_equal(c, c_ref), (rep, f)
+            assert np.array_equal(ids, ids_ref), (rep, f)
+            assert b.field_info(f)["n_pairs"] == pairs_ref
+    ms, fallbacks = b.stats()
+    assert ms > 0 and fallbacks == 0
+    b.destroy()
+
+
+def test_batch_field_fallback_is_exact():
+    """A field with far more candidates than the batch's per-field capacity
+    (8192) is recomputed on the single-field path; the others stay batched."""
+    w = W.tiny()
+    cat = W.load(w)
+    g = sas.Grid(w.grid)
+    x, y, e = _dev(cat)
+    w2 = _fields(1, 9)[0][0]
+    cat2 = W.load(w2)
+    g2 = sas.Grid(w2.grid)
+    x2, y2, e2 = _dev(cat2)
+    b = sas.Batch([(g, x, y, e, cat.t, cat.ticks_per_hour, 2),
+                   (g2, x2, y2, e2, cat2.t, cat2.ticks_per_hour, 12)])
+    b.run()
+    ref = oracle.stack(cat, w.grid, 2)
+    c, ids = b.candidates(0)
+    assert len(ref.cands) > 8192 and len(c) == len(ref.cands)
+    assert np.array_equal(c["count"].astype(np.int64), ref.cands["distinct"].astype(np.int64))
+    assert np.array_equal(ids.astype(np.int64), ref.ids.astype(np.int64))
+    c2, ids2, _ = _single(g2, cat2, 12)
+    cb, idsb = b.candidates(1)
+    assert np.array_equal(cb, c2) and np.array_equal(idsb, ids2)
+    assert b.stats()[1] == 1
+    b.destroy()
+
+
+def test_autotune_returns_a_valid_faster_config():
+    w = W.scaled(W.decam_tno(), frac_noise=0.05, width_px=700, height_px=500, n_movers=40,
+                 grid_half=12, seed=21)
+    cat = W.load(w)
+    g = sas.Grid(w.grid)
+    x, y, e = _dev(cat)
+    best, ms = sas.sas_autotune(g, x, y, e, cat.t, cat.ticks_per_hour, 10, reps=2)
+    assert best.superbin in (1, 2, 3) and best.velocity_block in (1, 2, 4, 8) and ms > 0
+    r = sas.stack_catalog(g, cat, 10, opts=best)
+    c, ids = r.candidates()
+    c0, ids0, _ = _single(g, cat, 10)
+    assert np.array_equal(c, c0) and np.array_equal(ids, ids0)
