@@ -28,6 +28,15 @@ struct sas_result {
   sas_candidate* d_cands;
   uint32_t* d_ids;
   sas_result_info info;
+  // The search's bucketed catalog, per-epoch counts and shift tables, kept so
+  // that stamps can be cut from the same search (sas_stamps).
+  Det* d_dets;
+  uint32_t* d_boff;
+  uint32_t* d_ecount;
+  int32_t* d_sxt;
+  int32_t* d_syt;
+  SearchGeom g;
+  CoarseGeom cg;
 };
 
 namespace {
@@ -252,15 +261,22 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     CK(sc.alloc(&d_dt, E), "alloc dt");
     CK(sc.alloc(&d_t0, 1), "alloc t0");
     CK(cudaMemcpyAsync(d_t, cat->t, E * 8, cudaMemcpyHostToDevice, s), "copy t");
-    CK(sc.alloc(&d_ecount, E), "alloc ecount");
+    CK(cudaMallocAsync((void**)&d_ecount, (size_t)E * 4, s), "alloc ecount");
+    res->d_ecount = d_ecount;
     CK(sc.alloc(&d_bcount, nb), "alloc bucket counts");
-    CK(sc.alloc(&d_boff, nb + 1), "alloc bucket offsets");
+    CK(cudaMallocAsync((void**)&d_boff, (nb + 1) * 4, s), "alloc bucket offsets");
+    res->d_boff = d_boff;
     CK(sc.alloc(&d_cursor, nb), "alloc cursor");
     CK(sc.alloc(&d_scan, scan_scratch_elems(nb)), "alloc scan scratch");
     CK(sc.alloc(&d_bof, n), "alloc bucket_of");
-    CK(sc.alloc(&d_dets, n), "alloc dets");
-    CK(sc.alloc(&d_sxt, (size_t)d.nvx * E), "alloc sx table");
-    CK(sc.alloc(&d_syt, (size_t)d.nvy * E), "alloc sy table");
+    CK(cudaMallocAsync((void**)&d_dets, n * sizeof(Det), s), "alloc dets");
+    res->d_dets = d_dets;
+    CK(cudaMallocAsync((void**)&d_sxt, (size_t)d.nvx * E * 4, s), "alloc sx table");
+    res->d_sxt = d_sxt;
+    CK(cudaMallocAsync((void**)&d_syt, (size_t)d.nvy * E * 4, s), "alloc sy table");
+    res->d_syt = d_syt;
+    res->g = g;
+    res->cg = cg;
     CK(sc.alloc(&d_small, 4), "alloc counters");
     CK(sc.alloc(&d_small64, 4), "alloc counters64");
     CK(cudaMemsetAsync(d_ecount, 0, E * 4, s), "memset");
@@ -407,6 +423,9 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   if (rc != SAS_OK) {
     if (res->d_ids) cudaFreeAsync(res->d_ids, s);
     if (res->d_cands) cudaFreeAsync(res->d_cands, s);
+    for (void* p : {(void*)res->d_dets, (void*)res->d_boff, (void*)res->d_ecount, (void*)res->d_sxt,
+                    (void*)res->d_syt})
+      if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);
     delete res;
     return rc;
@@ -447,8 +466,9 @@ int sas_candidates(const sas_result* r, sas_candidate* out, uint64_t cap, uint64
 
 void sas_result_free(sas_result* r) {
   if (!r) return;
-  if (r->d_cands) cudaFree(r->d_cands);
-  if (r->d_ids) cudaFree(r->d_ids);
+  for (void* p : {(void*)r->d_cands, (void*)r->d_ids, (void*)r->d_dets, (void*)r->d_boff,
+                  (void*)r->d_ecount, (void*)r->d_sxt, (void*)r->d_syt})
+    if (p) cudaFree(p);
   delete r;
 }
 
