@@ -17,6 +17,9 @@ Network (input x = count / 16):
   conv3 32->32 (11 -> 9), ReLU; flatten in (channel, row, column) order;
   fc1 2592 -> 64, ReLU; fc2 64 -> 1 (the logit).
 Loss: mean binary cross-entropy with logits.
+Arithmetic: float64 throughout.  forward/gradients take an optional `store`
+rounding applied where the GPU stores an activation; bf16_round there is the
+network's stated precision (BF16 activations, wide accumulation).
 Flat parameter layout (float32 on the GPU, float64 here), in this order:
   conv1.w [32,9,3,3], conv1.b [32], conv2.w [32,32,3,3], conv2.b [32],
   conv3.w [32,32,3,3], conv3.b [32], fc1.w [64,2592], fc1.b [64],
@@ -122,15 +125,21 @@ def _conv_back(x, w, g):
     return dx, dw, g.sum(axis=(0, 2, 3))
 
 
-def forward(flat, stamp_counts):
-    """Logits [B] and the activations needed by backward."""
+def forward(flat, stamp_counts, store=None):
+    """Logits [B] and the activations needed by backward.
+
+    store: None for exact float64 activations, or a function applied to every
+    stored activation (input x0, a1, a2, a3, fc1 output a4) -- bf16_round gives
+    the network's stated arithmetic (BF16 activations, wide accumulation); all
+    arithmetic stays float64."""
+    st = store if store is not None else (lambda a: a)
     p = unflatten(np.asarray(flat, np.float64))
-    x0 = np.asarray(stamp_counts, np.float64) / 16.0
-    z1 = _conv(x0, p["conv1.w"], p["conv1.b"]); a1 = np.maximum(z1, 0)
-    z2 = _conv(a1, p["conv2.w"], p["conv2.b"]); a2 = np.maximum(z2, 0)
-    z3 = _conv(a2, p["conv3.w"], p["conv3.b"]); a3 = np.maximum(z3, 0)
+    x0 = st(np.asarray(stamp_counts, np.float64) / 16.0)
+    z1 = _conv(x0, p["conv1.w"], p["conv1.b"]); a1 = st(np.maximum(z1, 0))
+    z2 = _conv(a1, p["conv2.w"], p["conv2.b"]); a2 = st(np.maximum(z2, 0))
+    z3 = _conv(a2, p["conv3.w"], p["conv3.b"]); a3 = st(np.maximum(z3, 0))
     f = a3.reshape(len(x0), -1)
-    z4 = f @ p["fc1.w"].T + p["fc1.b"]; a4 = np.maximum(z4, 0)
+    z4 = f @ p["fc1.w"].T + p["fc1.b"]; a4 = st(np.maximum(z4, 0))
     logit = a4 @ p["fc2.w"] + p["fc2.b"][0]
     return logit, dict(x0=x0, a1=a1, a2=a2, a3=a3, f=f, a4=a4, p=p)
 
@@ -142,9 +151,11 @@ def bce_with_logits(logit, y):
     return float(np.mean(np.maximum(logit, 0) - logit * y + np.log1p(np.exp(-np.abs(logit)))))
 
 
-def gradients(flat, stamp_counts, y):
-    """(loss, flat gradient of the mean BCE loss)."""
-    logit, a = forward(flat, stamp_counts)
+def gradients(flat, stamp_counts, y, store=None):
+    """(loss, flat gradient of the mean BCE loss).  With store (see forward),
+    back-propagation runs through the stored activations: their ReLU masks
+    and their values in the weight gradients."""
+    logit, a = forward(flat, stamp_counts, store)
     p = a["p"]
     B = len(logit)
     y = np.asarray(y, np.float64)
@@ -174,8 +185,17 @@ def adam_step(flat, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def bf16_round(a):
-    """Round float32 values to the nearest bfloat16 (ties to even)."""
+    """Round values to float32, then to the nearest bfloat16 (ties to even);
+    returns float32 (finite inputs)."""
     a = np.asarray(a, np.float32)
     u = a.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32)
+
+
+def bf16_store(a):
+    """Round float64 values directly to the nearest bfloat16 (8 significant
+    bits, ties to even); returns float64.  The `store` rounding of forward and
+    gradients for the network's BF16 activations (normal range)."""
+    m, e = np.frexp(np.asarray(a, np.float64))
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)

@@ -118,3 +118,58 @@ def test_stamps_match_brute_force_counts():
                         if 0 <= kx2 < grid.nvx and 0 <= ky2 < grid.nvy:
                             want = counts.get((ky2 * grid.nvx + kx2, xx, yy), 0)
                         assert st[c, (dy + 1) * 3 + dx + 1, i, j] == want
+
+
+def test_bf16_store_rounds_to_eight_bits():
+    a = np.array([0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -8 + 2 ** -30, -3.14159, 257.0, 259.0])
+    r = vetter.bf16_store(a)
+    assert list(r[:4]) == [0.0, 1.0, 1.0, 1.0 + 2 ** -7]
+    assert r[4] == 1.0 + 2 ** -7            # just above the tie: rounds up (no double rounding)
+    assert r[5] == -3.140625 and r[6] == 256.0 and r[7] == 260.0
+    # on float32 inputs it agrees with the float32 -> bfloat16 rounding
+    x = np.random.default_rng(0).normal(0, 10, 10000).astype(np.float32)
+    assert np.array_equal(vetter.bf16_store(x.astype(np.float64)), vetter.bf16_round(x).astype(np.float64))
+
+
+def _shift_network(seed):
+    """Weights under which every activation is a small integer, exactly
+    representable in BF16: each conv output channel copies one input channel
+    at one tap (weight 1, bias 0); each fc1 unit sums a few features."""
+    rng = np.random.default_rng(seed)
+    p = {name: np.zeros(shape) for name, shape in vetter.SHAPES}
+    for name, cin in (("conv1.w", 9), ("conv2.w", 32), ("conv3.w", 32)):
+        for o in range(32):
+            p[name][o, rng.integers(0, cin), rng.integers(0, 3), rng.integers(0, 3)] = 1.0
+    for j in range(64):
+        p["fc1.w"][j, rng.choice(2592, 20, replace=False)] = 1.0
+    p["fc2.w"][:] = rng.choice([-0.5, 0.25, 1.0], 64)
+    p["fc2.b"][0] = -3.0
+    return vetter.flatten(p)
+
+
+def test_store_rounding_is_a_no_op_on_representable_activations():
+    """With exactly representable activations, BF16 storage changes nothing:
+    the rounded forward and backward equal the exact (finite-difference
+    pinned) ones bit for bit -- so the rounding touches activations only, not
+    weights or deltas."""
+    flat = _shift_network(5)
+    rng = np.random.default_rng(6)
+    st = 16 * rng.integers(0, 3, size=(4, 9, 15, 15))
+    y = np.array([1.0, 0.0, 0.0, 1.0])
+    l0, a0 = vetter.forward(flat, st)
+    l1, a1 = vetter.forward(flat, st, vetter.bf16_store)
+    assert np.array_equal(l0, l1)
+    assert a0["a4"].max() > 0 and a0["a4"].max() < 256
+    g0 = vetter.gradients(flat, st, y)
+    g1 = vetter.gradients(flat, st, y, vetter.bf16_store)
+    assert g0[0] == g1[0] and np.array_equal(g0[1], g1[1])
+
+
+def test_store_rounding_applies_at_every_stored_activation():
+    flat = _small_params(8)
+    st = np.random.default_rng(3).integers(0, 300, size=(3, 9, 15, 15))
+    _, a = vetter.forward(flat, st, vetter.bf16_store)
+    _, ex = vetter.forward(flat, st)
+    for k in ("x0", "a1", "a2", "a3", "a4"):
+        assert np.array_equal(a[k], vetter.bf16_store(a[k])), k
+        assert not np.array_equal(a[k], ex[k]), k
