@@ -267,6 +267,87 @@ int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
 int sas_cell_counts_noalloc(const sas_grid* grid, const sas_catalog* cat, const uint32_t* cells,
                             uint64_t n_cells, uint32_t* distinct, uint32_t* raw, void* stream);
 
+/* ---- Candidate vetter ---------------------------------------------------------
+ *
+ * Filtering the search results better is the paper's suggested route to fainter
+ * objects (Sec. 4).  The vetter scores each candidate with a small CNN from
+ * its count stamp, so the search can run at a lower n_min.
+ *
+ * Stamp of candidate (v_idx, bx, by), kx = v_idx % nvx, ky = v_idx / nvx: a
+ * [9][15][15] uint16 array.  Plane q = (dy + 1) * 3 + (dx + 1), dx, dy in
+ * {-1, 0, 1}, is the distinct-epoch histogram (Sec. 2.1 step 2) of lattice
+ * point (kx + dx, ky + dy) over bins (bx - 7 + j, by - 7 + i) at element
+ * (i, j).  Points off the lattice (the whole lattice, not only the searched
+ * v range or annulus) and bins off the domain count 0.  Counts saturate at
+ * 65535. */
+
+/* Stamps of candidates [first, first + count) of a result, in output order,
+ * into out: a device array of count * 9 * 15 * 15 uint16 owned by the
+ * caller.  Runs on the current device (the result's) and is asynchronous on
+ * `stream`.  Errors: SAS_ERR_ARG (null result, range beyond n_candidates,
+ * null out with count > 0), SAS_ERR_CUDA. */
+int sas_stamps(const sas_result* result, uint64_t first, uint64_t count, uint16_t* out,
+               void* stream);
+
+/* The network (input = count / 16):
+ *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),
+ *   ReLU; conv3 32 -> 32 (11 -> 9), ReLU; flatten in (channel, row, column)
+ *   order; fc1 2592 -> 64, ReLU; fc2 64 -> 1 = logit (score of a real mover).
+ * Loss: mean binary cross-entropy with logits.
+ * Parameters: 187,137 FP32 master values in this flat order:
+ *   conv1.w [32][9][3][3], conv1.b [32], conv2.w [32][32][3][3], conv2.b [32],
+ *   conv3.w [32][32][3][3], conv3.b [32], fc1.w [64][2592], fc1.b [64],
+ *   fc2.w [64], fc2.b [1].
+ * Arithmetic: the kernels use BF16 copies of the weights (round to nearest
+ * even), round the input and every stored activation to BF16 and accumulate
+ * in FP32; deltas and gradients are FP32; Adam updates the FP32 masters and
+ * refreshes the BF16 copies.  Gradients are bit-reproducible for a batch.
+ * A vetter lives on the device that was current at sas_vet_create; every call
+ * makes that device current for its duration. */
+#define SAS_VET_MAX_BATCH 8192u
+typedef struct sas_vet sas_vet;
+
+uint64_t sas_vet_num_params(void);
+
+/* Allocate a vetter whose training batches hold up to max_batch stamps
+ * (1..SAS_VET_MAX_BATCH; about 72 KB of device memory per stamp).  Parameters
+ * start at zero; Adam starts with beta1 0.9, beta2 0.999, eps 1e-8.
+ * Errors: SAS_ERR_ARG, SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_vet_create(int device, uint32_t max_batch, sas_vet** out);
+int sas_vet_destroy(sas_vet* vetter);
+int sas_vet_set_adam(sas_vet* vetter, float beta1, float beta2, float eps);
+
+/* Checkpoint: host arrays of sas_vet_num_params() floats.  set_state loads
+ * the masters (and the Adam moments and step count, or resets them when m and
+ * v are NULL) and synchronizes; get_state copies out any non-NULL argument. */
+int sas_vet_set_state(sas_vet* vetter, const float* params, const float* m, const float* v,
+                      uint64_t step);
+int sas_vet_get_state(const sas_vet* vetter, float* params, float* m, float* v, uint64_t* step);
+/* The BF16 working copy of the parameters (flat order, raw bits), to host. */
+int sas_vet_get_bf16(const sas_vet* vetter, uint16_t* out);
+
+/* logits[i] of n stamps (device arrays: stamps [n][9][15][15] uint16,
+ * logits [n] float); any n, processed in batches of max_batch.  Asynchronous
+ * on `stream`. */
+int sas_vet_forward(sas_vet* vetter, const uint16_t* stamps, uint64_t n, float* logits,
+                    void* stream);
+
+/* Gradient (device float [sas_vet_num_params()]) of the mean BCE loss of n
+ * (1..max_batch) stamps with labels (device float [n], 1 = mover, 0 = not)
+ * at the current parameters; the loss goes to *loss (device float, may be
+ * NULL).  Asynchronous on `stream`. */
+int sas_vet_gradients(sas_vet* vetter, const uint16_t* stamps, const float* labels, uint32_t n,
+                      float* grad, float* loss, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) with a caller's gradient (device float
+ * [sas_vet_num_params()]), learning rate lr >= 0.  Asynchronous. */
+int sas_vet_apply_gradients(sas_vet* vetter, const float* grad, float lr, void* stream);
+
+/* sas_vet_gradients followed by sas_vet_apply_gradients on an internal
+ * gradient buffer.  Asynchronous. */
+int sas_vet_train_step(sas_vet* vetter, const uint16_t* stamps, const float* labels, uint32_t n,
+                       float lr, float* loss, void* stream);
+
 /* Measurement utility: throughput of conflict-free 32-bit shared-memory
  * atomicAdd on every SM of the current device, in operations per second,
  * measured with CUDA events over `iters` operations per thread; this is the

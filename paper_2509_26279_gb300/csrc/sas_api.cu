@@ -464,6 +464,20 @@ int sas_candidates(const sas_result* r, sas_candidate* out, uint64_t cap, uint64
   return SAS_OK;
 }
 
+int sas_stamps(const sas_result* r, uint64_t first, uint64_t count, uint16_t* out, void* stream) {
+  if (!r) return fail(SAS_ERR_ARG, "null result");
+  const uint64_t nc = r->info.n_candidates;
+  if (first > nc || count > nc - first)
+    return fail(SAS_ERR_ARG, "candidates [%llu, %llu) outside the result's %llu", (unsigned long long)first,
+                (unsigned long long)(first + count), (unsigned long long)nc);
+  if (count == 0) return SAS_OK;
+  if (!out) return fail(SAS_ERR_ARG, "null stamp buffer");
+  cudaError_t e = launch_stamps(r->d_cands + first, count, r->g, r->cg, r->d_dets, r->d_boff, r->d_ecount,
+                                r->d_sxt, r->d_syt, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stamps");
+  return SAS_OK;
+}
+
 void sas_result_free(sas_result* r) {
   if (!r) return;
   for (void* p : {(void*)r->d_cands, (void*)r->d_ids, (void*)r->d_dets, (void*)r->d_boff,

@@ -197,6 +197,13 @@ cudaError_t launch_gather_ids(const Key* keys, uint32_t n, const unsigned long l
 cudaError_t launch_write_candidates(const Key* keys, uint32_t n, const unsigned long long* id_off,
                                     sas_candidate* out, cudaStream_t s);
 
+// sas_stamps.cu: 9 x 15 x 15 distinct-epoch count stamps of n candidates, u16
+// [n][9][15][15], from a search's bucketed catalog and shift tables.
+cudaError_t launch_stamps(const sas_candidate* cands, uint64_t n, const SearchGeom& g,
+                          const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
+                          const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
+                          uint16_t* out, cudaStream_t s);
+
 // sas_probe.cu
 cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
 

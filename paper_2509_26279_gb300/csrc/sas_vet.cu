@@ -1,0 +1,788 @@
+// Candidate vetter: a small CNN that scores a candidate from its count stamp,
+// trained and run on the GPU (BF16 weights and activations, FP32 accumulation).
+//
+// Filtering the search results better is the paper's own suggestion for going
+// fainter (Sec. 4); this network is that filter.  Network (input = count / 16):
+//   conv1 9->32 3x3 valid + ReLU (15 -> 13), conv2 32->32 (13 -> 11) + ReLU,
+//   conv3 32->32 (11 -> 9) + ReLU, flatten (channel, row, column),
+//   fc1 2592 -> 64 + ReLU, fc2 64 -> 1 = logit;  loss: mean BCE with logits.
+// Flat parameter order: conv1.w [32,9,3,3], conv1.b, conv2.w [32,32,3,3],
+// conv2.b, conv3.w, conv3.b, fc1.w [64,2592], fc1.b, fc2.w [64], fc2.b.
+//
+// Numerics: weights are used as BF16 copies of FP32 master values; every stored
+// activation (input, conv outputs, fc1 output) is rounded to BF16; products are
+// exact in FP32 and accumulate in FP32.  Back-propagated deltas and weight
+// gradients are FP32.  Weight gradients are summed per block over a fixed
+// stamp-to-block assignment and then over blocks in a fixed order, so a
+// gradient is bit-reproducible for a given batch.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sas_internal.cuh"
+
+struct sas_vet {
+  int device;
+  uint32_t max_batch;
+  uint64_t step;
+  float beta1, beta2, eps;
+  // parameters
+  float* master;
+  float* m;
+  float* v;
+  float* grad;
+  __nv_bfloat16* wb;     // BF16 copy in the flat order
+  __nv_bfloat16* wf1t;   // BF16 copy of fc1.w transposed to [2592][64]
+  // activations and deltas of one batch
+  __nv_bfloat16* a1;     // [B][32][13][13]
+  __nv_bfloat16* a2;     // [B][32][11][11]
+  __nv_bfloat16* a3;     // [B][2592]
+  __nv_bfloat16* a4;     // [B][64]
+  float* logits;         // [B]
+  float* glogit;         // [B]
+  float* g4;             // [B][64]
+  float* g3;             // [B][2592]
+  float* g2;             // [B][32][11][11]
+  float* g1;             // [B][32][13][13]
+  float* partial;        // per-block weight-gradient partial sums
+  float* loss;           // [1]
+};
+
+namespace sas {
+namespace vet {
+
+constexpr int kS = 15, kQ = 9, kCh = 32;
+constexpr int kH1 = 13, kH2 = 11, kH3 = 9;
+constexpr int kF = kCh * kH3 * kH3;  // 2592
+constexpr int kHid = 64;
+constexpr int kW1 = 0, kB1 = kW1 + kCh * kQ * 9, kW2 = kB1 + kCh, kB2 = kW2 + kCh * kCh * 9;
+constexpr int kW3 = kB2 + kCh, kB3 = kW3 + kCh * kCh * 9, kWf1 = kB3 + kCh, kBf1 = kWf1 + kHid * kF;
+constexpr int kWf2 = kBf1 + kHid, kBf2 = kWf2 + kHid, kNParams = kBf2 + 1;
+static_assert(kNParams == 187137, "parameter layout");
+
+constexpr int kBackBlocks = 256;      // blocks (and partial sums) of the conv backward kernels
+constexpr int kPartialStride = kCh * kCh * 9 + kCh;  // >= parts * weights + biases of any layer
+static_assert(kPartialStride >= 3 * kCh * kQ * 9 + kCh, "partial stride");
+
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// ---- forward: the three convolutions of one stamp per block iteration ---------
+
+constexpr int kFwdThreads = 512;
+
+// out[o][p] = relu(b[o] + sum_{c,tap} in[c][p + tap] * w[o][c][tap]), p over the
+// HO x HO output; a warp owns 8 output channels and 32 pixels at a time.
+template <int C, int HI>
+__device__ __forceinline__ void conv_fwd(const float* in, const float* ws, const float* bias,
+                                         float* out_s, __nv_bfloat16* out_g) {
+  constexpr int HO = HI - 2, P = HO * HO;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int o0 = (warp & 3) * 8;
+  const int pstride = (kFwdThreads / 128) * 32;
+  for (int p = (warp >> 2) * 32 + lane; p < P; p += pstride) {
+    const int y = p / HO, x = p - y * HO;
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = bias[o0 + j];
+    for (int c = 0; c < C; ++c) {
+      const float* ip = in + c * HI * HI + y * HI + x;
+      const float* wp = ws + c * 9 * kCh + o0;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const float a = ip[(tap / 3) * HI + tap % 3];
+        const float4 w0 = *reinterpret_cast<const float4*>(wp + tap * kCh);
+        const float4 w1 = *reinterpret_cast<const float4*>(wp + tap * kCh + 4);
+        acc[0] = fmaf(a, w0.x, acc[0]); acc[1] = fmaf(a, w0.y, acc[1]);
+        acc[2] = fmaf(a, w0.z, acc[2]); acc[3] = fmaf(a, w0.w, acc[3]);
+        acc[4] = fmaf(a, w1.x, acc[4]); acc[5] = fmaf(a, w1.y, acc[5]);
+        acc[6] = fmaf(a, w1.z, acc[6]); acc[7] = fmaf(a, w1.w, acc[7]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float r = bf(fmaxf(acc[j], 0.f));
+      if (out_s) out_s[(o0 + j) * P + p] = r;
+      if (out_g) out_g[(o0 + j) * P + p] = __float2bfloat16_rn(r);
+    }
+  }
+}
+
+// Weights of a conv layer into shared memory as float [c][tap][o].
+template <int C>
+__device__ void load_conv_w(const __nv_bfloat16* w, float* ws) {
+  for (int i = threadIdx.x; i < kCh * C * 9; i += blockDim.x) {
+    const int o = i / (C * 9), r = i - o * C * 9;
+    ws[r * kCh + o] = ld(w + i);  // r = c * 9 + tap
+  }
+}
+
+constexpr int kFwdSmemFloats = kCh * kQ * 9 + 2 * kCh * kCh * 9 + 3 * kCh + kQ * kS * kS +
+                               kCh * kH1 * kH1 + kCh * kH2 * kH2;
+
+__global__ void __launch_bounds__(kFwdThreads) k_conv_fwd(const uint16_t* __restrict__ stamps,
+                                                          uint32_t n, const __nv_bfloat16* __restrict__ wb,
+                                                          __nv_bfloat16* a1g, __nv_bfloat16* a2g,
+                                                          __nv_bfloat16* __restrict__ a3g) {
+  extern __shared__ __align__(16) float sm[];
+  float* w1s = sm;
+  float* w2s = w1s + kCh * kQ * 9;
+  float* w3s = w2s + kCh * kCh * 9;
+  float* bs = w3s + kCh * kCh * 9;
+  float* x0 = bs + 3 * kCh;
+  float* a1 = x0 + kQ * kS * kS;
+  float* a2 = a1 + kCh * kH1 * kH1;
+  load_conv_w<kQ>(wb + kW1, w1s);
+  load_conv_w<kCh>(wb + kW2, w2s);
+  load_conv_w<kCh>(wb + kW3, w3s);
+  if (threadIdx.x < 3 * kCh) {
+    const int l = threadIdx.x / kCh, o = threadIdx.x % kCh;
+    bs[threadIdx.x] = ld(wb + (l == 0 ? kB1 : l == 1 ? kB2 : kB3) + o);
+  }
+  for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+    const uint16_t* st = stamps + (size_t)b * kQ * kS * kS;
+    for (int i = threadIdx.x; i < kQ * kS * kS; i += blockDim.x) x0[i] = bf((float)st[i] * 0.0625f);
+    __syncthreads();
+    conv_fwd<kQ, kS>(x0, w1s, bs, a1, a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr);
+    __syncthreads();
+    conv_fwd<kCh, kH1>(a1, w2s, bs + kCh, a2, a2g ? a2g + (size_t)b * kCh * kH2 * kH2 : nullptr);
+    __syncthreads();
+    conv_fwd<kCh, kH2>(a2, w3s, bs + 2 * kCh, nullptr, a3g + (size_t)b * kF);
+    __syncthreads();
+  }
+}
+
+// ---- forward: fc1 (+ReLU) and fc2 for 32 stamps per block --------------------
+
+constexpr int kFcTB = 32, kFcKC = 64;
+
+__global__ void __launch_bounds__(256) k_fc_fwd(const __nv_bfloat16* __restrict__ a3g, uint32_t n,
+                                                const __nv_bfloat16* __restrict__ wf1t,
+                                                const __nv_bfloat16* __restrict__ wb,
+                                                __nv_bfloat16* a4g, float* __restrict__ logits) {
+  __shared__ __align__(16) float As[kFcTB][kFcKC + 1];
+  __shared__ __align__(16) float Bs[kFcKC][kHid];
+  const int t = threadIdx.x, jq = t & 15, sg = t >> 4;
+  const uint32_t b0 = blockIdx.x * kFcTB;
+  float acc[2][4] = {};
+  for (int k0 = 0; k0 < kF; k0 += kFcKC) {
+    const int kc = min(kFcKC, kF - k0);
+    for (int i = t; i < kFcTB * kFcKC; i += 256) {
+      const int s = i / kFcKC, k = i % kFcKC;
+      As[s][k] = (b0 + s < n && k < kc) ? ld(a3g + (size_t)(b0 + s) * kF + k0 + k) : 0.f;
+    }
+    for (int i = t; i < kFcKC * kHid; i += 256) {
+      const int k = i / kHid;
+      Bs[k][i % kHid] = k < kc ? ld(wf1t + (size_t)(k0 + k) * kHid + i % kHid) : 0.f;
+    }
+    __syncthreads();
+    for (int k = 0; k < kc; ++k) {
+      const float4 w = *reinterpret_cast<const float4*>(&Bs[k][jq * 4]);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const float a = As[sg * 2 + s][k];
+        acc[s][0] = fmaf(a, w.x, acc[s][0]); acc[s][1] = fmaf(a, w.y, acc[s][1]);
+        acc[s][2] = fmaf(a, w.z, acc[s][2]); acc[s][3] = fmaf(a, w.w, acc[s][3]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const uint32_t b = b0 + sg * 2 + s;
+    float part = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = jq * 4 + jj;
+      const float a = bf(fmaxf(acc[s][jj] + ld(wb + kBf1 + j), 0.f));
+      if (a4g && b < n) a4g[(size_t)b * kHid + j] = __float2bfloat16_rn(a);
+      part = fmaf(a, ld(wb + kWf2 + j), part);
+    }
+    // the 16 threads of a stamp are 16 consecutive lanes
+    for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (jq == 0 && b < n) logits[b] = part + ld(wb + kBf2);
+  }
+}
+
+// ---- loss, fc2 gradients, fc1 output deltas ------------------------------------
+
+// One block: per-stamp loss and d loss / d logit; loss mean; fc2 gradients.
+constexpr int kLossThreads = 1024;
+
+__global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ logits,
+                                                       const float* __restrict__ labels, uint32_t n,
+                                                       const __nv_bfloat16* __restrict__ a4g,
+                                                       float* __restrict__ glogit,
+                                                       float* __restrict__ grad, float* __restrict__ loss) {
+  __shared__ float red[kLossThreads];
+  const int t = threadIdx.x;
+  const float inv_n = 1.f / (float)n;
+  float l = 0.f;
+  for (uint32_t b = t; b < n; b += blockDim.x) {
+    const float z = logits[b], y = labels[b];
+    l += fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
+    glogit[b] = (1.f / (1.f + expf(-z)) - y) * inv_n;
+  }
+  red[t] = l;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] += red[t + s];
+    __syncthreads();
+  }
+  if (t == 0) *loss = red[0] * inv_n;
+  __syncthreads();
+  // fc2.w[j] = sum_b glogit[b] * a4[b][j]; fc2.b = sum_b glogit[b]
+  // 16 parts of the batch per hidden unit, combined in a fixed order
+  const int j = t & 63, part = t >> 6;
+  float acc = 0.f, accb = 0.f;
+  for (uint32_t b = part; b < n; b += 16) {
+    const float g = glogit[b];
+    acc = fmaf(g, ld(a4g + (size_t)b * kHid + j), acc);
+    accb += g;
+  }
+  red[t] = acc;
+  __syncthreads();
+  if (t < 64) {
+    float s = 0.f;
+    for (int p = 0; p < 16; ++p) s += red[p * 64 + t];
+    grad[kWf2 + t] = s;
+  }
+  __syncthreads();
+  red[t] = (j == 0) ? accb : 0.f;
+  __syncthreads();
+  if (t == 0) {
+    float s = 0.f;
+    for (int p = 0; p < 16; ++p) s += red[p * 64];
+    grad[kBf2] = s;
+  }
+}
+
+// g4[b][j] = glogit[b] * w2[j] * (a4[b][j] > 0)
+__global__ void k_g4(const float* __restrict__ glogit, const __nv_bfloat16* __restrict__ a4g,
+                     const __nv_bfloat16* __restrict__ wb, uint32_t n, float* __restrict__ g4) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)n * kHid) return;
+  const int j = (int)(i % kHid);
+  g4[i] = ld(a4g + i) > 0.f ? glogit[i / kHid] * ld(wb + kWf2 + j) : 0.f;
+}
+
+// fc1.w[j][k] = sum_b g4[b][j] * a3[b][k];  fc1.b[j] = sum_b g4[b][j].
+// Block: 32 columns k, all 64 rows j, whole batch.
+__global__ void __launch_bounds__(256) k_fc1_dw(const float* __restrict__ g4,
+                                                const __nv_bfloat16* __restrict__ a3g, uint32_t n,
+                                                float* __restrict__ grad) {
+  __shared__ __align__(16) float Gs[32][kHid];
+  __shared__ float Fs[32][33];
+  const int t = threadIdx.x, jq = t & 15, kp = t >> 4;
+  const int k0 = blockIdx.x * 32;
+  float acc[4][2] = {}, accb[4] = {};
+  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+    for (int i = t; i < 32 * kHid; i += 256) {
+      const uint32_t b = b0 + i / kHid;
+      Gs[i / kHid][i % kHid] = b < n ? g4[(size_t)b * kHid + i % kHid] : 0.f;
+    }
+    for (int i = t; i < 32 * 32; i += 256) {
+      const uint32_t b = b0 + i / 32;
+      const int k = k0 + i % 32;
+      Fs[i / 32][i % 32] = (b < n && k < kF) ? ld(a3g + (size_t)b * kF + k) : 0.f;
+    }
+    __syncthreads();
+    for (int bb = 0; bb < 32; ++bb) {
+      const float4 g = *reinterpret_cast<const float4*>(&Gs[bb][jq * 4]);
+      const float f0 = Fs[bb][kp * 2], f1 = Fs[bb][kp * 2 + 1];
+      acc[0][0] = fmaf(g.x, f0, acc[0][0]); acc[0][1] = fmaf(g.x, f1, acc[0][1]);
+      acc[1][0] = fmaf(g.y, f0, acc[1][0]); acc[1][1] = fmaf(g.y, f1, acc[1][1]);
+      acc[2][0] = fmaf(g.z, f0, acc[2][0]); acc[2][1] = fmaf(g.z, f1, acc[2][1]);
+      acc[3][0] = fmaf(g.w, f0, acc[3][0]); acc[3][1] = fmaf(g.w, f1, acc[3][1]);
+      accb[0] += g.x; accb[1] += g.y; accb[2] += g.z; accb[3] += g.w;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int j = jq * 4 + jj;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = k0 + kp * 2 + kk;
+      if (k < kF) grad[kWf1 + (size_t)j * kF + k] = acc[jj][kk];
+    }
+    if (blockIdx.x == 0 && kp == 0) grad[kBf1 + j] = accb[jj];
+  }
+}
+
+// g3[b][k] = (sum_j g4[b][j] * fc1.w[j][k]) * (a3[b][k] > 0).
+// Block: 64 columns k x 32 stamps.
+__global__ void __launch_bounds__(256) k_fc1_dx(const float* __restrict__ g4,
+                                                const __nv_bfloat16* __restrict__ wb,
+                                                const __nv_bfloat16* __restrict__ a3g, uint32_t n,
+                                                float* __restrict__ g3) {
+  __shared__ float Gs[32][kHid + 1];
+  __shared__ float Ws[kHid][64];
+  const int t = threadIdx.x, kk = t & 63, bg = t >> 6;
+  const int k0 = blockIdx.x * 64;
+  const uint32_t b0 = blockIdx.y * 32;
+  for (int i = t; i < 32 * kHid; i += 256) {
+    const uint32_t b = b0 + i / kHid;
+    Gs[i / kHid][i % kHid] = b < n ? g4[(size_t)b * kHid + i % kHid] : 0.f;
+  }
+  for (int i = t; i < kHid * 64; i += 256) {
+    const int j = i / 64, k = k0 + i % 64;
+    Ws[j][i % 64] = k < kF ? ld(wb + kWf1 + (size_t)j * kF + k) : 0.f;
+  }
+  __syncthreads();
+  float acc[8] = {};
+  for (int j = 0; j < kHid; ++j) {
+    const float w = Ws[j][kk];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[s] = fmaf(Gs[bg * 8 + s][j], w, acc[s]);
+  }
+  const int k = k0 + kk;
+  if (k >= kF) return;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const uint32_t b = b0 + bg * 8 + s;
+    if (b < n) g3[(size_t)b * kF + k] = ld(a3g + (size_t)b * kF + k) > 0.f ? acc[s] : 0.f;
+  }
+}
+
+// ---- conv backward: weight gradients and (masked) input deltas ---------------
+
+constexpr int kBackThreads = 256;
+
+// Layer with C input channels of HI x HI (output 32 x HO x HO).  gin: the
+// masked delta of this layer's output [n][32][HO*HO]; ain: its input
+// activations [n][C][HI*HI] (BF16), or the stamps for the first layer.
+// With DX, gout[n][C][HI*HI] = (sum over o, taps of gin * w) * (ain > 0).
+// Block partial (at partial + blockIdx.x * kPartialStride):
+//   [parts][32][C][9] weight sums, then [32] bias sums.
+template <int C, int HI, bool DX, bool STAMP>
+__global__ void __launch_bounds__(kBackThreads) k_conv_back(
+    const float* __restrict__ gin, const __nv_bfloat16* __restrict__ ain,
+    const uint16_t* __restrict__ stamps, uint32_t n, const __nv_bfloat16* __restrict__ w,
+    float* __restrict__ gout, float* __restrict__ partial) {
+  constexpr int HO = HI - 2, P = HO * HO, Q = HI * HI;
+  constexpr int PARTS = kBackThreads / (8 * C);  // 1 for C = 32, 3 for C = 9
+  static_assert(PARTS >= 1, "too many channels");
+  extern __shared__ __align__(16) float sm[];
+  float* g_s = sm;             // [32][P]
+  float* a_s = g_s + kCh * P;  // [C][Q]
+  float* w_s = a_s + C * Q;    // [32][9][C]  (DX only)
+  const int t = threadIdx.x;
+  if (DX) {
+    for (int i = t; i < kCh * C * 9; i += blockDim.x) {
+      const int o = i / (C * 9), r = i - o * C * 9, c = r / 9, tap = r % 9;
+      w_s[(o * 9 + tap) * C + c] = ld(w + i);
+    }
+  }
+  // weight-gradient ownership: (4 output channels, 1 input channel, 1 pixel part)
+  const int c_own = t % C, oq = (t / C) % 8, part = t / (8 * C);
+  const bool owner = part < PARTS;
+  float acc[4][9];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) acc[j][tap] = 0.f;
+  float accb = 0.f;
+  for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+    __syncthreads();
+    for (int i = t; i < kCh * P; i += blockDim.x) g_s[i] = gin[(size_t)b * kCh * P + i];
+    if (STAMP) {
+      for (int i = t; i < C * Q; i += blockDim.x)
+        a_s[i] = bf((float)stamps[(size_t)b * C * Q + i] * 0.0625f);
+    } else {
+      for (int i = t; i < C * Q; i += blockDim.x) a_s[i] = ld(ain + (size_t)b * C * Q + i);
+    }
+    __syncthreads();
+    if (owner) {
+      for (int p = part; p < P; p += PARTS) {
+        const int y = p / HO, x = p - y * HO;
+        float g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[j] = g_s[(oq * 4 + j) * P + p];
+        const float* ap = a_s + c_own * Q + y * HI + x;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const float a = ap[(tap / 3) * HI + tap % 3];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j][tap] = fmaf(g[j], a, acc[j][tap]);
+        }
+      }
+    }
+    if (t < kCh) {
+      for (int p = 0; p < P; ++p) accb += g_s[t * P + p];
+    }
+    if (DX) {
+      const int warp = t >> 5, lane = t & 31;
+      constexpr int CQ = C / 4;  // channel quads
+      for (int cq = warp; cq < CQ; cq += kBackThreads / 32) {
+        for (int q = lane; q < Q; q += 32) {
+          const int yi = q / HI, xi = q - yi * HI;
+          float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+          for (int o = 0; o < kCh; ++o) {
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+              const int yo = yi - dy;
+              if (yo < 0 || yo >= HO) continue;
+#pragma unroll
+              for (int dx = 0; dx < 3; ++dx) {
+                const int xo = xi - dx;
+                if (xo < 0 || xo >= HO) continue;
+                const float gg = g_s[o * P + yo * HO + xo];
+                const float4 ww = *reinterpret_cast<const float4*>(w_s + (o * 9 + dy * 3 + dx) * C + cq * 4);
+                d0 = fmaf(gg, ww.x, d0); d1 = fmaf(gg, ww.y, d1);
+                d2 = fmaf(gg, ww.z, d2); d3 = fmaf(gg, ww.w, d3);
+              }
+            }
+          }
+          float* go = gout + (size_t)b * C * Q;
+          const int c = cq * 4;
+          go[(c + 0) * Q + q] = a_s[(c + 0) * Q + q] > 0.f ? d0 : 0.f;
+          go[(c + 1) * Q + q] = a_s[(c + 1) * Q + q] > 0.f ? d1 : 0.f;
+          go[(c + 2) * Q + q] = a_s[(c + 2) * Q + q] > 0.f ? d2 : 0.f;
+          go[(c + 3) * Q + q] = a_s[(c + 3) * Q + q] > 0.f ? d3 : 0.f;
+        }
+      }
+    }
+  }
+  float* out = partial + (size_t)blockIdx.x * kPartialStride;
+  if (owner) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap)
+        out[(size_t)part * kCh * C * 9 + ((oq * 4 + j) * C + c_own) * 9 + tap] = acc[j][tap];
+  }
+  if (t < kCh) out[PARTS * kCh * C * 9 + t] = accb;
+}
+
+// grad[w_off + i] = sum over blocks and parts of the partial weight sums;
+// grad[b_off + o] likewise for the biases.  Fixed summation order.
+__global__ void k_reduce_partials(const float* __restrict__ partial, int n_blocks, int parts, int nw,
+                                  float* __restrict__ grad, int w_off, int b_off) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw + kCh) return;
+  float s = 0.f;
+  for (int blk = 0; blk < n_blocks; ++blk) {
+    const float* p = partial + (size_t)blk * kPartialStride;
+    if (i < nw) {
+      for (int q = 0; q < parts; ++q) s += p[(size_t)q * nw + i];
+    } else {
+      s += p[(size_t)parts * nw + (i - nw)];
+    }
+  }
+  grad[i < nw ? w_off + i : b_off + (i - nw)] = s;
+}
+
+// ---- parameters --------------------------------------------------------------
+
+__global__ void k_cast(const float* __restrict__ master, __nv_bfloat16* __restrict__ wb,
+                       __nv_bfloat16* __restrict__ wf1t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  const __nv_bfloat16 h = __float2bfloat16_rn(master[i]);
+  wb[i] = h;
+  if (i >= kWf1 && i < kBf1) {
+    const int r = i - kWf1, j = r / kF, k = r - j * kF;
+    wf1t[(size_t)k * kHid + j] = h;
+  }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master values; refreshes the BF16 copies.
+__global__ void k_adam(float* __restrict__ master, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ grad, float lr, float beta1, float beta2, float eps,
+                       float bc1, float bc2, __nv_bfloat16* __restrict__ wb,
+                       __nv_bfloat16* __restrict__ wf1t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParams) return;
+  const float g = grad[i];
+  const float mi = beta1 * m[i] + (1.f - beta1) * g;
+  const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  const float p = master[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  master[i] = p;
+  const __nv_bfloat16 h = __float2bfloat16_rn(p);
+  wb[i] = h;
+  if (i >= kWf1 && i < kBf1) {
+    const int r = i - kWf1, j = r / kF, k = r - j * kF;
+    wf1t[(size_t)k * kHid + j] = h;
+  }
+}
+
+// ---- host side -----------------------------------------------------------------
+
+template <int C, int HI, bool DX>
+constexpr size_t back_smem() {
+  return sizeof(float) * ((size_t)kCh * (HI - 2) * (HI - 2) + (size_t)C * HI * HI + (DX ? (size_t)kCh * 9 * C : 0));
+}
+
+cudaError_t set_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kFwdSmemFloats * sizeof(float)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_back<kCh, kH2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)back_smem<kCh, kH2, true>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_back<kCh, kH1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)back_smem<kCh, kH1, true>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_conv_back<kQ, kS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)back_smem<kQ, kS, false>());
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+int fwd_blocks() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n = sms > 0 ? sms : 152;
+  }
+  return n;
+}
+
+// Forward of n <= max_batch stamps; with keep, stores the activations training needs.
+cudaError_t forward(sas_vet* vt, const uint16_t* stamps, uint32_t n, bool keep, float* logits,
+                    cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
+  k_conv_fwd<<<blocks, kFwdThreads, kFwdSmemFloats * sizeof(float), s>>>(
+      stamps, n, vt->wb, keep ? vt->a1 : nullptr, keep ? vt->a2 : nullptr, vt->a3);
+  k_fc_fwd<<<(n + kFcTB - 1) / kFcTB, 256, 0, s>>>(vt->a3, n, vt->wf1t, vt->wb, keep ? vt->a4 : nullptr,
+                                                    logits);
+  note_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n,
+                      float* grad, cudaStream_t s) {
+  cudaError_t e = forward(vt, stamps, n, true, vt->logits, s);
+  if (e != cudaSuccess) return e;
+  k_loss<<<1, kLossThreads, 0, s>>>(vt->logits, labels, n, vt->a4, vt->glogit, grad, vt->loss);
+  k_g4<<<(unsigned)(((uint64_t)n * kHid + 255) / 256), 256, 0, s>>>(vt->glogit, vt->a4, vt->wb, n, vt->g4);
+  k_fc1_dw<<<(kF + 31) / 32, 256, 0, s>>>(vt->g4, vt->a3, n, grad);
+  k_fc1_dx<<<dim3((kF + 63) / 64, (n + 31) / 32), 256, 0, s>>>(vt->g4, vt->wb, vt->a3, n, vt->g3);
+  const int nb = (int)std::min<uint32_t>(n, kBackBlocks);
+  k_conv_back<kCh, kH2, true, false><<<nb, kBackThreads, back_smem<kCh, kH2, true>(), s>>>(
+      vt->g3, vt->a2, nullptr, n, vt->wb + kW3, vt->g2, vt->partial);
+  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
+                                                                      grad, kW3, kB3);
+  k_conv_back<kCh, kH1, true, false><<<nb, kBackThreads, back_smem<kCh, kH1, true>(), s>>>(
+      vt->g2, vt->a1, nullptr, n, vt->wb + kW2, vt->g1, vt->partial);
+  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
+                                                                      grad, kW2, kB2);
+  k_conv_back<kQ, kS, false, true><<<nb, kBackThreads, back_smem<kQ, kS, false>(), s>>>(
+      vt->g1, nullptr, stamps, n, vt->wb + kW1, nullptr, vt->partial);
+  k_reduce_partials<<<(kCh * kQ * 9 + kCh + 255) / 256, 256, 0, s>>>(
+      vt->partial, nb, kBackThreads / (8 * kQ), kCh * kQ * 9, grad, kW1, kB1);
+  note_launch(10);
+  return cudaGetLastError();
+}
+
+cudaError_t adam(sas_vet* vt, const float* grad, float lr, cudaStream_t s) {
+  vt->step += 1;
+  const double bc1 = 1.0 - std::pow((double)vt->beta1, (double)vt->step);
+  const double bc2 = 1.0 - std::pow((double)vt->beta2, (double)vt->step);
+  k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(vt->master, vt->m, vt->v, grad, lr, vt->beta1, vt->beta2,
+                                               vt->eps, (float)bc1, (float)bc2, vt->wb, vt->wf1t);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace vet
+}  // namespace sas
+
+// ---- C ABI -----------------------------------------------------------------------
+
+using namespace sas;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_errorf(SAS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void free_vet(sas_vet* vt) {
+  void* ptrs[] = {vt->master, vt->m, vt->v, vt->grad, vt->wb, vt->wf1t, vt->a1, vt->a2, vt->a3,
+                  vt->a4, vt->logits, vt->glogit, vt->g4, vt->g3, vt->g2, vt->g1, vt->partial, vt->loss};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete vt;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t sas_vet_num_params(void) { return (uint64_t)vet::kNParams; }
+
+int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
+  if (!out) return set_error(SAS_ERR_ARG, "sas_vet_create: out is NULL");
+  *out = nullptr;
+  if (max_batch == 0 || max_batch > SAS_VET_MAX_BATCH)
+    return set_errorf(SAS_ERR_ARG, "sas_vet_create: max_batch must be 1..%u", (unsigned)SAS_VET_MAX_BATCH);
+  DeviceGuard guard(device);
+  if (cudaError_t e = vet::set_attrs(); e != cudaSuccess) return cuda_fail(e, "sas_vet_create");
+  sas_vet* vt = new sas_vet();
+  std::memset(vt, 0, sizeof(*vt));
+  vt->device = device;
+  vt->max_batch = max_batch;
+  vt->beta1 = 0.9f;
+  vt->beta2 = 0.999f;
+  vt->eps = 1e-8f;
+  const size_t B = max_batch, N = vet::kNParams;
+  struct Req {
+    void** p;
+    size_t bytes;
+  } reqs[] = {
+      {(void**)&vt->master, N * 4}, {(void**)&vt->m, N * 4}, {(void**)&vt->v, N * 4},
+      {(void**)&vt->grad, N * 4}, {(void**)&vt->wb, N * 2}, {(void**)&vt->wf1t, (size_t)vet::kF * vet::kHid * 2},
+      {(void**)&vt->a1, B * vet::kCh * vet::kH1 * vet::kH1 * 2}, {(void**)&vt->a2, B * vet::kCh * vet::kH2 * vet::kH2 * 2},
+      {(void**)&vt->a3, B * vet::kF * 2}, {(void**)&vt->a4, B * vet::kHid * 2}, {(void**)&vt->logits, B * 4},
+      {(void**)&vt->glogit, B * 4}, {(void**)&vt->g4, B * vet::kHid * 4}, {(void**)&vt->g3, B * vet::kF * 4},
+      {(void**)&vt->g2, B * vet::kCh * vet::kH2 * vet::kH2 * 4}, {(void**)&vt->g1, B * vet::kCh * vet::kH1 * vet::kH1 * 4},
+      {(void**)&vt->partial, (size_t)vet::kBackBlocks * vet::kPartialStride * 4}, {(void**)&vt->loss, 4},
+  };
+  for (auto& r : reqs) {
+    if (cudaError_t e = cudaMalloc(r.p, r.bytes); e != cudaSuccess) {
+      free_vet(vt);
+      return cuda_fail(e, "sas_vet_create: cudaMalloc");
+    }
+  }
+  cudaMemset(vt->master, 0, N * 4);
+  cudaMemset(vt->m, 0, N * 4);
+  cudaMemset(vt->v, 0, N * 4);
+  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb, vt->wf1t);
+  note_launch();
+  if (cudaError_t e = cudaDeviceSynchronize(); e != cudaSuccess) {
+    free_vet(vt);
+    return cuda_fail(e, "sas_vet_create");
+  }
+  *out = vt;
+  return SAS_OK;
+}
+
+int sas_vet_destroy(sas_vet* vt) {
+  if (!vt) return SAS_OK;
+  DeviceGuard guard(vt->device);
+  cudaDeviceSynchronize();
+  free_vet(vt);
+  return SAS_OK;
+}
+
+int sas_vet_set_adam(sas_vet* vt, float beta1, float beta2, float eps) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_set_adam: NULL vetter");
+  if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+    return set_error(SAS_ERR_ARG, "sas_vet_set_adam: need 0 <= beta < 1 and eps > 0");
+  vt->beta1 = beta1;
+  vt->beta2 = beta2;
+  vt->eps = eps;
+  return SAS_OK;
+}
+
+int sas_vet_set_state(sas_vet* vt, const float* params, const float* m, const float* v, uint64_t step) {
+  if (!vt || !params) return set_error(SAS_ERR_ARG, "sas_vet_set_state: NULL argument");
+  if ((m == nullptr) != (v == nullptr))
+    return set_error(SAS_ERR_ARG, "sas_vet_set_state: give both Adam moments or neither");
+  DeviceGuard guard(vt->device);
+  const size_t bytes = (size_t)vet::kNParams * 4;
+  cudaError_t e = cudaMemcpy(vt->master, params, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = m ? cudaMemcpy(vt->m, m, bytes, cudaMemcpyHostToDevice) : cudaMemset(vt->m, 0, bytes);
+  if (e == cudaSuccess) e = v ? cudaMemcpy(vt->v, v, bytes, cudaMemcpyHostToDevice) : cudaMemset(vt->v, 0, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "sas_vet_set_state");
+  vt->step = m ? step : 0;
+  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb, vt->wf1t);
+  note_launch();
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_set_state");
+}
+
+int sas_vet_get_state(const sas_vet* vt, float* params, float* m, float* v, uint64_t* step) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_get_state: NULL vetter");
+  DeviceGuard guard(vt->device);
+  const size_t bytes = (size_t)vet::kNParams * 4;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && params) e = cudaMemcpy(params, vt->master, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && m) e = cudaMemcpy(m, vt->m, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemcpy(v, vt->v, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "sas_vet_get_state");
+  if (step) *step = vt->step;
+  return SAS_OK;
+}
+
+int sas_vet_get_bf16(const sas_vet* vt, uint16_t* out) {
+  if (!vt || !out) return set_error(SAS_ERR_ARG, "sas_vet_get_bf16: NULL argument");
+  DeviceGuard guard(vt->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, vt->wb, (size_t)vet::kNParams * 2, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_get_bf16");
+}
+
+int sas_vet_forward(sas_vet* vt, const uint16_t* stamps, uint64_t n, float* logits, void* stream) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_forward: NULL vetter");
+  if (n && (!stamps || !logits)) return set_error(SAS_ERR_ARG, "sas_vet_forward: NULL buffer");
+  DeviceGuard guard(vt->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  for (uint64_t b0 = 0; b0 < n; b0 += vt->max_batch) {
+    const uint32_t nb = (uint32_t)std::min<uint64_t>(vt->max_batch, n - b0);
+    if (cudaError_t e = vet::forward(vt, stamps + b0 * 9 * 225, nb, false, logits + b0, s); e != cudaSuccess)
+      return cuda_fail(e, "sas_vet_forward");
+  }
+  return SAS_OK;
+}
+
+int sas_vet_gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n, float* grad,
+                      float* loss, void* stream) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_gradients: NULL vetter");
+  if (n == 0 || n > vt->max_batch)
+    return set_errorf(SAS_ERR_ARG, "sas_vet_gradients: n must be 1..%u", vt->max_batch);
+  if (!stamps || !labels || !grad) return set_error(SAS_ERR_ARG, "sas_vet_gradients: NULL buffer");
+  DeviceGuard guard(vt->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = vet::gradients(vt, stamps, labels, n, grad, s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, vt->loss, 4, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_gradients");
+}
+
+int sas_vet_apply_gradients(sas_vet* vt, const float* grad, float lr, void* stream) {
+  if (!vt || !grad) return set_error(SAS_ERR_ARG, "sas_vet_apply_gradients: NULL argument");
+  if (!(lr >= 0.f)) return set_error(SAS_ERR_ARG, "sas_vet_apply_gradients: lr must be >= 0");
+  DeviceGuard guard(vt->device);
+  cudaError_t e = vet::adam(vt, grad, lr, (cudaStream_t)stream);
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_apply_gradients");
+}
+
+int sas_vet_train_step(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n, float lr,
+                       float* loss, void* stream) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_train_step: NULL vetter");
+  if (n == 0 || n > vt->max_batch)
+    return set_errorf(SAS_ERR_ARG, "sas_vet_train_step: n must be 1..%u", vt->max_batch);
+  if (!stamps || !labels) return set_error(SAS_ERR_ARG, "sas_vet_train_step: NULL buffer");
+  if (!(lr >= 0.f)) return set_error(SAS_ERR_ARG, "sas_vet_train_step: lr must be >= 0");
+  DeviceGuard guard(vt->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = vet::gradients(vt, stamps, labels, n, vt->grad, s);
+  if (e == cudaSuccess) e = vet::adam(vt, vt->grad, lr, s);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, vt->loss, 4, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_train_step");
+}
+
+}  // extern "C"

@@ -370,3 +370,110 @@ def sas_autotune(grid: Grid, x, y, epoch, t, ticks_per_hour: int, n_min: int,
                              ctypes.byref(base) if base is not None else None, int(reps),
                              _stream_handle(stream), ctypes.byref(best), ctypes.byref(ms)))
     return best, ms.value
+
+
+# ---- stamps and the candidate vetter ------------------------------------------------
+
+_lib.sas_stamps.argtypes = [_p, ctypes.c_uint64, ctypes.c_uint64, _p, _p]
+_lib.sas_vet_num_params.restype = ctypes.c_uint64
+_lib.sas_vet_create.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(_p)]
+_lib.sas_vet_destroy.argtypes = [_p]
+_lib.sas_vet_set_adam.argtypes = [_p, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+_lib.sas_vet_set_state.argtypes = [_p, _p, _p, _p, ctypes.c_uint64]
+_lib.sas_vet_get_state.argtypes = [_p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]
+_lib.sas_vet_get_bf16.argtypes = [_p, _p]
+_lib.sas_vet_forward.argtypes = [_p, _p, ctypes.c_uint64, _p, _p]
+_lib.sas_vet_gradients.argtypes = [_p, _p, _p, ctypes.c_uint32, _p, _p, _p]
+_lib.sas_vet_apply_gradients.argtypes = [_p, _p, ctypes.c_float, _p]
+_lib.sas_vet_train_step.argtypes = [_p, _p, _p, ctypes.c_uint32, ctypes.c_float, _p, _p]
+EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
+             "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
+             "sas_vet_forward", "sas_vet_gradients", "sas_vet_apply_gradients",
+             "sas_vet_train_step"]
+
+STAMP_SHAPE = (9, 15, 15)
+VET_MAX_BATCH = 8192
+
+
+def sas_stamps(result: Result, out_dev, first: int = 0, count: int | None = None, stream=None) -> int:
+    """Stamps of candidates [first, first + count) into a device uint16 array
+    of count x 9 x 15 x 15 (asynchronous on stream); returns count."""
+    if count is None:
+        count = result.info()["n_candidates"] - first
+    _check(_lib.sas_stamps(result._h, int(first), int(count), _dev_ptr(out_dev) if count else None,
+                           _stream_handle(stream)))
+    return count
+
+
+def vet_num_params() -> int:
+    return int(_lib.sas_vet_num_params())
+
+
+class Vetter:
+    """sas_vet_*: the candidate-vetting CNN on one device.  Device arrays are
+    torch CUDA tensors (or __cuda_array_interface__ objects); host arrays are
+    NumPy."""
+
+    def __init__(self, device: int = 0, max_batch: int = 1024):
+        h = _p()
+        _check(_lib.sas_vet_create(int(device), int(max_batch), ctypes.byref(h)))
+        self._h = h
+        self.max_batch = int(max_batch)
+        self.n_params = vet_num_params()
+
+    def set_adam(self, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(_lib.sas_vet_set_adam(self._h, beta1, beta2, eps))
+
+    def set_state(self, params, m=None, v=None, step: int = 0):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.shape == (self.n_params,)
+        mm = None if m is None else np.ascontiguousarray(m, np.float32)
+        vv = None if v is None else np.ascontiguousarray(v, np.float32)
+        _check(_lib.sas_vet_set_state(self._h, p.ctypes.data, None if mm is None else mm.ctypes.data,
+                                      None if vv is None else vv.ctypes.data, int(step)))
+
+    def get_state(self):
+        """(params, m, v, step) as float32 host arrays."""
+        p = np.zeros(self.n_params, np.float32)
+        m = np.zeros(self.n_params, np.float32)
+        v = np.zeros(self.n_params, np.float32)
+        st = ctypes.c_uint64()
+        _check(_lib.sas_vet_get_state(self._h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                      ctypes.byref(st)))
+        return p, m, v, st.value
+
+    def get_bf16(self) -> np.ndarray:
+        """The BF16 working copy as float32 values."""
+        raw = np.zeros(self.n_params, np.uint16)
+        _check(_lib.sas_vet_get_bf16(self._h, raw.ctypes.data))
+        return (raw.astype(np.uint32) << 16).view(np.float32)
+
+    def forward(self, stamps_dev, n: int, logits_dev, stream=None):
+        _check(_lib.sas_vet_forward(self._h, _dev_ptr(stamps_dev) if n else None, int(n),
+                                    _dev_ptr(logits_dev) if n else None, _stream_handle(stream)))
+
+    def gradients(self, stamps_dev, labels_dev, n: int, grad_dev, loss_dev=None, stream=None):
+        _check(_lib.sas_vet_gradients(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), int(n),
+                                      _dev_ptr(grad_dev),
+                                      None if loss_dev is None else _dev_ptr(loss_dev),
+                                      _stream_handle(stream)))
+
+    def apply_gradients(self, grad_dev, lr: float, stream=None):
+        _check(_lib.sas_vet_apply_gradients(self._h, _dev_ptr(grad_dev), float(lr),
+                                            _stream_handle(stream)))
+
+    def train_step(self, stamps_dev, labels_dev, n: int, lr: float, loss_dev=None, stream=None):
+        _check(_lib.sas_vet_train_step(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), int(n),
+                                       float(lr), None if loss_dev is None else _dev_ptr(loss_dev),
+                                       _stream_handle(stream)))
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.sas_vet_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
