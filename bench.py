@@ -114,21 +114,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def stack_traffic(n_pairs: int):
-    """DRAM bytes per stack launch from the committed ncu summary, if it was taken
-    on the current stack kernel source; otherwise None."""
-    p = os.path.join(ROOT, "profiles", "stack_traffic.json")
+def stack_traffic(workload: str):
+    """DRAM bytes per stack launch from the committed ncu summary of this
+    workload, if it was taken on the current stack kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"k_stack_{workload}.md")
     src = os.path.join(ROOT, "paper_2509_26279_gb300", "csrc", "sas_stack.cu")
     if not os.path.exists(p):
         return None
-    try:
-        d = json.load(open(p))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("stack_source_sha256") != h:
-            return None
-        return int(d["dram_bytes_per_launch_full_size"])
-    except (OSError, ValueError, KeyError):
+    fields = {}
+    for line in open(p):
+        k, sep, v = line.strip().partition(":")
+        if sep and k in ("stack_source_sha256", "traffic_bytes_per_launch"):
+            fields[k] = v.strip()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if fields.get("stack_source_sha256") != h or "traffic_bytes_per_launch" not in fields:
         return None
+    return int(fields["traffic_bytes_per_launch"])
 
 
 def cpu_baseline(w: W.Workload, cat, budget_s: float = 15.0) -> dict:
@@ -293,7 +294,7 @@ def main():
         return 0
     achieved = n_pairs / (statistics.mean(stack_ms) * 1e-3)
     roof = {"bound": "smem_atomic", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
-            "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": stack_traffic(n_pairs),
+            "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": stack_traffic(args.workload),
             "kernel": "k_stack", "stack_ms": statistics.mean(stack_ms),
             "peak_source": f"sas_probe_shared_atomic_peak, this run ({probe_mhz:.0f} MHz)"}
     cfg = workload_desc(w, cat)

@@ -352,7 +352,8 @@ int sas_vet_train_step(sas_vet* vetter, const uint16_t* stamps, const float* lab
  * atomicAdd on every SM of the current device, in operations per second,
  * measured with CUDA events over `iters` operations per thread; this is the
  * peak against which the stack kernel's detection-shifts/s are compared.
- * Also reports the median SM clock (MHz) implied by clock64() over the run. */
+ * Also reports the SM clock (MHz) during the probe: clock64() cycles over the
+ * global timer's nanoseconds on one SM, in the fastest repetition. */
 int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s,
                                  double* sm_mhz);
 

@@ -14,12 +14,21 @@ namespace {
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeUnroll = 8;
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// clk[0], clk[1]: SM cycles and nanoseconds (global timer) over block 0's loop,
+// from which the SM clock during the probe follows.
 __global__ void __launch_bounds__(kProbeThreads, 2)
-    k_atomic_probe(uint32_t iters, uint32_t* sink, unsigned long long* cycles) {
+    k_atomic_probe(uint32_t iters, uint32_t* sink, unsigned long long* clk) {
   __shared__ uint32_t s[kProbeThreads * kProbeUnroll];
   for (int i = threadIdx.x; i < kProbeThreads * kProbeUnroll; i += blockDim.x) s[i] = 0;
   __syncthreads();
   const long long c0 = clock64();
+  const unsigned long long t0 = global_ns();
   uint32_t* base = s + threadIdx.x;
   uint32_t acc = 0;
   for (uint32_t it = 0; it < iters; ++it) {
@@ -28,8 +37,12 @@ __global__ void __launch_bounds__(kProbeThreads, 2)
   }
   __syncthreads();
   const long long c1 = clock64();
+  const unsigned long long t1 = global_ns();
   if (threadIdx.x == 0) {
-    atomicAdd(cycles, (unsigned long long)(c1 - c0));
+    if (blockIdx.x == 0) {
+      clk[0] = (unsigned long long)(c1 - c0);
+      clk[1] = t1 - t0;
+    }
     sink[blockIdx.x] = s[0] + acc;
   }
 }
@@ -48,14 +61,14 @@ cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s,
   uint32_t* sink = nullptr;
   unsigned long long* cycles = nullptr;
   if ((e = cudaMallocAsync(&sink, blocks * sizeof(uint32_t), st)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync(&cycles, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  if ((e = cudaMallocAsync(&cycles, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best_ms = 1e30f;
   double mhz = 0;
   for (int rep = 0; rep < 4; ++rep) {  // rep 0 warms up
-    cudaMemsetAsync(cycles, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(cycles, 0, 2 * sizeof(unsigned long long), st);
     cudaEventRecord(a, st);
     k_atomic_probe<<<blocks, kProbeThreads, 0, st>>>(iters, sink, cycles);
     note_launch();
@@ -63,11 +76,11 @@ cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s,
     if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
-    unsigned long long cyc = 0;
-    cudaMemcpy(&cyc, cycles, sizeof(cyc), cudaMemcpyDeviceToHost);
+    unsigned long long cyc[2] = {0, 0};
+    cudaMemcpy(cyc, cycles, sizeof(cyc), cudaMemcpyDeviceToHost);
     if (rep > 0 && ms < best_ms) {
       best_ms = ms;
-      mhz = (double)cyc / blocks / (ms * 1e3);
+      mhz = cyc[1] ? (double)cyc[0] / ((double)cyc[1] * 1e-3) : 0.0;
     }
   }
   cudaEventDestroy(a);
