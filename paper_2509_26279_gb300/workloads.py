@@ -25,6 +25,8 @@ exposures over ~4 h, TNO and MBA rate ranges of Sec. 3.3 converted at
                   lattice 1001x1001 step 600 mpx/h (+-300 px/h); bin 3 px; N_min 15
   batched_fields  60 CCD fields, epochs U{20..150} over 4 h, noise/epoch log-U[1e3,8e3],
                   movers and lattice as decam_tno; bin 2 px; N_min = ceil(E/4)
+  vetter_fields   as batched_fields with magnitudes U[23,26.5] (p 0.9 -> 0.06) and 40
+                  stationary artifacts per field (p ~ U[0.5,1])
 """
 from __future__ import annotations
 
@@ -69,7 +71,8 @@ class GridSpec:
 class Catalog:
     """Structure-of-arrays detection catalog C = [x_i, y_i, t_i] (Sec. 2.1).
     ``epoch[i]`` indexes ``t``; ``mover[i]`` is the injected mover that made
-    detection i, or -1 for a noise peak (truth, not an input of the method)."""
+    detection i, -1 for a noise peak or STATIC (-2) for a stationary artifact
+    (truth, not an input of the method)."""
     x: np.ndarray          # int32 [n]
     y: np.ndarray          # int32 [n]
     epoch: np.ndarray      # uint16 [n]
@@ -107,6 +110,8 @@ class FieldRecipe:
     p_detect: tuple            # (p_bright, p_faint) linear in magnitude over mag range
     mag_range: tuple = (23.0, 25.5)
     jitter_px: float = 0.5
+    n_static: int = 0          # stationary artifacts (fixed position, detected with p_static)
+    p_static: tuple = (0.5, 1.0)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -117,6 +122,8 @@ class Workload:
     n_min: int
     seed: int
 
+
+STATIC = -2  # Catalog.mover value of a stationary artifact's detection
 
 MOVER_DTYPE = np.dtype([("x0", "f8"), ("y0", "f8"), ("vx", "f8"), ("vy", "f8"),
                         ("mag", "f8"), ("p", "f8")])
@@ -152,6 +159,15 @@ def make_catalog(recipe: FieldRecipe, seed: int, mag_range: Optional[tuple] = No
     frac = np.clip((movers["mag"] - lo) / (hi - lo), 0.0, None) if hi > lo else np.zeros(nm)
     movers["p"] = np.clip(pb + (pf - pb) * frac, 0.0, 1.0)
 
+    # stationary artifacts draw from their own stream, so fields without them
+    # are unchanged
+    ns = recipe.n_static
+    if ns:
+        srng = np.random.default_rng([seed, 7919])
+        sx0 = srng.uniform(0, W, ns)
+        sy0 = srng.uniform(0, H, ns)
+        sp = srng.uniform(recipe.p_static[0], recipe.p_static[1], ns)
+
     xs, ys, es, ms = [], [], [], []
     t0 = t.min()
     for e in range(E):
@@ -170,6 +186,14 @@ def make_catalog(recipe: FieldRecipe, seed: int, mag_range: Optional[tuple] = No
             xe = np.concatenate([xe, px[idx]])
             ye = np.concatenate([ye, py[idx]])
             me = np.concatenate([me, idx])
+        if ns:
+            det = srng.random(ns) < sp
+            qx = np.rint(sx0 + srng.normal(0, recipe.jitter_px * MPX, ns)).astype(np.int64)
+            qy = np.rint(sy0 + srng.normal(0, recipe.jitter_px * MPX, ns)).astype(np.int64)
+            keep = det & (qx >= 0) & (qx < W) & (qy >= 0) & (qy < H)
+            xe = np.concatenate([xe, qx[keep]])
+            ye = np.concatenate([ye, qy[keep]])
+            me = np.concatenate([me, np.full(int(keep.sum()), STATIC, np.int64)])
         perm = rng.permutation(xe.shape[0])   # catalog order shuffled within an epoch
         xs.append(xe[perm]); ys.append(ye[perm]); ms.append(me[perm])
         es.append(np.full(xe.shape[0], e, np.int64))
@@ -215,6 +239,26 @@ def batched_fields(n_fields: int = 60, seed: int = BASE_SEED + 4) -> List[Worklo
         noise = int(round(math.exp(rng.uniform(math.log(1e3), math.log(8e3)))))
         r = FieldRecipe(2048, 4096, E, 4.0, noise, 200, (0.5, 20.0), (0.9, 0.3))
         out.append(Workload(f"batched_fields[{f}]", r, field_grid(2048, 4096, 2000, 364, 55),
+                            -(-E // 4), seed * 1000 + f))
+    return out
+
+
+def vetter_fields(n_fields: int, seed: int = BASE_SEED + 5) -> List[Workload]:
+    """Fields for training and judging the candidate vetter: the geometry,
+    lattice and bin of decam_tno with the batched spread of epochs (U{20..150})
+    and noise (log-U[1e3, 8e3]); mover magnitudes extended to U[23, 26.5] with
+    the same detection-probability slope (p = 0.9 at m = 23 down to 0.06 at
+    m = 26.5), and 40 stationary artifacts per field detected with p ~ U[0.5, 1]
+    (a source at rest: count near E at zero velocity).  n_min is the plain
+    threshold ceil(E/4)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for f in range(n_fields):
+        E = int(rng.integers(20, 151))
+        noise = int(round(math.exp(rng.uniform(math.log(1e3), math.log(8e3)))))
+        r = FieldRecipe(2048, 4096, E, 4.0, noise, 200, (0.5, 20.0), (0.9, 0.06),
+                        mag_range=(23.0, 26.5), n_static=40)
+        out.append(Workload(f"vetter_fields[{f}]", r, field_grid(2048, 4096, 2000, 364, 55),
                             -(-E // 4), seed * 1000 + f))
     return out
 
