@@ -16,6 +16,10 @@ N_min = 25.  The metric is detection-shifts per second: in-domain
   roofline  the stack kernel against the shared-memory atomic peak measured in
             this run by the library's probe (one atomic per detection-shift)
 
+  fields    fields/s of the plain form (one search per field) against the
+            batched + vetted form on 60 uneven fields, with recall per
+            magnitude bin and purity (after training the vetter, untimed)
+
 --impl reference times the CPU oracle (the plain definition, single thread) on
 a bounded lattice-row sample of the same workload.
 Multi-GPU (torchrun): each rank searches its own field (weak scaling); the
@@ -151,6 +155,122 @@ def cpu_baseline(w: W.Workload, cat, budget_s: float = 15.0) -> dict:
                       f"({pairs} detection-shifts in {secs:.1f} s)"}
 
 
+def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epochs: int = 15,
+                   reps: int = 2) -> dict:
+    """fields/s on the batched uneven fields (60 CCDs, epochs U{20..150}, noise
+    log-U[1e3, 8e3]): the plain form (one sas_stack per field at N_min =
+    ceil(E/4)) against the batched + vetted form (one graph-captured batch
+    pass, then ownership selection, stamps and the CNN per field), at the plain
+    threshold and at the lowered one; recall per 0.5-mag bin and purity of each
+    form's reported candidates.  The vetter is trained first (not timed) on
+    separate seeded fields."""
+    import torch
+    from paper_2509_26279_gb300 import sas, vetting
+
+    t0 = time.perf_counter()
+    st, lab = vetting.training_set(W.vetter_fields(train_fields, seed=W.BASE_SEED + 50), dev)
+    vt = sas.Vetter(dev.index or 0, 512)
+    vt.set_state(vetting.init_params(1))
+    hist = vetting.train(vt, st, lab, epochs=epochs, batch=512, lr=1e-3)
+    n_train = int(st.shape[0])
+    del st, lab
+    cst, clab = vetting.training_set(W.vetter_fields(10, seed=W.BASE_SEED + 70), dev)
+    tau = vetting.calibrate(vetting.logits_of(vt, cst), clab.cpu().numpy(), 0.95)
+    del cst, clab
+    train_s = time.perf_counter() - t0
+
+    fields = [vetting.Field(w, dev) for w in W.batched_fields(n_fields)]
+    nb = len(vetting.MAG_EDGES) - 1
+
+    def score(per_field):
+        tot, fnd, rep, mat = [0] * nb, [0] * nb, 0, 0
+        for f, (cands, ids, keep) in zip(fields, per_field):
+            m = vetting.truth_match(cands, ids, f.cat.mover)
+            if keep is not None:
+                m = m[keep]
+            r = vetting.recall_by_mag(np.unique(m[m >= 0]), f.cat.movers)
+            tot = [a + b for a, b in zip(tot, r["total"])]
+            fnd = [a + b for a, b in zip(fnd, r["found"])]
+            rep += len(m)
+            mat += int((m >= 0).sum())
+        return {"recall_by_mag": [round(b / a, 4) if a else None for a, b in zip(tot, fnd)],
+                "movers_by_mag": tot, "reported": rep, "purity": round(mat / rep, 4) if rep else None}
+
+    def timed(fn):
+        fn()                                   # warm-up
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        return best, out
+
+    def plain():
+        res = [f.search(f.w.n_min, stream) for f in fields]
+        return res
+
+    ms_plain, res = timed(plain)
+    plain_out = []
+    for r in res:
+        c, i = r.candidates()
+        plain_out.append((c, i, None))
+        r.free()
+
+    def make_batch(thr):
+        return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
+                         stream=stream)
+
+    def vetted_pass(batch):
+        def run():
+            batch.run(stream)
+            out = []
+            for k in range(len(fields)):
+                n = batch.field_info(k)["n_candidates"]
+                idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+                kept = batch.owned(k, idx, stream)
+                stamps = torch.empty((max(kept, 1), 9, 15, 15), dtype=torch.int16, device=dev)
+                batch.stamps(k, idx, kept, stamps, stream)
+                logits = torch.empty(max(kept, 1), dtype=torch.float32, device=dev)
+                vt.forward(stamps, kept, logits, stream=stream)
+                out.append((idx, logits, kept))
+            return out
+        return run
+
+    result = {"workload": f"batched_fields: {n_fields} CCDs 2048x4096 px, epochs U{{20..150}} over 4 h, "
+                          f"noise/epoch log-U[1e3,8e3], 200 movers each, 111x111 lattice, bin 2 px",
+              "plain": {"form": "one sas_stack per field, N_min = ceil(E/4)", "ms": round(ms_plain, 3),
+                        "fields_per_s": round(n_fields / (ms_plain * 1e-3), 2), **score(plain_out)},
+              "vetter_training": {"fields": train_fields, "stamps": n_train, "epochs": epochs,
+                                  "final_loss": round(hist[-1], 4), "seconds": round(train_s, 1),
+                                  "threshold": round(tau, 4),
+                                  "threshold_rule": "purity 0.95 on 10 separate calibration fields"}}
+    for name, thr, desc in (("batched_vetted", lambda f: f.w.n_min, "batch at N_min = ceil(E/4)"),
+                            ("batched_vetted_low", lambda f: vetting.n_low(f.E),
+                             "batch at N_min = max(5, ceil(E/14))")):
+        batch = make_batch(thr)
+        ms, out = timed(vetted_pass(batch))
+        per_field = []
+        for k, (idx, logits, kept) in enumerate(out):
+            c, i = batch.candidates(k)
+            sel = idx[:kept].cpu().numpy().astype(np.int64)
+            keep = sel[logits[:kept].cpu().numpy() >= tau]
+            mask = np.zeros(len(c), bool)
+            mask[keep] = True
+            per_field.append((c, i, mask))
+        _, fallbacks = batch.stats()
+        result[name] = {"form": desc + ", ownership selection, CNN logit >= calibrated threshold",
+                        "ms": round(ms, 3),
+                        "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
+                        **score(per_field)}
+        batch.destroy()
+    return result
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -196,6 +316,7 @@ def main():
     ap.add_argument("--workload", default="decam_tno", choices=["decam_tno", "fast_movers", "tiny"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-fields", action="store_true", help="skip the fields/s comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -314,6 +435,8 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(launches), "roofline": roof}
+    if world == 1 and not args.no_fields:
+        out["fields"] = fields_section(dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, cat, args.cpu_budget_s)
     print(json.dumps(out), flush=True)

@@ -224,6 +224,14 @@ int sas_batch_candidates(const sas_batch* batch, uint32_t field, sas_candidate* 
  * field fallbacks so far. */
 int sas_batch_stats(const sas_batch* batch, float* ms_last, uint64_t* fallbacks);
 void sas_batch_destroy(sas_batch* batch);
+/* sas_peaks, sas_stamps and sas_owned for field `field` of the last run (idx NULL in
+ * sas_batch_stamps: candidates 0..count). */
+int sas_batch_peaks(const sas_batch* batch, uint32_t field, uint32_t* idx, uint64_t* n_peaks,
+                    void* stream);
+int sas_batch_stamps(const sas_batch* batch, uint32_t field, const uint32_t* idx, uint64_t count,
+                     uint16_t* out, void* stream);
+int sas_batch_owned(const sas_batch* batch, uint32_t field, uint32_t* idx, uint64_t* n_kept,
+                    void* stream);
 
 /* Autotuner: times sas_stack on (grid, cat, n_min) for each candidate pair of
  * superbin in {1, 2, 3} and velocity_block in {1, 2, 4, 8} (other fields of
@@ -288,6 +296,30 @@ int sas_cell_counts_noalloc(const sas_grid* grid, const sas_catalog* cat, const 
  * null out with count > 0), SAS_ERR_CUDA. */
 int sas_stamps(const sas_result* result, uint64_t first, uint64_t count, uint16_t* out,
                void* stream);
+/* Stamps of candidates idx[0..count) (device uint32 indices into the result's
+ * candidates, each < n_candidates) into out; otherwise as sas_stamps. */
+int sas_stamps_indexed(const sas_result* result, const uint32_t* idx, uint64_t count,
+                       uint16_t* out, void* stream);
+
+/* Local peaks of a result's candidates: candidate i is a peak when no other
+ * candidate within one lattice step in kx and in ky and one bin in bx and in
+ * by precedes it in the output order.  A mover's cluster of neighbouring
+ * threshold crossings (Sec. 2.2's velocity tolerance spans several lattice
+ * steps) keeps its best cell; this is a cheap, order-defined stand-in for the
+ * paper's peeling of clusters (Sec. 2.1 step 3).  Writes the ascending
+ * indices of the peaks to idx (device uint32, room for n_candidates) and their
+ * number to *n_peaks (host); synchronizes the stream.
+ * Errors: SAS_ERR_ARG, SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_peaks(const sas_result* result, uint32_t* idx, uint64_t* n_peaks, void* stream);
+
+/* Ownership selection of a result's candidates, a one-pass stand-in for the
+ * paper's peeling of clusters (Sec. 2.1 step 3: the best cluster's detections
+ * are removed before the next is taken).  Each detection belongs to the first
+ * candidate, in output order, whose ids contain it; candidate i is kept when it
+ * owns at least half of its ids.  A mover's ghost cells (nearby velocities and
+ * bins that also collect its detections) lose their detections to its best
+ * cell and drop out.  Output as sas_peaks.  Uses O(catalog size) scratch. */
+int sas_owned(const sas_result* result, uint32_t* idx, uint64_t* n_kept, void* stream);
 
 /* The network (input = count / 16):
  *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),
@@ -326,18 +358,21 @@ int sas_vet_get_state(const sas_vet* vetter, float* params, float* m, float* v, 
 /* The BF16 working copy of the parameters (flat order, raw bits), to host. */
 int sas_vet_get_bf16(const sas_vet* vetter, uint16_t* out);
 
-/* logits[i] of n stamps (device arrays: stamps [n][9][15][15] uint16,
- * logits [n] float); any n, processed in batches of max_batch.  Asynchronous
- * on `stream`. */
-int sas_vet_forward(sas_vet* vetter, const uint16_t* stamps, uint64_t n, float* logits,
-                    void* stream);
+/* logits[i] of n stamps (device arrays: stamps [.][9][15][15] uint16,
+ * logits [n] float); stamp i is stamps[index[i]] when index (device uint32
+ * [n]) is given, else stamps[i]; any n, processed in batches of max_batch.
+ * Asynchronous on `stream`. */
+int sas_vet_forward(sas_vet* vetter, const uint16_t* stamps, const uint32_t* index, uint64_t n,
+                    float* logits, void* stream);
 
 /* Gradient (device float [sas_vet_num_params()]) of the mean BCE loss of n
- * (1..max_batch) stamps with labels (device float [n], 1 = mover, 0 = not)
- * at the current parameters; the loss goes to *loss (device float, may be
- * NULL).  Asynchronous on `stream`. */
-int sas_vet_gradients(sas_vet* vetter, const uint16_t* stamps, const float* labels, uint32_t n,
-                      float* grad, float* loss, void* stream);
+ * (1..max_batch) stamps with labels (device float, parallel to stamps; 1 =
+ * mover, 0 = not) at the current parameters; the batch is stamps[index[i]]
+ * (and labels[index[i]]) when index (device uint32 [n]) is given, else the
+ * first n.  The loss goes to *loss (device float, may be NULL).
+ * Asynchronous on `stream`. */
+int sas_vet_gradients(sas_vet* vetter, const uint16_t* stamps, const float* labels,
+                      const uint32_t* index, uint32_t n, float* grad, float* loss, void* stream);
 
 /* One Adam step (Kingma & Ba 2015) with a caller's gradient (device float
  * [sas_vet_num_params()]), learning rate lr >= 0.  Asynchronous. */
@@ -345,8 +380,8 @@ int sas_vet_apply_gradients(sas_vet* vetter, const float* grad, float lr, void* 
 
 /* sas_vet_gradients followed by sas_vet_apply_gradients on an internal
  * gradient buffer.  Asynchronous. */
-int sas_vet_train_step(sas_vet* vetter, const uint16_t* stamps, const float* labels, uint32_t n,
-                       float lr, float* loss, void* stream);
+int sas_vet_train_step(sas_vet* vetter, const uint16_t* stamps, const float* labels,
+                       const uint32_t* index, uint32_t n, float lr, float* loss, void* stream);
 
 /* Measurement utility: throughput of conflict-free 32-bit shared-memory
  * atomicAdd on every SM of the current device, in operations per second,

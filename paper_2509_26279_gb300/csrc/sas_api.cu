@@ -37,6 +37,7 @@ struct sas_result {
   int32_t* d_syt;
   SearchGeom g;
   CoarseGeom cg;
+  uint64_t n_det;  // catalog size (detection ids are < n_det)
 };
 
 namespace {
@@ -105,6 +106,24 @@ struct Tracer {
 };
 
 }  // namespace
+
+namespace sas {
+CandView result_view(const sas_result* r) {
+  CandView v;
+  v.cands = r->d_cands;
+  v.n = r->info.n_candidates;
+  v.g = r->g;
+  v.cg = r->cg;
+  v.dets = r->d_dets;
+  v.boff = r->d_boff;
+  v.ecount = r->d_ecount;
+  v.sxt = r->d_sxt;
+  v.syt = r->d_syt;
+  v.ids = r->d_ids;
+  v.n_det = r->n_det;
+  return v;
+}
+}  // namespace sas
 
 extern "C" {
 
@@ -184,6 +203,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   if (!res) return fail(SAS_ERR_OOM, "host allocation");
   memset(res, 0, sizeof(*res));
   res->device = dev;
+  res->n_det = n;
 
   if (n == 0 || v_begin == v_end) {
     res->info.t0 = 0;
@@ -472,10 +492,31 @@ int sas_stamps(const sas_result* r, uint64_t first, uint64_t count, uint16_t* ou
                 (unsigned long long)(first + count), (unsigned long long)nc);
   if (count == 0) return SAS_OK;
   if (!out) return fail(SAS_ERR_ARG, "null stamp buffer");
-  cudaError_t e = launch_stamps(r->d_cands + first, count, r->g, r->cg, r->d_dets, r->d_boff, r->d_ecount,
-                                r->d_sxt, r->d_syt, out, (cudaStream_t)stream);
+  cudaError_t e = launch_stamps(result_view(r), nullptr, first, count, out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "stamps");
   return SAS_OK;
+}
+
+int sas_stamps_indexed(const sas_result* r, const uint32_t* idx, uint64_t count, uint16_t* out,
+                       void* stream) {
+  if (!r) return fail(SAS_ERR_ARG, "null result");
+  if (count == 0) return SAS_OK;
+  if (!idx || !out) return fail(SAS_ERR_ARG, "null index or stamp buffer");
+  cudaError_t e = launch_stamps(result_view(r), idx, 0, count, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stamps");
+  return SAS_OK;
+}
+
+int sas_owned(const sas_result* r, uint32_t* idx, uint64_t* n_kept, void* stream) {
+  if (!r || !n_kept) return fail(SAS_ERR_ARG, "null argument");
+  if (r->info.n_candidates && !idx) return fail(SAS_ERR_ARG, "null index buffer");
+  return select_owned(result_view(r), idx, n_kept, (cudaStream_t)stream);
+}
+
+int sas_peaks(const sas_result* r, uint32_t* idx, uint64_t* n_peaks, void* stream) {
+  if (!r || !n_peaks) return fail(SAS_ERR_ARG, "null argument");
+  if (r->info.n_candidates && !idx) return fail(SAS_ERR_ARG, "null index buffer");
+  return select_peaks(result_view(r), idx, n_peaks, (cudaStream_t)stream);
 }
 
 void sas_result_free(sas_result* r) {

@@ -407,6 +407,57 @@ int sas_batch_candidates(const sas_batch* b, uint32_t field, sas_candidate* out,
   return SAS_OK;
 }
 
+namespace {
+
+CandView batch_view(const sas_batch* b, uint32_t field) {
+  if (b->fallback[field]) return result_view(b->fallback[field]);
+  sas_result_info info;
+  sas_batch_field_info(b, field, &info);
+  const BatchField& f = b->hf[field];
+  CandView v;
+  v.cands = f.cands;
+  v.n = info.n_candidates;
+  v.g = f.args.g;
+  v.cg = f.args.cg;
+  v.dets = f.args.dets;
+  v.boff = f.args.boff;
+  v.ecount = f.ecount;
+  v.sxt = f.sxt;
+  v.syt = f.syt;
+  v.ids = f.ids;
+  v.n_det = b->cats[field].n;
+  return v;
+}
+
+}  // namespace
+
+int sas_batch_peaks(const sas_batch* b, uint32_t field, uint32_t* idx, uint64_t* n_peaks, void* stream) {
+  if (!b || field >= b->n_fields || !n_peaks) return set_error(SAS_ERR_ARG, "bad argument");
+  const CandView v = batch_view(b, field);
+  if (v.n && !idx) return set_error(SAS_ERR_ARG, "null index buffer");
+  return select_peaks(v, idx, n_peaks, (cudaStream_t)stream);
+}
+
+int sas_batch_owned(const sas_batch* b, uint32_t field, uint32_t* idx, uint64_t* n_kept, void* stream) {
+  if (!b || field >= b->n_fields || !n_kept) return set_error(SAS_ERR_ARG, "bad argument");
+  const CandView v = batch_view(b, field);
+  if (v.n && !idx) return set_error(SAS_ERR_ARG, "null index buffer");
+  return select_owned(v, idx, n_kept, (cudaStream_t)stream);
+}
+
+int sas_batch_stamps(const sas_batch* b, uint32_t field, const uint32_t* idx, uint64_t count, uint16_t* out,
+                     void* stream) {
+  if (!b || field >= b->n_fields) return set_error(SAS_ERR_ARG, "bad argument");
+  const CandView v = batch_view(b, field);
+  if (!idx && count > v.n)
+    return set_errorf(SAS_ERR_ARG, "%llu stamps asked of a field with %llu candidates",
+                      (unsigned long long)count, (unsigned long long)v.n);
+  if (count == 0) return SAS_OK;
+  if (!out) return set_error(SAS_ERR_ARG, "null stamp buffer");
+  cudaError_t e = launch_stamps(v, idx, 0, count, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? SAS_OK : cuda_err(e, "batch stamps");
+}
+
 int sas_batch_stats(const sas_batch* b, float* ms_last, uint64_t* fallbacks) {
   if (!b) return set_error(SAS_ERR_ARG, "null batch");
   if (ms_last) *ms_last = b->ms_last;

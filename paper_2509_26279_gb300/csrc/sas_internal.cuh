@@ -197,12 +197,40 @@ cudaError_t launch_gather_ids(const Key* keys, uint32_t n, const unsigned long l
 cudaError_t launch_write_candidates(const Key* keys, uint32_t n, const unsigned long long* id_off,
                                     sas_candidate* out, cudaStream_t s);
 
-// sas_stamps.cu: 9 x 15 x 15 distinct-epoch count stamps of n candidates, u16
-// [n][9][15][15], from a search's bucketed catalog and shift tables.
-cudaError_t launch_stamps(const sas_candidate* cands, uint64_t n, const SearchGeom& g,
-                          const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
-                          const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
+// A finished search's candidates together with what is needed to recount any
+// cell of its lattice: bucketed catalog, per-epoch counts, shift tables.
+struct CandView {
+  const sas_candidate* cands;  // device, output order
+  uint64_t n;
+  SearchGeom g;
+  CoarseGeom cg;
+  const Det* dets;
+  const uint32_t* boff;
+  const uint32_t* ecount;
+  const int32_t* sxt;
+  const int32_t* syt;
+  const uint32_t* ids;         // device, candidate i's ids at [id_off, id_off + id_len)
+  uint64_t n_det;              // catalog size
+};
+
+// sas_stamps.cu: 9 x 15 x 15 distinct-epoch count stamps, u16 [count][9][15][15],
+// of candidates idx[0..count) (idx NULL: candidates first..first+count).
+cudaError_t launch_stamps(const CandView& v, const uint32_t* idx, uint64_t first, uint64_t count,
                           uint16_t* out, cudaStream_t s);
+
+// sas_select.cu: ascending indices of the local peaks of v's candidates (no
+// candidate within one lattice step and one bin precedes them in the output
+// order) into idx (device, room for v.n); *n_peaks on the host; synchronizes s.
+// Returns a sas_status.
+int select_peaks(const CandView& v, uint32_t* idx, uint64_t* n_peaks, cudaStream_t s);
+
+// sas_select.cu: ownership selection -- detection d belongs to the first
+// candidate (output order) whose ids contain it; candidate i is kept when it
+// owns at least half of its ids.  Same output convention as select_peaks.
+int select_owned(const CandView& v, uint32_t* idx, uint64_t* n_kept, cudaStream_t s);
+
+// sas_api.cu: the candidate view of a finished search.
+CandView result_view(const sas_result* r);
 
 // sas_probe.cu
 cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);

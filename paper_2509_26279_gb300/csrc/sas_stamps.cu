@@ -19,14 +19,15 @@ constexpr int kCells = kSide * kSide;
 // in the 15 x 15-bin window (one bucket scan per epoch), then writes the
 // popcounts.
 __global__ void __launch_bounds__(kStampThreads) k_stamps(
-    const sas_candidate* __restrict__ cands, uint64_t n, SearchGeom g, CoarseGeom cg,
+    const sas_candidate* __restrict__ cands, const uint32_t* __restrict__ idx, uint64_t first,
+    uint64_t n, SearchGeom g, CoarseGeom cg,
     const Det* __restrict__ dets, const uint32_t* __restrict__ boff,
     const uint32_t* __restrict__ ecount, const int32_t* __restrict__ sxt,
     const int32_t* __restrict__ syt, uint16_t* __restrict__ out) {
   extern __shared__ uint32_t s_mask[];  // [kCells][W]
   const uint32_t W = (g.E + 31) / 32;
   for (uint64_t c = blockIdx.x; c < n; c += gridDim.x) {
-    const sas_candidate cd = cands[c];
+    const sas_candidate cd = cands[idx ? (uint64_t)idx[c] : first + c];
     const int kx = (int)(cd.v_idx % (uint32_t)g.nvx), ky = (int)(cd.v_idx / (uint32_t)g.nvx);
     for (int q = 0; q < 9; ++q) {
       const int kx2 = kx + q % 3 - 1, ky2 = ky + q / 3 - 1;
@@ -74,16 +75,15 @@ __global__ void __launch_bounds__(kStampThreads) k_stamps(
 
 }  // namespace
 
-cudaError_t launch_stamps(const sas_candidate* cands, uint64_t n, const SearchGeom& g,
-                          const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
-                          const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
+cudaError_t launch_stamps(const CandView& v, const uint32_t* idx, uint64_t first, uint64_t count,
                           uint16_t* out, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  const size_t smem = (size_t)kCells * ((g.E + 31) / 32) * 4;
+  if (count == 0) return cudaSuccess;
+  const size_t smem = (size_t)kCells * ((v.g.E + 31) / 32) * 4;
   cudaError_t e = cudaFuncSetAttribute(k_stamps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)(n < 152ull * 16 ? n : 152ull * 16);
-  k_stamps<<<blocks, kStampThreads, smem, s>>>(cands, n, g, cg, dets, boff, ecount, sxt, syt, out);
+  const unsigned blocks = (unsigned)(count < 152ull * 16 ? count : 152ull * 16);
+  k_stamps<<<blocks, kStampThreads, smem, s>>>(v.cands, idx, first, count, v.g, v.cg, v.dets, v.boff,
+                                                v.ecount, v.sxt, v.syt, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -124,6 +124,7 @@ constexpr int kFwdSmemFloats = kCh * kQ * 9 + 2 * kCh * kCh * 9 + 3 * kCh + kQ *
                                kCh * kH1 * kH1 + kCh * kH2 * kH2;
 
 __global__ void __launch_bounds__(kFwdThreads) k_conv_fwd(const uint16_t* __restrict__ stamps,
+                                                          const uint32_t* __restrict__ idx,
                                                           uint32_t n, const __nv_bfloat16* __restrict__ wb,
                                                           __nv_bfloat16* a1g, __nv_bfloat16* a2g,
                                                           __nv_bfloat16* __restrict__ a3g) {
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_conv_fwd(const uint16_t* __rest
     bs[threadIdx.x] = ld(wb + (l == 0 ? kB1 : l == 1 ? kB2 : kB3) + o);
   }
   for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
-    const uint16_t* st = stamps + (size_t)b * kQ * kS * kS;
+    const uint16_t* st = stamps + (size_t)(idx ? idx[b] : b) * kQ * kS * kS;
     for (int i = threadIdx.x; i < kQ * kS * kS; i += blockDim.x) x0[i] = bf((float)st[i] * 0.0625f);
     __syncthreads();
     conv_fwd<kQ, kS>(x0, w1s, bs, a1, a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr);
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(256) k_fc_fwd(const __nv_bfloat16* __restrict_
 constexpr int kLossThreads = 1024;
 
 __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__ logits,
-                                                       const float* __restrict__ labels, uint32_t n,
+                                                       const float* __restrict__ labels,
+                                                       const uint32_t* __restrict__ idx, uint32_t n,
                                                        const __nv_bfloat16* __restrict__ a4g,
                                                        float* __restrict__ glogit,
                                                        float* __restrict__ grad, float* __restrict__ loss) {
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(const float* __restrict__
   const float inv_n = 1.f / (float)n;
   float l = 0.f;
   for (uint32_t b = t; b < n; b += blockDim.x) {
-    const float z = logits[b], y = labels[b];
+    const float z = logits[b], y = labels[idx ? idx[b] : b];
     l += fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
     glogit[b] = (1.f / (1.f + expf(-z)) - y) * inv_n;
   }
@@ -361,8 +363,8 @@ constexpr int kBackThreads = 256;
 template <int C, int HI, bool DX, bool STAMP>
 __global__ void __launch_bounds__(kBackThreads) k_conv_back(
     const float* __restrict__ gin, const __nv_bfloat16* __restrict__ ain,
-    const uint16_t* __restrict__ stamps, uint32_t n, const __nv_bfloat16* __restrict__ w,
-    float* __restrict__ gout, float* __restrict__ partial) {
+    const uint16_t* __restrict__ stamps, const uint32_t* __restrict__ idx, uint32_t n,
+    const __nv_bfloat16* __restrict__ w, float* __restrict__ gout, float* __restrict__ partial) {
   constexpr int HO = HI - 2, P = HO * HO, Q = HI * HI;
   constexpr int PARTS = kBackThreads / (8 * C);  // 1 for C = 32, 3 for C = 9
   static_assert(PARTS >= 1, "too many channels");
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(kBackThreads) k_conv_back(
     for (int i = t; i < kCh * P; i += blockDim.x) g_s[i] = gin[(size_t)b * kCh * P + i];
     if (STAMP) {
       for (int i = t; i < C * Q; i += blockDim.x)
-        a_s[i] = bf((float)stamps[(size_t)b * C * Q + i] * 0.0625f);
+        a_s[i] = bf((float)stamps[(size_t)(idx ? idx[b] : b) * C * Q + i] * 0.0625f);
     } else {
       for (int i = t; i < C * Q; i += blockDim.x) a_s[i] = ld(ain + (size_t)b * C * Q + i);
     }
@@ -549,37 +551,37 @@ int fwd_blocks() {
 }
 
 // Forward of n <= max_batch stamps; with keep, stores the activations training needs.
-cudaError_t forward(sas_vet* vt, const uint16_t* stamps, uint32_t n, bool keep, float* logits,
-                    cudaStream_t s) {
+cudaError_t forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* idx, uint32_t n, bool keep,
+                    float* logits, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
   k_conv_fwd<<<blocks, kFwdThreads, kFwdSmemFloats * sizeof(float), s>>>(
-      stamps, n, vt->wb, keep ? vt->a1 : nullptr, keep ? vt->a2 : nullptr, vt->a3);
+      stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr, keep ? vt->a2 : nullptr, vt->a3);
   k_fc_fwd<<<(n + kFcTB - 1) / kFcTB, 256, 0, s>>>(vt->a3, n, vt->wf1t, vt->wb, keep ? vt->a4 : nullptr,
                                                     logits);
   note_launch(2);
   return cudaGetLastError();
 }
 
-cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n,
-                      float* grad, cudaStream_t s) {
-  cudaError_t e = forward(vt, stamps, n, true, vt->logits, s);
+cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, const uint32_t* idx,
+                      uint32_t n, float* grad, cudaStream_t s) {
+  cudaError_t e = forward(vt, stamps, idx, n, true, vt->logits, s);
   if (e != cudaSuccess) return e;
-  k_loss<<<1, kLossThreads, 0, s>>>(vt->logits, labels, n, vt->a4, vt->glogit, grad, vt->loss);
+  k_loss<<<1, kLossThreads, 0, s>>>(vt->logits, labels, idx, n, vt->a4, vt->glogit, grad, vt->loss);
   k_g4<<<(unsigned)(((uint64_t)n * kHid + 255) / 256), 256, 0, s>>>(vt->glogit, vt->a4, vt->wb, n, vt->g4);
   k_fc1_dw<<<(kF + 31) / 32, 256, 0, s>>>(vt->g4, vt->a3, n, grad);
   k_fc1_dx<<<dim3((kF + 63) / 64, (n + 31) / 32), 256, 0, s>>>(vt->g4, vt->wb, vt->a3, n, vt->g3);
   const int nb = (int)std::min<uint32_t>(n, kBackBlocks);
   k_conv_back<kCh, kH2, true, false><<<nb, kBackThreads, back_smem<kCh, kH2, true>(), s>>>(
-      vt->g3, vt->a2, nullptr, n, vt->wb + kW3, vt->g2, vt->partial);
+      vt->g3, vt->a2, nullptr, nullptr, n, vt->wb + kW3, vt->g2, vt->partial);
   k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW3, kB3);
   k_conv_back<kCh, kH1, true, false><<<nb, kBackThreads, back_smem<kCh, kH1, true>(), s>>>(
-      vt->g2, vt->a1, nullptr, n, vt->wb + kW2, vt->g1, vt->partial);
+      vt->g2, vt->a1, nullptr, nullptr, n, vt->wb + kW2, vt->g1, vt->partial);
   k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW2, kB2);
   k_conv_back<kQ, kS, false, true><<<nb, kBackThreads, back_smem<kQ, kS, false>(), s>>>(
-      vt->g1, nullptr, stamps, n, vt->wb + kW1, nullptr, vt->partial);
+      vt->g1, nullptr, stamps, idx, n, vt->wb + kW1, nullptr, vt->partial);
   k_reduce_partials<<<(kCh * kQ * 9 + kCh + 255) / 256, 256, 0, s>>>(
       vt->partial, nb, kBackThreads / (8 * kQ), kCh * kQ * 9, grad, kW1, kB1);
   note_launch(10);
@@ -736,28 +738,31 @@ int sas_vet_get_bf16(const sas_vet* vt, uint16_t* out) {
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_get_bf16");
 }
 
-int sas_vet_forward(sas_vet* vt, const uint16_t* stamps, uint64_t n, float* logits, void* stream) {
+int sas_vet_forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* index, uint64_t n, float* logits,
+                    void* stream) {
   if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_forward: NULL vetter");
   if (n && (!stamps || !logits)) return set_error(SAS_ERR_ARG, "sas_vet_forward: NULL buffer");
   DeviceGuard guard(vt->device);
   cudaStream_t s = (cudaStream_t)stream;
   for (uint64_t b0 = 0; b0 < n; b0 += vt->max_batch) {
     const uint32_t nb = (uint32_t)std::min<uint64_t>(vt->max_batch, n - b0);
-    if (cudaError_t e = vet::forward(vt, stamps + b0 * 9 * 225, nb, false, logits + b0, s); e != cudaSuccess)
+    const uint16_t* st = index ? stamps : stamps + b0 * 9 * 225;
+    if (cudaError_t e = vet::forward(vt, st, index ? index + b0 : nullptr, nb, false, logits + b0, s);
+        e != cudaSuccess)
       return cuda_fail(e, "sas_vet_forward");
   }
   return SAS_OK;
 }
 
-int sas_vet_gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n, float* grad,
-                      float* loss, void* stream) {
+int sas_vet_gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, const uint32_t* index,
+                      uint32_t n, float* grad, float* loss, void* stream) {
   if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_gradients: NULL vetter");
   if (n == 0 || n > vt->max_batch)
     return set_errorf(SAS_ERR_ARG, "sas_vet_gradients: n must be 1..%u", vt->max_batch);
   if (!stamps || !labels || !grad) return set_error(SAS_ERR_ARG, "sas_vet_gradients: NULL buffer");
   DeviceGuard guard(vt->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = vet::gradients(vt, stamps, labels, n, grad, s);
+  cudaError_t e = vet::gradients(vt, stamps, labels, index, n, grad, s);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, vt->loss, 4, cudaMemcpyDeviceToDevice, s);
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_gradients");
 }
@@ -770,8 +775,8 @@ int sas_vet_apply_gradients(sas_vet* vt, const float* grad, float lr, void* stre
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_apply_gradients");
 }
 
-int sas_vet_train_step(sas_vet* vt, const uint16_t* stamps, const float* labels, uint32_t n, float lr,
-                       float* loss, void* stream) {
+int sas_vet_train_step(sas_vet* vt, const uint16_t* stamps, const float* labels, const uint32_t* index,
+                       uint32_t n, float lr, float* loss, void* stream) {
   if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_train_step: NULL vetter");
   if (n == 0 || n > vt->max_batch)
     return set_errorf(SAS_ERR_ARG, "sas_vet_train_step: n must be 1..%u", vt->max_batch);
@@ -779,7 +784,7 @@ int sas_vet_train_step(sas_vet* vt, const uint16_t* stamps, const float* labels,
   if (!(lr >= 0.f)) return set_error(SAS_ERR_ARG, "sas_vet_train_step: lr must be >= 0");
   DeviceGuard guard(vt->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = vet::gradients(vt, stamps, labels, n, vt->grad, s);
+  cudaError_t e = vet::gradients(vt, stamps, labels, index, n, vt->grad, s);
   if (e == cudaSuccess) e = vet::adam(vt, vt->grad, lr, s);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, vt->loss, 4, cudaMemcpyDeviceToDevice, s);
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_train_step");

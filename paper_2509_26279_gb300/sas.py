@@ -343,6 +343,22 @@ class Batch:
                                          ctypes.byref(ni), 0))
         return cands, ids
 
+    def peaks(self, f: int, idx_dev, stream=None) -> int:
+        n = ctypes.c_uint64()
+        _check(_lib.sas_batch_peaks(self._h, int(f), _opt_ptr(idx_dev), ctypes.byref(n),
+                                    _stream_handle(stream)))
+        return n.value
+
+    def owned(self, f: int, idx_dev, stream=None) -> int:
+        n = ctypes.c_uint64()
+        _check(_lib.sas_batch_owned(self._h, int(f), _opt_ptr(idx_dev), ctypes.byref(n),
+                                    _stream_handle(stream)))
+        return n.value
+
+    def stamps(self, f: int, idx_dev, count: int, out_dev, stream=None):
+        _check(_lib.sas_batch_stamps(self._h, int(f), _opt_ptr(idx_dev), int(count),
+                                     _opt_ptr(out_dev) if count else None, _stream_handle(stream)))
+
     def stats(self):
         ms, fb = ctypes.c_float(), ctypes.c_uint64()
         _check(_lib.sas_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(fb)))
@@ -382,14 +398,21 @@ _lib.sas_vet_set_adam.argtypes = [_p, ctypes.c_float, ctypes.c_float, ctypes.c_f
 _lib.sas_vet_set_state.argtypes = [_p, _p, _p, _p, ctypes.c_uint64]
 _lib.sas_vet_get_state.argtypes = [_p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]
 _lib.sas_vet_get_bf16.argtypes = [_p, _p]
-_lib.sas_vet_forward.argtypes = [_p, _p, ctypes.c_uint64, _p, _p]
-_lib.sas_vet_gradients.argtypes = [_p, _p, _p, ctypes.c_uint32, _p, _p, _p]
+_lib.sas_vet_forward.argtypes = [_p, _p, _p, ctypes.c_uint64, _p, _p]
+_lib.sas_vet_gradients.argtypes = [_p, _p, _p, _p, ctypes.c_uint32, _p, _p, _p]
 _lib.sas_vet_apply_gradients.argtypes = [_p, _p, ctypes.c_float, _p]
-_lib.sas_vet_train_step.argtypes = [_p, _p, _p, ctypes.c_uint32, ctypes.c_float, _p, _p]
+_lib.sas_vet_train_step.argtypes = [_p, _p, _p, _p, ctypes.c_uint32, ctypes.c_float, _p, _p]
+_lib.sas_stamps_indexed.argtypes = [_p, _p, ctypes.c_uint64, _p, _p]
+_lib.sas_peaks.argtypes = [_p, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_batch_peaks.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_batch_stamps.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64, _p, _p]
+_lib.sas_owned.argtypes = [_p, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
              "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
              "sas_vet_forward", "sas_vet_gradients", "sas_vet_apply_gradients",
-             "sas_vet_train_step"]
+             "sas_vet_train_step", "sas_stamps_indexed", "sas_peaks", "sas_batch_peaks",
+             "sas_batch_stamps", "sas_owned", "sas_batch_owned"]
 
 STAMP_SHAPE = (9, 15, 15)
 VET_MAX_BATCH = 8192
@@ -403,6 +426,35 @@ def sas_stamps(result: Result, out_dev, first: int = 0, count: int | None = None
     _check(_lib.sas_stamps(result._h, int(first), int(count), _dev_ptr(out_dev) if count else None,
                            _stream_handle(stream)))
     return count
+
+
+def sas_stamps_indexed(result: Result, idx_dev, count: int, out_dev, stream=None) -> int:
+    """Stamps of candidates idx[0..count) (device uint32 indices)."""
+    _check(_lib.sas_stamps_indexed(result._h, _dev_ptr(idx_dev) if count else None, int(count),
+                                   _dev_ptr(out_dev) if count else None, _stream_handle(stream)))
+    return count
+
+
+def sas_peaks(result: Result, idx_dev, stream=None) -> int:
+    """Local peaks: ascending candidate indices into idx_dev (device uint32 with
+    room for n_candidates); returns their number (synchronizes)."""
+    n = ctypes.c_uint64()
+    _check(_lib.sas_peaks(result._h, _dev_ptr(idx_dev) if idx_dev is not None else None, ctypes.byref(n),
+                          _stream_handle(stream)))
+    return n.value
+
+
+def sas_owned(result: Result, idx_dev, stream=None) -> int:
+    """Ownership selection: ascending kept candidate indices into idx_dev
+    (device uint32, room for n_candidates); returns their number (synchronizes)."""
+    n = ctypes.c_uint64()
+    _check(_lib.sas_owned(result._h, _dev_ptr(idx_dev) if idx_dev is not None else None, ctypes.byref(n),
+                          _stream_handle(stream)))
+    return n.value
+
+
+def _opt_ptr(a):
+    return None if a is None else _dev_ptr(a)
 
 
 def vet_num_params() -> int:
@@ -448,24 +500,25 @@ class Vetter:
         _check(_lib.sas_vet_get_bf16(self._h, raw.ctypes.data))
         return (raw.astype(np.uint32) << 16).view(np.float32)
 
-    def forward(self, stamps_dev, n: int, logits_dev, stream=None):
-        _check(_lib.sas_vet_forward(self._h, _dev_ptr(stamps_dev) if n else None, int(n),
+    def forward(self, stamps_dev, n: int, logits_dev, index=None, stream=None):
+        _check(_lib.sas_vet_forward(self._h, _dev_ptr(stamps_dev) if n else None,
+                                    _opt_ptr(index) if n else None, int(n),
                                     _dev_ptr(logits_dev) if n else None, _stream_handle(stream)))
 
-    def gradients(self, stamps_dev, labels_dev, n: int, grad_dev, loss_dev=None, stream=None):
-        _check(_lib.sas_vet_gradients(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), int(n),
-                                      _dev_ptr(grad_dev),
-                                      None if loss_dev is None else _dev_ptr(loss_dev),
+    def gradients(self, stamps_dev, labels_dev, n: int, grad_dev, loss_dev=None, index=None,
+                  stream=None):
+        _check(_lib.sas_vet_gradients(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), _opt_ptr(index),
+                                      int(n), _dev_ptr(grad_dev), _opt_ptr(loss_dev),
                                       _stream_handle(stream)))
 
     def apply_gradients(self, grad_dev, lr: float, stream=None):
         _check(_lib.sas_vet_apply_gradients(self._h, _dev_ptr(grad_dev), float(lr),
                                             _stream_handle(stream)))
 
-    def train_step(self, stamps_dev, labels_dev, n: int, lr: float, loss_dev=None, stream=None):
-        _check(_lib.sas_vet_train_step(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), int(n),
-                                       float(lr), None if loss_dev is None else _dev_ptr(loss_dev),
-                                       _stream_handle(stream)))
+    def train_step(self, stamps_dev, labels_dev, n: int, lr: float, loss_dev=None, index=None,
+                   stream=None):
+        _check(_lib.sas_vet_train_step(self._h, _dev_ptr(stamps_dev), _dev_ptr(labels_dev), _opt_ptr(index),
+                                       int(n), float(lr), _opt_ptr(loss_dev), _stream_handle(stream)))
 
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:

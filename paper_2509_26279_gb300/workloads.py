@@ -25,8 +25,7 @@ exposures over ~4 h, TNO and MBA rate ranges of Sec. 3.3 converted at
                   lattice 1001x1001 step 600 mpx/h (+-300 px/h); bin 3 px; N_min 15
   batched_fields  60 CCD fields, epochs U{20..150} over 4 h, noise/epoch log-U[1e3,8e3],
                   movers and lattice as decam_tno; bin 2 px; N_min = ceil(E/4)
-  vetter_fields   as batched_fields with magnitudes U[23,26.5] (p 0.9 -> 0.06) and 40
-                  stationary artifacts per field (p ~ U[0.5,1])
+  vetter_fields   as batched_fields with magnitudes U[23,26.5] (p 0.9 -> 0.06)
 """
 from __future__ import annotations
 
@@ -248,16 +247,17 @@ def vetter_fields(n_fields: int, seed: int = BASE_SEED + 5) -> List[Workload]:
     lattice and bin of decam_tno with the batched spread of epochs (U{20..150})
     and noise (log-U[1e3, 8e3]); mover magnitudes extended to U[23, 26.5] with
     the same detection-probability slope (p = 0.9 at m = 23 down to 0.06 at
-    m = 26.5), and 40 stationary artifacts per field detected with p ~ U[0.5, 1]
-    (a source at rest: count near E at zero velocity).  n_min is the plain
-    threshold ceil(E/4)."""
+    m = 26.5).  n_min is the plain threshold ceil(E/4).  (Stationary artifacts
+    are left out: a count stamp holds no absolute velocity, so a source at rest
+    looks like a mover at its own velocity; the search's speed annulus is what
+    excludes them.)"""
     rng = np.random.default_rng(seed)
     out = []
     for f in range(n_fields):
         E = int(rng.integers(20, 151))
         noise = int(round(math.exp(rng.uniform(math.log(1e3), math.log(8e3)))))
         r = FieldRecipe(2048, 4096, E, 4.0, noise, 200, (0.5, 20.0), (0.9, 0.06),
-                        mag_range=(23.0, 26.5), n_static=40)
+                        mag_range=(23.0, 26.5))
         out.append(Workload(f"vetter_fields[{f}]", r, field_grid(2048, 4096, 2000, 364, 55),
                             -(-E // 4), seed * 1000 + f))
     return out

@@ -271,3 +271,115 @@ def test_training_reduces_loss_on_separable_stamps():
         if i % 10 == 0:
             losses.append(float(loss.item()))
     assert losses[-1] < 0.1 * losses[0], losses
+
+
+# ---- local peaks and indexed stamps ---------------------------------------------------
+
+from oracle import peaks as OP  # noqa: E402
+
+
+def gpu_peaks(res):
+    n = res.info()["n_candidates"]
+    idx = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    k = sas.sas_peaks(res, idx)
+    return idx[:k].cpu().numpy().astype(np.int64), idx
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_peaks_random_tiny(seed):
+    cat, grid, n_min = cases.random_tiny(seed + 900)
+    res = sas.stack_catalog(sas.Grid(grid), cat, max(1, n_min - 1))
+    ref = oracle.stack(cat, grid, max(1, n_min - 1))
+    got, _ = gpu_peaks(res)
+    want = OP.peaks(ref.cands["v_idx"], ref.cands["bx"], ref.cands["by"], grid.nvx)
+    assert np.array_equal(got, want)
+
+
+def test_peaks_and_indexed_stamps_tno_like():
+    w = W.scaled(W.decam_tno(), frac_noise=0.3, width_px=1024, height_px=1024, grid_half=25)
+    cat = W.load(w)
+    res = sas.stack_catalog(sas.Grid(w.grid), cat, 12)
+    ref = oracle.stack(cat, w.grid, 12)
+    got, idx = gpu_peaks(res)
+    want = OP.peaks(ref.cands["v_idx"], ref.cands["bx"], ref.cands["by"], w.grid.nvx)
+    assert np.array_equal(got, want) and 0 < len(got) < len(ref.cands)
+    k = min(len(got), 60)
+    out = torch.zeros((k, 9, 15, 15), dtype=torch.int16, device="cuda")
+    sas.sas_stamps_indexed(res, idx, k, out)
+    torch.cuda.synchronize()
+    st = out.cpu().numpy().view(np.uint16).astype(np.int64)
+    cells = np.stack([ref.cands["v_idx"], ref.cands["bx"], ref.cands["by"]], 1)[want[:k]]
+    assert np.array_equal(st, V.stamps(cat, w.grid, cells))
+
+
+def test_batch_peaks_and_stamps_equal_single_field():
+    ws = W.vetter_fields(3, seed=77)
+    ws = [W.scaled(w, frac_noise=0.2, width_px=1024, height_px=1024, grid_half=25) for w in ws]
+    fields, keep = [], []
+    for w in ws:
+        cat = W.load(w)
+        g = sas.Grid(w.grid)
+        dx, dy = torch.from_numpy(cat.x).cuda(), torch.from_numpy(cat.y).cuda()
+        de = torch.from_numpy(cat.epoch.view(np.int16)).cuda()
+        n_low = max(6, -(-w.recipe.n_epochs // 10))
+        fields.append((g, dx, dy, de, cat.t, cat.ticks_per_hour, n_low))
+        keep.append((cat, w, n_low))
+    b = sas.Batch(fields)
+    b.run()
+    for f, (cat, w, n_low) in enumerate(keep):
+        single = sas.stack_catalog(sas.Grid(w.grid), cat, n_low)
+        n = single.info()["n_candidates"]
+        idx_b = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+        kb = b.peaks(f, idx_b)
+        ps, idx_s = gpu_peaks(single)
+        assert kb == len(ps) and np.array_equal(idx_b[:kb].cpu().numpy(), ps)
+        sb = torch.zeros((max(kb, 1), 9, 15, 15), dtype=torch.int16, device="cuda")
+        ss = torch.zeros_like(sb)
+        b.stamps(f, idx_b, kb, sb)
+        sas.sas_stamps_indexed(single, idx_s, kb, ss)
+        torch.cuda.synchronize()
+        assert torch.equal(sb, ss)
+
+
+# ---- ownership selection ------------------------------------------------------------
+
+from oracle import owned as OO  # noqa: E402
+
+
+def gpu_owned(res):
+    n = res.info()["n_candidates"]
+    idx = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    k = sas.sas_owned(res, idx)
+    return idx[:k].cpu().numpy().astype(np.int64), idx
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_owned_random_tiny(seed):
+    cat, grid, n_min = cases.random_tiny(seed + 1300)
+    res = sas.stack_catalog(sas.Grid(grid), cat, max(1, n_min - 1))
+    ref = oracle.stack(cat, grid, max(1, n_min - 1))
+    got, _ = gpu_owned(res)
+    assert np.array_equal(got, OO.owned(ref.id_lists()))
+
+
+def test_owned_tno_like_and_batch():
+    ws = [W.scaled(w, frac_noise=0.3, width_px=1024, height_px=1024, grid_half=25)
+          for w in W.vetter_fields(2, seed=91)]
+    fields, keep = [], []
+    for w in ws:
+        cat = W.load(w)
+        fields.append((sas.Grid(w.grid), torch.from_numpy(cat.x).cuda(), torch.from_numpy(cat.y).cuda(),
+                       torch.from_numpy(cat.epoch.view(np.int16)).cuda(), cat.t, cat.ticks_per_hour, 8))
+        keep.append((cat, w))
+    b = sas.Batch(fields)
+    b.run()
+    for f, (cat, w) in enumerate(keep):
+        res = sas.stack_catalog(sas.Grid(w.grid), cat, 8)
+        ref = oracle.stack(cat, w.grid, 8)
+        got, _ = gpu_owned(res)
+        want = OO.owned(ref.id_lists())
+        assert np.array_equal(got, want) and 0 < len(want) < len(ref.cands)
+        n = res.info()["n_candidates"]
+        idx_b = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+        kb = b.owned(f, idx_b)
+        assert np.array_equal(idx_b[:kb].cpu().numpy().astype(np.int64), want)

@@ -1,0 +1,14 @@
+"""Threshold calibration of the vetter (host logic)."""
+import numpy as np
+
+from paper_2509_26279_gb300 import vetting
+
+
+def test_calibrate_picks_lowest_threshold_meeting_purity():
+    logits = np.array([5.0, 4.0, 3.0, 2.0, 1.0, 0.0])
+    labels = np.array([1, 1, 0, 1, 0, 0])
+    # precision from the top: 1, 1, 2/3, 3/4, 3/5, 1/2
+    assert vetting.calibrate(logits, labels, 0.75) == 2.0
+    assert vetting.calibrate(logits, labels, 0.95) == 4.0
+    assert vetting.calibrate(logits, labels, 0.5) == 0.0
+    assert vetting.calibrate(logits, np.zeros(6), 0.5) == float("inf")
