@@ -160,8 +160,9 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     """fields/s on the batched uneven fields (60 CCDs, epochs U{20..150}, noise
     log-U[1e3, 8e3]): the plain form (one sas_stack per field at N_min =
     ceil(E/4)) against the batched + vetted form (one graph-captured batch
-    pass, then ownership selection, stamps and the CNN per field), at the plain
-    threshold and at the lowered one; recall per 0.5-mag bin and purity of each
+    pass, then ownership selection, stamps and the CNN), at the plain
+    threshold and at the lowered one (sas_batch_vet: ownership, stamps and CNN of
+    all fields in one pass); recall per 0.5-mag bin and purity of each
     form's reported candidates.  The vetter is trained first (not timed) on
     separate seeded fields."""
     import torch
@@ -225,20 +226,15 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
         return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
                          stream=stream)
 
-    def vetted_pass(batch):
+    def vetted_pass(batch, cap):
+        fo = torch.empty(cap, dtype=torch.int32, device=dev)
+        co = torch.empty(cap, dtype=torch.int32, device=dev)
+        lo = torch.empty(cap, dtype=torch.float32, device=dev)
+
         def run():
             batch.run(stream)
-            out = []
-            for k in range(len(fields)):
-                n = batch.field_info(k)["n_candidates"]
-                idx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
-                kept = batch.owned(k, idx, stream)
-                stamps = torch.empty((max(kept, 1), 9, 15, 15), dtype=torch.int16, device=dev)
-                batch.stamps(k, idx, kept, stamps, stream)
-                logits = torch.empty(max(kept, 1), dtype=torch.float32, device=dev)
-                vt.forward(stamps, kept, logits, stream=stream)
-                out.append((idx, logits, kept))
-            return out
+            n = batch.vet(vt, fo, co, lo, cap, stream)
+            return fo[:n], co[:n], lo[:n]
         return run
 
     result = {"workload": f"batched_fields: {n_fields} CCDs 2048x4096 px, epochs U{{20..150}} over 4 h, "
@@ -253,17 +249,21 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                             ("batched_vetted_low", lambda f: vetting.n_low(f.E),
                              "batch at N_min = max(5, ceil(E/14))")):
         batch = make_batch(thr)
-        ms, out = timed(vetted_pass(batch))
+        batch.run(stream)
+        cap = sum(max(batch.field_info(k)["n_candidates"], 1) for k in range(len(fields))) + 1
+        ms, (fo, co, lo) = timed(vetted_pass(batch, cap))
+        fo, co, lo = fo.cpu().numpy(), co.cpu().numpy(), lo.cpu().numpy()
         per_field = []
-        for k, (idx, logits, kept) in enumerate(out):
+        for k in range(len(fields)):
             c, i = batch.candidates(k)
-            sel = idx[:kept].cpu().numpy().astype(np.int64)
-            keep = sel[logits[:kept].cpu().numpy() >= tau]
+            sel = fo == k
+            idx = co[sel]
             mask = np.zeros(len(c), bool)
-            mask[keep] = True
+            mask[idx[vetting.vetted_keep(c["count"][idx], lo[sel], fields[k].w.n_min, tau)]] = True
             per_field.append((c, i, mask))
         _, fallbacks = batch.stats()
-        result[name] = {"form": desc + ", ownership selection, CNN logit >= calibrated threshold",
+        result[name] = {"form": desc + ", ownership selection; kept when count >= ceil(E/4) or the CNN "
+                                       "logit >= the calibrated threshold",
                         "ms": round(ms, 3),
                         "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
                         **score(per_field)}

@@ -208,7 +208,7 @@ void sas_result_free(sas_result* result);
  * the caller may rewrite their contents between runs (same sizes, same
  * epoch times) and must keep them alive until sas_batch_destroy.
  * sas_batch_run replays the pass on `stream` and synchronizes; a field that
- * exceeded the batch's fixed capacities (emissions, 8192 candidates, ids) or
+ * exceeded the batch's fixed capacities (emissions, 32768 candidates, ids) or
  * whose counters wrapped is recomputed by sas_stack, so every field's result
  * equals sas_stack's.  Results stay valid until the next run.
  * Errors: as sas_stack; SAS_ERR_ARG for fields that cannot share a launch. */
@@ -232,6 +232,22 @@ int sas_batch_stamps(const sas_batch* batch, uint32_t field, const uint32_t* idx
                      uint16_t* out, void* stream);
 int sas_batch_owned(const sas_batch* batch, uint32_t field, uint32_t* idx, uint64_t* n_kept,
                     void* stream);
+
+typedef struct sas_vet sas_vet;
+
+/* Vetting of every field of the last run in one pass: ownership selection
+ * (as sas_owned), stamps of the kept candidates and their CNN logits (as
+ * sas_vet_forward).  Writes one item per kept candidate: field_out[i],
+ * cand_out[i] (its index in the field's candidate list) and logit_out[i]
+ * (device arrays with room for `cap` items; the batch's total candidate count
+ * always suffices), *n_out on the host.  Items are grouped by field, candidate
+ * indices ascending within a field; the fields searched in the batch come
+ * first in field order, then any field recomputed on the single-field path.
+ * The vetter must live on the batch's device.  Synchronizes the stream.
+ * Errors: SAS_ERR_ARG, SAS_ERR_OVERFLOW (cap too small), SAS_ERR_OOM,
+ * SAS_ERR_CUDA. */
+int sas_batch_vet(const sas_batch* batch, sas_vet* vetter, uint32_t* field_out, uint32_t* cand_out,
+                  float* logit_out, uint64_t cap, uint64_t* n_out, void* stream);
 
 /* Autotuner: times sas_stack on (grid, cat, n_min) for each candidate pair of
  * superbin in {1, 2, 3} and velocity_block in {1, 2, 4, 8} (other fields of

@@ -168,8 +168,8 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     const sas_catalog& c = b->cats[f];
     det_off[f + 1] = det_off[f] + c.n;
     tab_off[f + 1] = tab_off[f] + (unsigned long long)(fp.g.nvx + fp.g.nvy) * fp.g.E;
-    const uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * c.n, 1u << 16), 1u << 24);
-    const uint32_t key_cap = kBatchSortMax;
+    const uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * c.n, 1u << 18), 1u << 24);
+    const uint32_t key_cap = kBatchKeyCap;
     emit_off[f + 1] = emit_off[f] + emit_cap;
     cand_off[f + 1] = cand_off[f] + key_cap;
     bucket_base[f + 1] = bucket_base[f] + fp.nb;
@@ -177,7 +177,7 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     fill_stack_args(fp, b->n_min[f], &hargs[f]);
     unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
     b->key_cap.push_back(key_cap);
-    b->ids_cap.push_back((uint64_t)key_cap * (fp.g.E + 8));
+    b->ids_cap.push_back((uint64_t)key_cap * (fp.g.E / 2 + 8));
   }
   BatchDev& B = b->dev;
   B.n_fields = (int)n_fields;
@@ -214,6 +214,7 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
   regs.push_back({(void**)&B.scan_scratch, scan_scratch_elems(B.total_buckets) * 4});
   regs.push_back({(void**)&B.bucket_of, B.total_dets * 4});
   regs.push_back({(void**)&B.dets, B.total_dets * sizeof(Det)});
+  regs.push_back({(void**)&B.keys_all, B.total_cand * sizeof(Key)});
   for (uint32_t f = 0; f < n_fields; ++f) {
     const FieldPlan& fp = b->plans[f];
     regs.push_back({(void**)&f_t[f], fp.g.E * 8});
@@ -221,7 +222,6 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     regs.push_back({(void**)&f_sxt[f], (size_t)fp.g.nvx * fp.g.E * 4});
     regs.push_back({(void**)&f_syt[f], (size_t)fp.g.nvy * fp.g.E * 4});
     regs.push_back({(void**)&f_emits[f], (emit_off[f + 1] - emit_off[f]) * sizeof(Emit)});
-    regs.push_back({(void**)&f_keys[f], (size_t)b->key_cap[f] * sizeof(Key)});
     regs.push_back({(void**)&f_idoff[f], ((size_t)b->key_cap[f] + 1) * 8});
     regs.push_back({(void**)&f_ids[f], b->ids_cap[f] * 4});
     regs.push_back({(void**)&f_idt[f], b->ids_cap[f] * 4});
@@ -237,6 +237,7 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
       off += align256(std::max<size_t>(r.bytes, 1));
     }
   }
+  for (uint32_t f = 0; f < n_fields; ++f) f_keys[f] = B.keys_all + cand_off[f];
   if ((ce = cudaMallocHost((void**)&b->h_ctr, (size_t)n_fields * kCtrN * 4)) != cudaSuccess ||
       (ce = cudaMallocHost((void**)&b->h_c64, (size_t)n_fields * kC64N * 8)) != cudaSuccess) {
     rc = cuda_err(ce, "pinned counters");
@@ -456,6 +457,113 @@ int sas_batch_stamps(const sas_batch* b, uint32_t field, const uint32_t* idx, ui
   if (!out) return set_error(SAS_ERR_ARG, "null stamp buffer");
   cudaError_t e = launch_stamps(v, idx, 0, count, out, (cudaStream_t)stream);
   return e == cudaSuccess ? SAS_OK : cuda_err(e, "batch stamps");
+}
+
+}  // extern "C"
+
+namespace {
+
+__global__ void k_fill_u32(uint32_t* p, uint64_t n, uint32_t v) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Device scratch of one sas_batch_vet call, released in stream order.
+struct VetScratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit VetScratch(cudaStream_t st) : s(st) {}
+  ~VetScratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), s);
+    if (e == cudaSuccess) {
+      ptrs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int sas_batch_vet(const sas_batch* b, sas_vet* vt, uint32_t* field_out, uint32_t* cand_out, float* logit_out,
+                  uint64_t cap, uint64_t* n_out, void* stream) {
+  if (!b || !vt || !n_out) return set_error(SAS_ERR_ARG, "null argument");
+  *n_out = 0;
+  if (vet_device(vt) != b->device) return set_error(SAS_ERR_ARG, "vetter and batch live on different devices");
+  cudaStream_t s = (cudaStream_t)stream;
+  const BatchDev& B = b->dev;
+  VetScratch sc(s);
+  uint8_t* d_active = nullptr;
+  uint32_t *owner = nullptr, *flag = nullptr, *off = nullptr, *scratch = nullptr;
+  std::vector<uint8_t> active(b->n_fields);
+  uint32_t max_e = 1;
+  for (uint32_t f = 0; f < b->n_fields; ++f) {
+    active[f] = b->fallback[f] ? 0 : 1;
+    max_e = std::max(max_e, b->hf[f].E);
+  }
+  cudaError_t e = sc.alloc(&d_active, b->n_fields);
+  if (e == cudaSuccess) e = sc.alloc(&owner, B.total_dets);
+  if (e == cudaSuccess) e = sc.alloc(&flag, B.total_cand);
+  if (e == cudaSuccess) e = sc.alloc(&off, B.total_cand + 1);
+  if (e == cudaSuccess) e = sc.alloc(&scratch, scan_scratch_elems(B.total_cand));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_active, active.data(), b->n_fields, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(owner, 0xFF, std::max<uint64_t>(B.total_dets, 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, std::max<uint64_t>(B.total_cand, 1) * 4, s);
+  if (e == cudaSuccess) e = batch_launch_owned(B, d_active, owner, flag, s);
+  if (e == cudaSuccess) e = launch_scan_u32(flag, off, B.total_cand, scratch, s);
+  uint32_t n_batched = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n_batched, off + B.total_cand, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(e, "batch vetting");
+  if (n_batched > cap) return set_errorf(SAS_ERR_OVERFLOW, "room for %llu items, %u needed", (unsigned long long)cap, n_batched);
+  if (n_batched && (!field_out || !cand_out || !logit_out)) return set_error(SAS_ERR_ARG, "null output buffer");
+  if (n_batched) e = batch_launch_compact(B, flag, off, field_out, cand_out, s);
+  // fields recomputed on the single-field path follow, each from its own result
+  uint64_t n = n_batched;
+  std::vector<std::pair<uint32_t, uint64_t>> fb_spans;  // (field, count) in output order
+  for (uint32_t f = 0; f < b->n_fields && e == cudaSuccess; ++f) {
+    if (!b->fallback[f]) continue;
+    const CandView v = result_view(b->fallback[f]);
+    if (v.n == 0) continue;
+    uint32_t* idx = nullptr;
+    if ((e = sc.alloc(&idx, v.n)) != cudaSuccess) break;
+    uint64_t k = 0;
+    if (int rc = select_owned(v, idx, &k, s)) return rc;
+    if (n + k > cap) return set_errorf(SAS_ERR_OVERFLOW, "room for %llu items, more needed", (unsigned long long)cap);
+    if (k && (!field_out || !cand_out || !logit_out)) return set_error(SAS_ERR_ARG, "null output buffer");
+    if (k) {
+      k_fill_u32<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(field_out + n, k, f);
+      note_launch();
+      e = cudaMemcpyAsync(cand_out + n, idx, k * 4, cudaMemcpyDeviceToDevice, s);
+    }
+    fb_spans.push_back({f, k});
+    n += k;
+  }
+  uint16_t* stamps = nullptr;
+  if (e == cudaSuccess && n) e = sc.alloc(&stamps, n * 9 * 225);
+  if (e == cudaSuccess && n_batched)
+    e = launch_batch_stamps(B.fields, max_e, field_out, cand_out, n_batched, stamps, s);
+  {
+    uint64_t pos = n_batched;
+    for (const auto& fs : fb_spans) {
+      if (e != cudaSuccess) break;
+      if (fs.second)
+        e = launch_stamps(result_view(b->fallback[fs.first]), cand_out + pos, 0, fs.second, stamps + pos * 9 * 225, s);
+      pos += fs.second;
+    }
+  }
+  if (e == cudaSuccess && n) e = vet_forward_all(vt, stamps, n, logit_out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_err(e, "batch vetting");
+  *n_out = n;
+  return SAS_OK;
 }
 
 int sas_batch_stats(const sas_batch* b, float* ms_last, uint64_t* fallbacks) {

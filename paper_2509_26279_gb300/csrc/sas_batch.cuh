@@ -18,9 +18,10 @@ enum : int {
 // Per-field 64-bit counters.
 enum : int { kC64Pairs = 0, kC64Balance = 1, kC64T0 = 2, kC64N = 4 };
 
-// Largest number of candidates of one field the in-shared-memory sort handles;
-// a field with more falls back to the single-field path.
-constexpr uint32_t kBatchSortMax = 8192;
+// Candidate-key slots of one field (a power of two: every field's keys form one
+// segment of a segmented sort); a field with more falls back to the
+// single-field path.
+constexpr uint32_t kBatchKeyCap = 32768;
 
 // Everything the batch kernels need to know about one field.
 struct BatchField {
@@ -67,10 +68,24 @@ struct BatchDev {
   unsigned long long total_emit;
   unsigned long long* cand_off;  // [n_fields + 1] candidate slots
   unsigned long long total_cand;
+  Key* keys_all;                 // [total_cand]: field f's keys at cand_off[f]
 };
 
 cudaError_t batch_launch_prep(const BatchDev& B, cudaStream_t s);
 cudaError_t batch_launch_post(const BatchDev& B, cudaStream_t s);
 cudaError_t batch_set_attrs();
+
+// Vetting of a batch (sas_batch_vet): ownership selection of every active
+// field's candidates in one pass over the arena.  active[f] != 0 for fields whose
+// results are in the arena; owner has total_dets words (all 0xFFFFFFFF on entry),
+// flag total_cand words (all 0 on entry).  Then the in-order compaction of the
+// flags into (field, candidate) pairs.
+cudaError_t batch_launch_owned(const BatchDev& B, const uint8_t* active, uint32_t* owner, uint32_t* flag,
+                               cudaStream_t s);
+cudaError_t batch_launch_compact(const BatchDev& B, const uint32_t* flag, const uint32_t* off,
+                                 uint32_t* field_out, uint32_t* cand_out, cudaStream_t s);
+// Stamps of (field[i], cand[i]) pairs (sas_stamps.cu); max_e: largest epoch count.
+cudaError_t launch_batch_stamps(const BatchField* F, uint32_t max_e, const uint32_t* field, const uint32_t* cand,
+                                uint64_t n, uint16_t* out, cudaStream_t s);
 
 }  // namespace sas

@@ -147,17 +147,13 @@ constexpr int kWarps = 8;
 
 // Exact counts of every bin of every emitted super-bin of every field; one warp
 // per emission slot (slots beyond a field's emission count exit).
-__global__ void k_batch_cell_count(const BatchField* __restrict__ F, int n_fields,
-                                   const unsigned long long* __restrict__ emit_off,
-                                   const Det* __restrict__ dets, const uint32_t* __restrict__ boff) {
-  const unsigned long long w = blockIdx.x * (unsigned long long)kWarps + (threadIdx.x >> 5);
+// Grid: x blocks per field, y = field; each warp walks the field's emissions.
+__global__ void k_batch_cell_count(const BatchField* __restrict__ F, const Det* __restrict__ dets,
+                                   const uint32_t* __restrict__ boff) {
   const int lane = threadIdx.x & 31;
-  if (w >= emit_off[n_fields]) return;
-  const int f = find_field(emit_off, n_fields, w);
-  const BatchField& bf = F[f];
-  const unsigned long long j = w - emit_off[f];
+  const BatchField& bf = F[blockIdx.y];
   const uint32_t n_emit = min(bf.counters[kCtrEmit], bf.emit_cap);
-  if (j >= n_emit) return;
+  for (uint32_t j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < n_emit; j += gridDim.x * kWarps) {
   const SearchGeom& g = bf.args.g;
   const CoarseGeom& cg = bf.args.cg;
   const Emit em = bf.args.emits[j];
@@ -215,47 +211,33 @@ __global__ void k_batch_cell_count(const BatchField* __restrict__ F, int n_field
       }
     }
   }
+  }
 }
 
-// One block per field: bitonic sort of the field's valid keys in shared memory
-// (up to kBatchSortMax keys; more sets the field's capacity flag), then the
-// exclusive scan of the raw counts of the first n_out keys into id offsets.
-__global__ void __launch_bounds__(1024) k_batch_sort_offsets(const BatchField* __restrict__ F) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Key* s = reinterpret_cast<Key*>(smem);
+// Keys slots beyond a field's valid keys get the maximum key, so the segmented
+// sort leaves the valid keys first; a field with more valid keys than slots
+// gets its capacity flag (and is recomputed on the single-field path).
+__global__ void k_batch_pad(const BatchField* __restrict__ F, Key* __restrict__ keys_all, uint64_t total) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const BatchField& bf = F[i / kBatchKeyCap];
+  const uint32_t local = (uint32_t)(i % kBatchKeyCap);
+  const uint32_t n_valid = bf.counters[kCtrValid];
+  if (local >= n_valid) keys_all[i] = max_key_b();
+  if (local == 0 && n_valid > kBatchKeyCap) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+}
+
+// One block per field, after the sort: the exclusive scan of the raw counts of
+// the first n_out keys gives the id offsets.
+__global__ void __launch_bounds__(1024) k_batch_offsets(const BatchField* __restrict__ F) {
   __shared__ unsigned long long s_warp[33];
   const BatchField& bf = F[blockIdx.x];
-  const uint32_t n_valid = bf.counters[kCtrValid];
-  if (n_valid > kBatchSortMax || n_valid > bf.key_cap) {
-    if (threadIdx.x == 0) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
-    return;
-  }
-  uint32_t n_pad = 1;
-  while (n_pad < n_valid) n_pad <<= 1;
-  for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) s[i] = i < n_valid ? bf.keys[i] : max_key_b();
-  __syncthreads();
-  for (uint32_t k = 2; k <= n_pad; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < n_pad; i += blockDim.x) {
-        const uint32_t ixj = i ^ j;
-        if (ixj > i) {
-          const bool asc = (i & k) == 0;
-          if (key_less_b(s[ixj], s[i]) == asc) {
-            const Key t = s[i];
-            s[i] = s[ixj];
-            s[ixj] = t;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
+  const uint32_t n_valid = min(bf.counters[kCtrValid], kBatchKeyCap);
   const uint32_t n_out = min(n_valid, bf.max_out);
   unsigned long long carry = 0;
   for (uint32_t base = 0; base < n_out; base += blockDim.x) {
     const uint32_t i = base + threadIdx.x;
-    const unsigned long long r = i < n_out ? (unsigned long long)(~(uint32_t)s[i].a) : 0ull;
-    // block exclusive scan of r
+    const unsigned long long r = i < n_out ? (unsigned long long)(~(uint32_t)bf.keys[i].a) : 0ull;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long inc = r;
     for (int o = 1; o < 32; o <<= 1) {
@@ -276,10 +258,7 @@ __global__ void __launch_bounds__(1024) k_batch_sort_offsets(const BatchField* _
       if (lane == nw - 1) s_warp[32] = sc;
     }
     __syncthreads();
-    if (i < n_out) {
-      bf.keys[i] = s[i];
-      bf.id_off[i] = carry + s_warp[w] + inc - r;
-    }
+    if (i < n_out) bf.id_off[i] = carry + s_warp[w] + inc - r;
     carry += s_warp[32];
     __syncthreads();
   }
@@ -294,19 +273,15 @@ __global__ void __launch_bounds__(1024) k_batch_sort_offsets(const BatchField* _
 
 // Contributing ids (ascending) and the candidate records of every field; one
 // warp per candidate slot.
-__global__ void k_batch_ids(const BatchField* __restrict__ F, int n_fields,
-                            const unsigned long long* __restrict__ cand_off,
-                            const Det* __restrict__ dets, const uint32_t* __restrict__ boff) {
+// Grid: x blocks per field, y = field; each warp walks the field's candidates.
+__global__ void k_batch_ids(const BatchField* __restrict__ F, const Det* __restrict__ dets,
+                            const uint32_t* __restrict__ boff) {
   __shared__ uint32_t s_cursor[kWarps];
   const int wl = threadIdx.x >> 5;
-  const unsigned long long w = blockIdx.x * (unsigned long long)kWarps + wl;
   const int lane = threadIdx.x & 31;
-  if (w >= cand_off[n_fields]) return;
-  const int f = find_field(cand_off, n_fields, w);
-  const BatchField& bf = F[f];
-  const unsigned long long c = w - cand_off[f];
-  const uint32_t n_out = bf.counters[kCtrOut];
-  if (c >= n_out || (bf.counters[kCtrFlags] & kFlagEmitCap)) return;
+  const BatchField& bf = F[blockIdx.y];
+  const uint32_t n_out = (bf.counters[kCtrFlags] & kFlagEmitCap) ? 0u : bf.counters[kCtrOut];
+  for (uint32_t c = blockIdx.x * kWarps + wl; c < n_out; c += gridDim.x * kWarps) {
   const SearchGeom& g = bf.args.g;
   const CoarseGeom& cg = bf.args.cg;
   const Key key = bf.keys[c];
@@ -351,14 +326,59 @@ __global__ void k_batch_ids(const BatchField* __restrict__ F, int n_fields,
   __syncwarp();
   if (s_cursor[wl] != raw) {
     if (lane == 0) atomicOr(bf.counters + kCtrFlags, kFlagInternal);
-    return;
+  } else {
+    for (uint32_t i = lane; i < raw; i += 32) {
+      const uint32_t v = bf.ids_tmp[off + i];
+      uint32_t r = 0;
+      for (uint32_t j = 0; j < raw; ++j) r += bf.ids_tmp[off + j] < v;
+      bf.ids[off + r] = v;
+    }
   }
-  for (uint32_t i = lane; i < raw; i += 32) {
-    const uint32_t v = bf.ids_tmp[off + i];
-    uint32_t r = 0;
-    for (uint32_t j = 0; j < raw; ++j) r += bf.ids_tmp[off + j] < v;
-    bf.ids[off + r] = v;
+  __syncwarp();  // the cursor is reset for the next candidate only after every lane read it
   }
+}
+
+// Ownership over a batch: grid x blocks per field, y = field; warp per candidate.
+__global__ void k_batch_owner(const BatchField* __restrict__ F, const unsigned long long* __restrict__ det_off,
+                              const uint8_t* __restrict__ active, uint32_t* __restrict__ owner) {
+  const int f = blockIdx.y;
+  if (!active[f]) return;
+  const BatchField& bf = F[f];
+  const uint32_t n_out = bf.counters[kCtrOut];
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t* own = owner + det_off[f];
+  for (uint32_t c = blockIdx.x * kWarps + (threadIdx.x >> 5); c < n_out; c += gridDim.x * kWarps) {
+    const sas_candidate cd = bf.cands[c];
+    for (uint32_t j = lane; j < cd.id_len; j += 32) atomicMin(&own[bf.ids[cd.id_off + j]], c);
+  }
+}
+
+__global__ void k_batch_owned_flag(const BatchField* __restrict__ F, const unsigned long long* __restrict__ det_off,
+                                   const unsigned long long* __restrict__ cand_off, const uint8_t* __restrict__ active,
+                                   const uint32_t* __restrict__ owner, uint32_t* __restrict__ flag) {
+  const int f = blockIdx.y;
+  if (!active[f]) return;
+  const BatchField& bf = F[f];
+  const uint32_t n_out = bf.counters[kCtrOut];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t* own = owner + det_off[f];
+  for (uint32_t c = blockIdx.x * kWarps + (threadIdx.x >> 5); c < n_out; c += gridDim.x * kWarps) {
+    const sas_candidate cd = bf.cands[c];
+    uint32_t mine = 0;
+    for (uint32_t j = lane; j < cd.id_len; j += 32) mine += own[bf.ids[cd.id_off + j]] == c;
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if (lane == 0) flag[cand_off[f] + c] = 2ull * mine >= cd.id_len;
+  }
+}
+
+__global__ void k_batch_compact(const unsigned long long* __restrict__ cand_off, int n_fields, uint64_t total,
+                                const uint32_t* __restrict__ flag, const uint32_t* __restrict__ off,
+                                uint32_t* __restrict__ field_out, uint32_t* __restrict__ cand_out) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= total || !flag[i]) return;
+  const int f = find_field(cand_off, n_fields, i);
+  field_out[off[i]] = (uint32_t)f;
+  cand_out[off[i]] = (uint32_t)(i - cand_off[f]);
 }
 
 unsigned grid_for(unsigned long long n, int threads) {
@@ -388,18 +408,34 @@ cudaError_t batch_launch_prep(const BatchDev& B, cudaStream_t s) {
 }
 
 cudaError_t batch_launch_post(const BatchDev& B, cudaStream_t s) {
-  k_batch_cell_count<<<(unsigned)((B.total_emit + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
-      B.fields, B.n_fields, B.emit_off, B.dets, B.boff);
-  k_batch_sort_offsets<<<B.n_fields, 1024, kBatchSortMax * sizeof(Key), s>>>(B.fields);
-  k_batch_ids<<<(unsigned)((B.total_cand + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
-      B.fields, B.n_fields, B.cand_off, B.dets, B.boff);
-  note_launch(3);
+  k_batch_cell_count<<<dim3(64, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.dets, B.boff);
+  k_batch_pad<<<(unsigned)((B.total_cand + 255) / 256), 256, 0, s>>>(B.fields, B.keys_all, B.total_cand);
+  note_launch(2);
+  cudaError_t e = launch_sort_segments(B.keys_all, (uint32_t)B.total_cand, kBatchKeyCap, s);
+  if (e != cudaSuccess) return e;
+  k_batch_offsets<<<B.n_fields, 1024, 0, s>>>(B.fields);
+  k_batch_ids<<<dim3(32, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.dets, B.boff);
+  note_launch(2);
   return cudaGetLastError();
 }
 
-cudaError_t batch_set_attrs() {
-  return cudaFuncSetAttribute(k_batch_sort_offsets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kBatchSortMax * sizeof(Key)));
+cudaError_t batch_set_attrs() { return cudaSuccess; }
+
+cudaError_t batch_launch_owned(const BatchDev& B, const uint8_t* active, uint32_t* owner, uint32_t* flag,
+                               cudaStream_t s) {
+  k_batch_owner<<<dim3(32, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.det_off, active, owner);
+  k_batch_owned_flag<<<dim3(32, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.det_off, B.cand_off, active, owner,
+                                                                    flag);
+  note_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_launch_compact(const BatchDev& B, const uint32_t* flag, const uint32_t* off,
+                                 uint32_t* field_out, uint32_t* cand_out, cudaStream_t s) {
+  k_batch_compact<<<(unsigned)((B.total_cand + 255) / 256), 256, 0, s>>>(B.cand_off, B.n_fields, B.total_cand,
+                                                                       flag, off, field_out, cand_out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace sas

@@ -188,6 +188,9 @@ cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, co
                               uint32_t n_min, Key* keys, uint32_t* n_valid,
                               unsigned long long* raw_total, cudaStream_t s);
 cudaError_t launch_sort_keys(Key* keys, uint32_t n, uint32_t n_pad, cudaStream_t s);
+// Sorts every aligned segment of `seg` keys (a power of two) of keys[0..n_total)
+// ascending; n_total is a multiple of seg.
+cudaError_t launch_sort_segments(Key* keys, uint32_t n_total, uint32_t seg, cudaStream_t s);
 cudaError_t launch_key_raw(const Key* keys, uint32_t n, uint32_t* raw, cudaStream_t s);
 cudaError_t launch_gather_ids(const Key* keys, uint32_t n, const unsigned long long* id_off,
                               const SearchGeom& g, const CoarseGeom& cg, const Det* dets,
@@ -228,6 +231,11 @@ int select_peaks(const CandView& v, uint32_t* idx, uint64_t* n_peaks, cudaStream
 // candidate (output order) whose ids contain it; candidate i is kept when it
 // owns at least half of its ids.  Same output convention as select_peaks.
 int select_owned(const CandView& v, uint32_t* idx, uint64_t* n_kept, cudaStream_t s);
+
+// sas_vet.cu: logits of n stamps (device), in batches of the vetter's
+// max_batch; the device a vetter lives on.
+cudaError_t vet_forward_all(sas_vet* vt, const uint16_t* stamps, uint64_t n, float* logits, cudaStream_t s);
+int vet_device(const sas_vet* vt);
 
 // sas_api.cu: the candidate view of a finished search.
 CandView result_view(const sas_result* r);

@@ -132,8 +132,12 @@ __device__ __forceinline__ void cmp_swap(Key& p, Key& q, bool asc) {
   }
 }
 
+// The bitonic network sorts every aligned segment of `seg` keys ascending: the
+// direction of stage k is the usual ((i & k) == 0) below k = seg, and ascending
+// at k = seg (one segment = the whole array for a single sort).
+
 // Stages k = 2..len inside each chunk of `len` keys (len <= kSortChunk).
-__global__ void k_bitonic_local_sort(Key* keys, uint32_t len) {
+__global__ void k_bitonic_local_sort(Key* keys, uint32_t len, uint32_t seg) {
   __shared__ Key s[kSortChunk];
   const uint32_t base = blockIdx.x * len;
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s[i] = keys[base + i];
@@ -142,7 +146,7 @@ __global__ void k_bitonic_local_sort(Key* keys, uint32_t len) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
         const uint32_t ixj = i ^ j;
-        if (ixj > i) cmp_swap(s[i], s[ixj], ((base + i) & k) == 0);
+        if (ixj > i) cmp_swap(s[i], s[ixj], ((base + i) & k) == 0 || k >= seg);
       }
       __syncthreads();
     }
@@ -151,7 +155,7 @@ __global__ void k_bitonic_local_sort(Key* keys, uint32_t len) {
 }
 
 // Steps j < kSortChunk of stage k, one chunk per block.
-__global__ void k_bitonic_local_merge(Key* keys, uint32_t k) {
+__global__ void k_bitonic_local_merge(Key* keys, uint32_t k, uint32_t seg) {
   __shared__ Key s[kSortChunk];
   const uint32_t base = blockIdx.x * kSortChunk;
   for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) s[i] = keys[base + i];
@@ -159,7 +163,7 @@ __global__ void k_bitonic_local_merge(Key* keys, uint32_t k) {
   for (uint32_t j = kSortChunk >> 1; j > 0; j >>= 1) {
     for (uint32_t i = threadIdx.x; i < kSortChunk; i += blockDim.x) {
       const uint32_t ixj = i ^ j;
-      if (ixj > i) cmp_swap(s[i], s[ixj], ((base + i) & k) == 0);
+      if (ixj > i) cmp_swap(s[i], s[ixj], ((base + i) & k) == 0 || k >= seg);
     }
     __syncthreads();
   }
@@ -167,13 +171,13 @@ __global__ void k_bitonic_local_merge(Key* keys, uint32_t k) {
 }
 
 // One step (k, j >= kSortChunk) over global memory.
-__global__ void k_bitonic_global(Key* keys, uint32_t n_pad, uint32_t k, uint32_t j) {
+__global__ void k_bitonic_global(Key* keys, uint32_t n_pad, uint32_t k, uint32_t j, uint32_t seg) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
   const uint32_t ixj = i ^ j;
   if (ixj > i) {
     Key p = keys[i], q = keys[ixj];
-    const bool asc = (i & k) == 0;
+    const bool asc = (i & k) == 0 || k >= seg;
     if (key_less(q, p) == asc) {
       keys[i] = q;
       keys[ixj] = p;
@@ -281,19 +285,24 @@ cudaError_t launch_sort_keys(Key* keys, uint32_t n, uint32_t n_pad, cudaStream_t
     k_fill_max<<<blocks_for(n_pad - n, 256), 256, 0, s>>>(keys, n, n_pad);
     note_launch();
   }
-  if (n_pad <= (uint32_t)kSortChunk) {
-    k_bitonic_local_sort<<<1, kSortThreads, 0, s>>>(keys, n_pad);
+  return launch_sort_segments(keys, n_pad, n_pad, s);
+}
+
+cudaError_t launch_sort_segments(Key* keys, uint32_t n_total, uint32_t seg, cudaStream_t s) {
+  if (seg <= 1 || n_total == 0) return cudaSuccess;
+  if (seg <= (uint32_t)kSortChunk) {
+    k_bitonic_local_sort<<<n_total / seg, kSortThreads, 0, s>>>(keys, seg, seg);
     note_launch();
     return cudaGetLastError();
   }
-  k_bitonic_local_sort<<<n_pad / kSortChunk, kSortThreads, 0, s>>>(keys, kSortChunk);
+  k_bitonic_local_sort<<<n_total / kSortChunk, kSortThreads, 0, s>>>(keys, kSortChunk, seg);
   note_launch();
-  for (uint32_t k = 2 * kSortChunk; k <= n_pad; k <<= 1) {
+  for (uint32_t k = 2 * kSortChunk; k <= seg; k <<= 1) {
     for (uint32_t j = k >> 1; j >= (uint32_t)kSortChunk; j >>= 1) {
-      k_bitonic_global<<<blocks_for(n_pad, 256), 256, 0, s>>>(keys, n_pad, k, j);
+      k_bitonic_global<<<blocks_for(n_total, 256), 256, 0, s>>>(keys, n_total, k, j, seg);
       note_launch();
     }
-    k_bitonic_local_merge<<<n_pad / kSortChunk, kSortThreads, 0, s>>>(keys, k);
+    k_bitonic_local_merge<<<n_total / kSortChunk, kSortThreads, 0, s>>>(keys, k, seg);
     note_launch();
   }
   return cudaGetLastError();

@@ -599,6 +599,18 @@ cudaError_t adam(sas_vet* vt, const float* grad, float lr, cudaStream_t s) {
 }
 
 }  // namespace vet
+
+cudaError_t vet_forward_all(sas_vet* vt, const uint16_t* stamps, uint64_t n, float* logits, cudaStream_t s) {
+  for (uint64_t b0 = 0; b0 < n; b0 += vt->max_batch) {
+    const uint32_t nb = (uint32_t)std::min<uint64_t>(vt->max_batch, n - b0);
+    cudaError_t e = vet::forward(vt, stamps + b0 * 9 * 225, nullptr, nb, false, logits + b0, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int vet_device(const sas_vet* vt) { return vt->device; }
+
 }  // namespace sas
 
 // ---- C ABI -----------------------------------------------------------------------

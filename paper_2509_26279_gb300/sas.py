@@ -355,6 +355,15 @@ class Batch:
                                     _stream_handle(stream)))
         return n.value
 
+    def vet(self, vetter, field_dev, cand_dev, logit_dev, cap: int, stream=None) -> int:
+        """sas_batch_vet: (field, candidate, logit) of every kept candidate of
+        every field into device arrays with room for cap items; returns the
+        number of items."""
+        n = ctypes.c_uint64()
+        _check(_lib.sas_batch_vet(self._h, vetter._h, _dev_ptr(field_dev), _dev_ptr(cand_dev),
+                                  _dev_ptr(logit_dev), int(cap), ctypes.byref(n), _stream_handle(stream)))
+        return n.value
+
     def stamps(self, f: int, idx_dev, count: int, out_dev, stream=None):
         _check(_lib.sas_batch_stamps(self._h, int(f), _opt_ptr(idx_dev), int(count),
                                      _opt_ptr(out_dev) if count else None, _stream_handle(stream)))
@@ -408,11 +417,12 @@ _lib.sas_batch_peaks.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.
 _lib.sas_batch_stamps.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64, _p, _p]
 _lib.sas_owned.argtypes = [_p, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 _lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_batch_vet.argtypes = [_p, _p, _p, _p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p]
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
              "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
              "sas_vet_forward", "sas_vet_gradients", "sas_vet_apply_gradients",
              "sas_vet_train_step", "sas_stamps_indexed", "sas_peaks", "sas_batch_peaks",
-             "sas_batch_stamps", "sas_owned", "sas_batch_owned"]
+             "sas_batch_stamps", "sas_owned", "sas_batch_owned", "sas_batch_vet"]
 
 STAMP_SHAPE = (9, 15, 15)
 VET_MAX_BATCH = 8192

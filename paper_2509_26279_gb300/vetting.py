@@ -9,8 +9,10 @@ Forms compared on the same fields, each reporting its candidate list:
              detection belongs to the first candidate containing it; a
              candidate stays when it owns at least half of its detections --
              the one-pass stand-in for the paper's peeling, Sec. 2.1 step 3);
-  vetted  -- the owned candidates whose CNN logit reaches a threshold chosen
-             on separate calibration fields for a target purity.
+  vetted  -- the owned candidates that the plain threshold accepts (count >=
+             N_min: the plain form stays the fallback) plus those below it whose
+             CNN logit reaches a threshold chosen on separate calibration
+             fields for a target purity.
 
 Truth (never an input of the method): a candidate is matched to mover m when
 at least half of its contributing detection ids were made by m; otherwise it
@@ -172,6 +174,12 @@ def train(vetter, stamps, labels, epochs: int = 20, batch: int = 512, lr: float 
     return hist
 
 
+def vetted_keep(counts, logits, plain_n_min: int, threshold: float) -> np.ndarray:
+    """The vetted form's decision for owned candidates: kept when the plain
+    threshold accepts them or the CNN scores them at or above threshold."""
+    return (np.asarray(counts) >= plain_n_min) | (np.asarray(logits) >= threshold)
+
+
 def logits_of(vetter, stamps) -> np.ndarray:
     """CNN logits of device stamps, to the host."""
     import torch
@@ -213,7 +221,7 @@ def evaluate(vetter, workloads: Sequence[W.Workload], device, threshold: float =
         pk, st = owned_stamps(rl, device)
         logits = torch.zeros(max(len(pk), 1), device=device)
         vetter.forward(st, len(pk), logits)
-        keep = logits[:len(pk)].cpu().numpy() >= threshold
+        keep = vetted_keep(cl["count"][pk], logits[:len(pk)].cpu().numpy(), w.n_min, threshold)
         sel = {"plain": (mp, None), "low": (ml, None), "owned": (ml[pk], None), "vetted": (ml[pk], keep)}
         for k, (m, kp) in sel.items():
             r = recall_by_mag(_recovered(m, kp), movers)

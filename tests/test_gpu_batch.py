@@ -64,7 +64,7 @@ def test_batch_equals_single_field_search():
 
 def test_batch_field_fallback_is_exact():
     """A field with far more candidates than the batch's per-field capacity
-    (8192) is recomputed on the single-field path; the others stay batched."""
+    (32768) is recomputed on the single-field path; the others stay batched."""
     w = W.tiny()
     cat = W.load(w)
     g = sas.Grid(w.grid)
@@ -78,13 +78,42 @@ def test_batch_field_fallback_is_exact():
     b.run()
     ref = oracle.stack(cat, w.grid, 2)
     c, ids = b.candidates(0)
-    assert len(ref.cands) > 8192 and len(c) == len(ref.cands)
+    assert len(ref.cands) > 32768 and len(c) == len(ref.cands)
     assert np.array_equal(c["count"].astype(np.int64), ref.cands["distinct"].astype(np.int64))
     assert np.array_equal(ids.astype(np.int64), ref.ids.astype(np.int64))
     c2, ids2, _ = _single(g2, cat2, 12)
     cb, idsb = b.candidates(1)
     assert np.array_equal(cb, c2) and np.array_equal(idsb, ids2)
     assert b.stats()[1] == 1
+    b.destroy()
+
+
+def test_batch_sorts_large_fields_without_fallback():
+    """12,838 candidates (more than one shared-memory sort) stay in the batch:
+    the segmented sort orders them exactly like the single-field path."""
+    w = W.tiny()
+    cat = W.load(w)
+    g = sas.Grid(w.grid)
+    x, y, e = _dev(cat)
+    w2 = _fields(1, 9)[0][0]
+    cat2 = W.load(w2)
+    g2 = sas.Grid(w2.grid)
+    x2, y2, e2 = _dev(cat2)
+    b = sas.Batch([(g, x, y, e, cat.t, cat.ticks_per_hour, 3),
+                   (g2, x2, y2, e2, cat2.t, cat2.ticks_per_hour, 12)])
+    for _ in range(2):
+        b.run()
+        ref = oracle.stack(cat, w.grid, 3)
+        c, ids = b.candidates(0)
+        assert len(ref.cands) > 8192 and len(c) == len(ref.cands)
+        for fg, fo in [("v_idx", "v_idx"), ("bx", "bx"), ("by", "by"), ("count", "distinct"),
+                       ("raw", "raw"), ("id_len", "id_len"), ("id_off", "id_off")]:
+            assert np.array_equal(c[fg].astype(np.int64), ref.cands[fo].astype(np.int64)), fg
+        assert np.array_equal(ids.astype(np.int64), ref.ids.astype(np.int64))
+        c2, ids2, _ = _single(g2, cat2, 12)
+        cb, idsb = b.candidates(1)
+        assert np.array_equal(cb, c2) and np.array_equal(idsb, ids2)
+    assert b.stats()[1] == 0
     b.destroy()
 
 

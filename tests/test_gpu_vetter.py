@@ -383,3 +383,47 @@ def test_owned_tno_like_and_batch():
         idx_b = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
         kb = b.owned(f, idx_b)
         assert np.array_equal(idx_b[:kb].cpu().numpy().astype(np.int64), want)
+
+
+def test_batch_vet_equals_per_field_pipeline():
+    """sas_batch_vet (one pass over all fields, including a field recomputed on
+    the single-field path) gives the same kept candidates and bit-identical
+    logits as ownership selection, stamps and the CNN run field by field."""
+    ws = [W.scaled(w, frac_noise=0.3, width_px=1024, height_px=1024, grid_half=25)
+          for w in W.vetter_fields(3, seed=123)]
+    fields = []
+    for w in ws:
+        cat = W.load(w)
+        fields.append((sas.Grid(w.grid), torch.from_numpy(cat.x).cuda(), torch.from_numpy(cat.y).cuda(),
+                       torch.from_numpy(cat.epoch.view(np.int16)).cuda(), cat.t, cat.ticks_per_hour,
+                       max(8, w.n_min)))
+    tw = W.tiny()                         # n_min 2: far beyond the batch's candidate capacity
+    tc = W.load(tw)
+    fields.append((sas.Grid(tw.grid), torch.from_numpy(tc.x).cuda(), torch.from_numpy(tc.y).cuda(),
+                   torch.from_numpy(tc.epoch.view(np.int16)).cuda(), tc.t, tc.ticks_per_hour, 2))
+    b = sas.Batch(fields)
+    b.run()
+    # a field recomputed on the single-field path reports its own stack time
+    redone = [f for f in range(len(fields)) if b.field_info(f)["ms_stack"] != 0]
+    assert 3 in redone and b.stats()[1] == len(redone)
+    vt, _ = make_vetter(5, max_batch=256, bias=0.05)
+    cap = sum(b.field_info(f)["n_candidates"] for f in range(len(fields)))
+    fo = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    co = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    lo = torch.zeros(cap, dtype=torch.float32, device="cuda")
+    n = b.vet(vt, fo, co, lo, cap)
+    fo, co, lo = fo[:n].cpu().numpy(), co[:n].cpu().numpy(), lo[:n].cpu().numpy()
+    order = [f for f in range(len(fields)) if f not in redone] + redone
+    assert list(dict.fromkeys(fo.tolist())) == order
+    for f in range(len(fields)):
+        nc = b.field_info(f)["n_candidates"]
+        idx = torch.zeros(max(nc, 1), dtype=torch.int32, device="cuda")
+        k = b.owned(f, idx)
+        st = torch.zeros((max(k, 1), 9, 15, 15), dtype=torch.int16, device="cuda")
+        b.stamps(f, idx, k, st)
+        lg = torch.zeros(max(k, 1), device="cuda")
+        vt.forward(st, k, lg)
+        torch.cuda.synchronize()
+        sel = fo == f
+        assert np.array_equal(co[sel], idx[:k].cpu().numpy())
+        assert np.array_equal(lo[sel], lg[:k].cpu().numpy())

@@ -12,3 +12,8 @@ def test_calibrate_picks_lowest_threshold_meeting_purity():
     assert vetting.calibrate(logits, labels, 0.95) == 4.0
     assert vetting.calibrate(logits, labels, 0.5) == 0.0
     assert vetting.calibrate(logits, np.zeros(6), 0.5) == float("inf")
+
+
+def test_vetted_keep_keeps_plain_threshold_candidates():
+    keep = vetting.vetted_keep([30, 10, 10, 25], [-5.0, 2.0, -1.0, -9.0], 25, 0.5)
+    assert keep.tolist() == [True, True, False, True]
