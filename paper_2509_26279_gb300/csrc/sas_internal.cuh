@@ -90,6 +90,7 @@ struct StackArgs {
   TileCfg tc;
   uint32_t magic;      // umulhi(X, magic) = X / (s*bin) for 0 <= X < tile extent
   int32_t bin_is_one;  // s*bin == 1: the quotient is X itself
+  int32_t merge;       // the P columns of a counter word span at most two super-bins
   uint32_t n_min;
   int32_t nvt_x, nvt_y;      // velocity blocks along kx, ky
   int32_t kx_lo, ky_lo;      // first lattice column/row covered by the blocks

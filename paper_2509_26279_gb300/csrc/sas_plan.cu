@@ -308,6 +308,13 @@ void fill_stack_args(const FieldPlan& fp, uint32_t n_min, StackArgs* sa) {
   const int64_t sbin = (int64_t)tc.s * fp.g.bin;
   sa->magic = sbin >= 2 ? magic_for((int32_t)sbin) : 0u;
   sa->bin_is_one = sbin == 1;
+  // The projections of the P lattice columns that share a counter word differ
+  // by at most spread_bound((P-1)|dvx|); below one super-bin they fall into at
+  // most two adjacent super-bins, so the stack kernel needs two reductions per
+  // word (one per run of equal columns) instead of P.
+  const int per_word = 32 / tc.cb;
+  sa->merge = per_word >= 2 &&
+              spread_bound((int64_t)(per_word - 1) * std::llabs((int64_t)fp.g.dvx), fp.dT, fp.g.tph) < sbin;
   sa->n_min = n_min;
   sa->kx_lo = 0;
   sa->ky_lo = fp.ky_lo;

@@ -26,6 +26,8 @@
 // fall short of the number of pairs added, by 255 or 256 per wrap; the kernel
 // accumulates (sum - pairs) into a global balance and the host reruns with wider
 // counters when it is not zero, so the result is exact for any input.
+#include <type_traits>
+
 #include "sas_internal.cuh"
 
 namespace sas {
@@ -114,7 +116,16 @@ __device__ __forceinline__ void red_shared_if(uint32_t pred, uint32_t addr, uint
       "r"(addr), "r"(inc));
 }
 
-template <int KX, int KY, int CB, bool MASKED>
+// Counter increments of a mask of lattice columns within one word: bit q
+// becomes 1 at the lowest bit of counter q.
+template <int CB>
+__device__ __forceinline__ uint32_t spread_bits(uint32_t b) {
+  if constexpr (CB == 8) return (b * 0x00204081u) & 0x01010101u;  // bit q -> bit 8q (q < 4)
+  else if constexpr (CB == 16) return (b * 0x00008001u) & 0x00010001u;  // bit q -> bit 16q (q < 2)
+  else return b;
+}
+
+template <int KX, int KY, int CB, bool MASKED, bool MERGE>
 __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 const int32_t* __restrict__ ox,
                                                 const int32_t* __restrict__ oy,
@@ -162,12 +173,40 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
   for (int ky = 0; ky < KY; ++ky)
     if ((okyb >> ky) & 1u) m |= okxb << (ky * KX);
   if (MASKED) m &= act;
+  if constexpr (MERGE && C::P >= 2) {
+    // The columns of one counter word project into at most two adjacent
+    // super-bins (the planner proved it), and the projection is monotone in kx:
+    // the columns equal to the word's first column form one run, the rest
+    // equal its last column.  One reduction per run carries every column's
+    // increment.
+    constexpr uint32_t gmask = (1u << C::P) - 1u;
+    uint32_t eqm[KX / C::P];
 #pragma unroll
-  for (int ky = 0; ky < KY; ++ky) {
+    for (int g = 0; g < KX / C::P; ++g) {
+      uint32_t e = 0;
 #pragma unroll
-    for (int kx = 0; kx < KX; ++kx) {
-      const uint32_t addr = rbase4[ky] + col4[kx] + (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty * 4);
-      red_shared_if(m & (1u << (ky * KX + kx)), addr, 1u << (CB * (kx % C::P)));
+      for (int q = 0; q < C::P; ++q) e |= (uint32_t)(col4[g * C::P + q] == col4[g * C::P]) << q;
+      eqm[g] = e;
+    }
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+      for (int g = 0; g < KX / C::P; ++g) {
+        const uint32_t rb = (m >> (ky * KX + g * C::P)) & gmask;
+        const uint32_t lo = spread_bits<CB>(rb & eqm[g]), hi = spread_bits<CB>(rb & ~eqm[g]);
+        const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
+        red_shared_if(lo, plane + col4[g * C::P], lo);
+        red_shared_if(hi, plane + col4[g * C::P + C::P - 1], hi);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < KX; ++kx) {
+        const uint32_t addr = rbase4[ky] + col4[kx] + (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty * 4);
+        red_shared_if(m & (1u << (ky * KX + kx)), addr, 1u << (CB * (kx % C::P)));
+      }
     }
   }
   return (uint32_t)__popc(m);
@@ -263,8 +302,12 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       __syncthreads();
       for (int i = tid; i < ne * (bxk + byk); i += kNT) {
         if (i < ne * bxk) {
-          const int el = i / bxk, k = i % bxk, kx = kxa + k;
-          s_ox[el * bxk + k] = (kx < g.nvx && s_win[el * 4 + 1] > 0)
+          // Columns past the lattice edge take the last column's origin: their
+          // pairs are masked out (active_mask), and a counter word that straddles
+          // the edge keeps projections that differ by less than a super-bin,
+          // which the merged reductions rely on.
+          const int el = i / bxk, k = i % bxk, kx = min(kxa + k, g.nvx - 1);
+          s_ox[el * bxk + k] = s_win[el * 4 + 1] > 0
                                    ? X0 + a.sxt[(size_t)kx * E + e_base + el] - s_win[el * 4]
                                    : kOutside;
         } else {
@@ -364,22 +407,21 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       const uint32_t full = (KX * KY == 32) ? 0xffffffffu : ((1u << (KX * KY)) - 1u);
       const int oxo = vtx * KX, oyo = vty * KY;
       uint32_t pairs = 0;
+      auto run = [&](auto masked, auto merge) {
+        for (uint32_t j = tid; j < n_staged; j += kNT) {
+          const uint2 r = staged[j];
+          const int el = (int)(r.x >> 24);
+          pairs += process_rec<KX, KY, CB, decltype(masked)::value, decltype(merge)::value>(
+              r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo, s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
+              a.magic, a.bin_is_one, tc.tx, txty, act);
+        }
+      };
+      using T = std::true_type;
+      using F = std::false_type;
       if (act == full) {
-        for (uint32_t j = tid; j < n_staged; j += kNT) {
-          const uint2 r = staged[j];
-          const int el = (int)(r.x >> 24);
-          pairs += process_rec<KX, KY, CB, false>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
-                                                  s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
-                                                  a.magic, a.bin_is_one, tc.tx, txty, act);
-        }
+        if (a.merge) run(F{}, T{}); else run(F{}, F{});
       } else {
-        for (uint32_t j = tid; j < n_staged; j += kNT) {
-          const uint2 r = staged[j];
-          const int el = (int)(r.x >> 24);
-          pairs += process_rec<KX, KY, CB, true>(r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo,
-                                                 s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
-                                                 a.magic, a.bin_is_one, tc.tx, txty, act);
-        }
+        if (a.merge) run(T{}, T{}); else run(T{}, F{});
       }
       pairs64 += pairs;
       balance -= pairs;

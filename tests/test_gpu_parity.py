@@ -302,3 +302,20 @@ def test_superbin_and_velocity_block_agree(sb, vb):
     assert len(ref.cands) > 0
     assert_same(res, ref)
     assert res.info()["superbin"] == sb
+
+
+@pytest.mark.parametrize("nvx", [2, 3, 5, 6, 7, 9])
+def test_lattice_edge_inside_a_counter_word(nvx):
+    """Lattice widths that end inside a counter word (four 8-bit counters per
+    word along kx), on slow lattices where the word's columns are merged into
+    at most two reductions: the columns past the edge must neither count nor
+    steer a reduction."""
+    w = W.scaled(W.decam_tno(), frac_noise=0.2, width_px=600, height_px=500, n_movers=30, grid_half=3,
+                 seed=40 + nvx)
+    g = w.grid
+    grid = W.GridSpec(vx0=g.vx0, vy0=g.vy0, dvx=g.dvx, dvy=g.dvy, nvx=nvx, nvy=g.nvy, x_min=g.x_min,
+                      y_min=g.y_min, nbx=g.nbx, nby=g.nby, bin=g.bin)
+    cat = W.load(w)
+    res, ref = run_both(cat, grid, 6)
+    assert len(ref.cands) > 0
+    assert_same(res, ref)
