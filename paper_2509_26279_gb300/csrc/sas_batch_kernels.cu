@@ -7,6 +7,7 @@
 #include <climits>
 
 #include "sas_batch.cuh"
+#include "sas_count.cuh"
 
 namespace sas {
 
@@ -153,64 +154,22 @@ __global__ void k_batch_cell_count(const BatchField* __restrict__ F, const Det* 
   const int lane = threadIdx.x & 31;
   const BatchField& bf = F[blockIdx.y];
   const uint32_t n_emit = min(bf.counters[kCtrEmit], bf.emit_cap);
-  for (uint32_t j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < n_emit; j += gridDim.x * kWarps) {
   const SearchGeom& g = bf.args.g;
   const CoarseGeom& cg = bf.args.cg;
-  const Emit em = bf.args.emits[j];
-  const int sb = bf.args.tc.s;
-  const uint32_t kx = em.v_idx % (uint32_t)g.nvx, ky = em.v_idx / (uint32_t)g.nvx;
-  const int nq = sb * sb;
-  const int32_t span = sb * g.bin;
-  uint32_t distinct[16], raw[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) distinct[q] = raw[q] = 0;
-  for (uint32_t eb = 0; eb < g.E; eb += 32) {
-    const uint32_t e = eb + lane;
-    uint32_t hit = 0;
-    if (e < g.E && bf.ecount[e] > 0) {
-      const int32_t ox = g.x_min + (int32_t)em.bx * g.bin + bf.sxt[(size_t)kx * g.E + e];
-      const int32_t oy = g.y_min + (int32_t)em.by * g.bin + bf.syt[(size_t)ky * g.E + e];
-      const int cxa = max(floor_div32(ox - cg.gx0, cg.cell), 0);
-      const int cxb = min(floor_div32(ox + span - 1 - cg.gx0, cg.cell), cg.ncx - 1);
-      const int cya = max(floor_div32(oy - cg.gy0, cg.cell), 0);
-      const int cyb = min(floor_div32(oy + span - 1 - cg.gy0, cg.cell), cg.ncy - 1);
-      for (int cy = cya; cy <= cyb && cxa <= cxb; ++cy) {
-        const size_t b0 = bf.bucket_base + ((size_t)e * cg.ncy + cy) * cg.ncx;
-        const uint32_t k1 = boff[b0 + cxb + 1];
-        for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
-          const Det d = dets[k];
-          const uint32_t X = (uint32_t)(d.x - ox), Y = (uint32_t)(d.y - oy);
-          if (X < (uint32_t)span && Y < (uint32_t)span) {
-            const int q = (int)(Y / (uint32_t)g.bin) * sb + (int)(X / (uint32_t)g.bin);
-            hit |= 1u << q;
-#pragma unroll
-            for (int qq = 0; qq < 16; ++qq) raw[qq] += (qq == q);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (q < nq) distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
-  }
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    if (q >= nq) break;
-    uint32_t r = raw[q];
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (lane == 0) {
-      const uint32_t bx = em.bx + (uint32_t)(q % sb), by = em.by + (uint32_t)(q / sb);
-      if (bx < (uint32_t)g.nbx && by < (uint32_t)g.nby && distinct[q] >= bf.args.n_min) {
-        Key k;
-        k.a = ((uint64_t)(~distinct[q]) << 32) | (uint64_t)(~r);
-        k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
-        k.c = bx;
-        k.pad = 0;
-        const uint32_t p = atomicAdd(bf.counters + kCtrValid, 1u);
-        if (p < bf.key_cap) bf.keys[p] = k; else atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
-      }
-    }
-  }
+  const uint64_t cell_m = div_magic((uint32_t)cg.cell), bin_m = div_magic((uint32_t)g.bin);
+  for (uint32_t j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < n_emit; j += gridDim.x * kWarps) {
+    const Emit em = bf.args.emits[j];
+    count_superbin(em, bf.args.tc.s, g, cg, cell_m, bin_m, dets, boff + bf.bucket_base, bf.ecount, bf.sxt,
+                   bf.syt, bf.args.n_min, lane,
+                   [&](int, uint32_t bx, uint32_t by, uint32_t distinct, uint32_t raw) {
+                     Key k;
+                     k.a = ((uint64_t)(~distinct) << 32) | (uint64_t)(~raw);
+                     k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
+                     k.c = bx;
+                     k.pad = 0;
+                     const uint32_t p = atomicAdd(bf.counters + kCtrValid, 1u);
+                     if (p < bf.key_cap) bf.keys[p] = k; else atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+                   });
   }
 }
 

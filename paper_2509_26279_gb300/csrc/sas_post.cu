@@ -1,6 +1,6 @@
 // After the stack kernel: exact counts of the emitted cells, deterministic
 // ordering, and the contributing detection ids (Sec. 2.1 step 3; Sec. 3.3).
-#include "sas_internal.cuh"
+#include "sas_count.cuh"
 
 namespace sas {
 
@@ -43,75 +43,30 @@ __device__ __forceinline__ bool bin_window(const SearchGeom& g, const CoarseGeom
   return w.cxa <= w.cxb && w.cya <= w.cyb;
 }
 
-// One warp per emitted super-bin (s x s bins): lane l handles epochs l, l+32, ...
-// For every bin q of the super-bin, the epochs with at least one detection in it
-// form a bitmask per 32-epoch block (__ballot_sync) whose popcount adds up to the
-// exact distinct-epoch count; raw counts are summed over the warp.
+// One warp per emitted super-bin (count_superbin); every bin that reaches
+// n_min appends its key.
 constexpr int kMaxS = 4;
 
-__global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, int sb,
-                             SearchGeom g, CoarseGeom cg, const Det* __restrict__ dets,
+__global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, int sb, SearchGeom g,
+                             CoarseGeom cg, uint64_t cell_m, uint64_t bin_m, const Det* __restrict__ dets,
                              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ ecount,
                              const int32_t* __restrict__ sxt, const int32_t* __restrict__ syt,
                              uint32_t n_min, Key* __restrict__ keys, uint32_t* __restrict__ n_valid,
                              unsigned long long* __restrict__ raw_total) {
   const uint32_t w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= n_emit) return;
+  if (w >= n_emit) return;  // whole warps leave together
   const Emit em = emits[w];
-  const uint32_t kx = em.v_idx % (uint32_t)g.nvx, ky = em.v_idx / (uint32_t)g.nvx;
-  const int nq = sb * sb;
-  const int32_t span = sb * g.bin;
-  uint32_t distinct[kMaxS * kMaxS], raw[kMaxS * kMaxS];
-#pragma unroll
-  for (int q = 0; q < kMaxS * kMaxS; ++q) distinct[q] = raw[q] = 0;
-  for (uint32_t eb = 0; eb < g.E; eb += 32) {
-    const uint32_t e = eb + lane;
-    uint32_t hit = 0;
-    if (e < g.E && ecount[e] > 0) {
-      const int32_t ox = g.x_min + (int32_t)em.bx * g.bin + sxt[(size_t)kx * g.E + e];
-      const int32_t oy = g.y_min + (int32_t)em.by * g.bin + syt[(size_t)ky * g.E + e];
-      const int cxa = max(floor_div32(ox - cg.gx0, cg.cell), 0);
-      const int cxb = min(floor_div32(ox + span - 1 - cg.gx0, cg.cell), cg.ncx - 1);
-      const int cya = max(floor_div32(oy - cg.gy0, cg.cell), 0);
-      const int cyb = min(floor_div32(oy + span - 1 - cg.gy0, cg.cell), cg.ncy - 1);
-      for (int cy = cya; cy <= cyb && cxa <= cxb; ++cy) {
-        const size_t b0 = ((size_t)e * cg.ncy + cy) * cg.ncx;
-        const uint32_t k1 = boff[b0 + cxb + 1];
-        for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
-          const Det d = dets[k];
-          const uint32_t X = (uint32_t)(d.x - ox), Y = (uint32_t)(d.y - oy);
-          if (X < (uint32_t)span && Y < (uint32_t)span) {
-            const int q = (int)(Y / (uint32_t)g.bin) * sb + (int)(X / (uint32_t)g.bin);
-            hit |= 1u << q;
-#pragma unroll
-            for (int qq = 0; qq < kMaxS * kMaxS; ++qq) raw[qq] += (qq == q);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < kMaxS * kMaxS; ++q)
-      if (q < nq) distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
-  }
-#pragma unroll
-  for (int q = 0; q < kMaxS * kMaxS; ++q) {
-    if (q >= nq) break;
-    uint32_t r = raw[q];
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (lane == 0) {
-      const uint32_t bx = em.bx + (uint32_t)(q % sb), by = em.by + (uint32_t)(q / sb);
-      if (bx < (uint32_t)g.nbx && by < (uint32_t)g.nby && distinct[q] >= n_min) {
-        Key k;
-        k.a = ((uint64_t)(~distinct[q]) << 32) | (uint64_t)(~r);
-        k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
-        k.c = bx;
-        k.pad = 0;
-        keys[atomicAdd(n_valid, 1u)] = k;  // compacted; the sort fixes the order
-        atomicAdd(raw_total, (unsigned long long)r);
-      }
-    }
-  }
+  count_superbin(em, sb, g, cg, cell_m, bin_m, dets, boff, ecount, sxt, syt, n_min, lane,
+                 [&](int, uint32_t bx, uint32_t by, uint32_t distinct, uint32_t raw) {
+                   Key k;
+                   k.a = ((uint64_t)(~distinct) << 32) | (uint64_t)(~raw);
+                   k.b = ((uint64_t)em.v_idx << 32) | (uint64_t)by;
+                   k.c = bx;
+                   k.pad = 0;
+                   keys[atomicAdd(n_valid, 1u)] = k;  // compacted; the sort fixes the order
+                   atomicAdd(raw_total, (unsigned long long)raw);
+                 });
 }
 
 __global__ void k_fill_max(Key* keys, uint32_t from, uint32_t to) {
@@ -273,7 +228,8 @@ cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, co
   if (n_emit == 0) return cudaSuccess;
   if (s_bins < 1 || s_bins > kMaxS) return cudaErrorInvalidValue;
   k_cell_count<<<blocks_for(n_emit, kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
-      emits, n_emit, s_bins, g, cg, dets, boff, ecount, sxt, syt, n_min, keys, n_valid, raw_total);
+      emits, n_emit, s_bins, g, cg, div_magic((uint32_t)cg.cell), div_magic((uint32_t)g.bin), dets, boff,
+      ecount, sxt, syt, n_min, keys, n_valid, raw_total);
   note_launch();
   return cudaGetLastError();
 }
