@@ -168,6 +168,34 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
     okyb |= (uint32_t)(Y < tw_y) << k;
     rbase4[k] = cells_s + (one ? Y : __umulhi(Y, magic)) * (uint32_t)(4 * tx);
   }
+  if constexpr (MERGE && C::P >= 2 && !MASKED) {
+    // Every lattice point of the tile is searched: a record's pairs are the
+    // valid columns times the valid rows, so each word group's two increments
+    // (runs of equal columns, see below) are formed once and reused per row.
+    constexpr uint32_t gmask = (1u << C::P) - 1u;
+    uint32_t lo[KX / C::P], hi[KX / C::P];
+#pragma unroll
+    for (int g = 0; g < KX / C::P; ++g) {
+      uint32_t e = 0;
+#pragma unroll
+      for (int q = 0; q < C::P; ++q) e |= (uint32_t)(col4[g * C::P + q] == col4[g * C::P]) << q;
+      const uint32_t xb = (okxb >> (g * C::P)) & gmask;
+      lo[g] = spread_bits<CB>(xb & e);
+      hi[g] = spread_bits<CB>(xb & ~e);
+    }
+#pragma unroll
+    for (int ky = 0; ky < KY; ++ky) {
+      const bool row = (okyb >> ky) & 1u;
+#pragma unroll
+      for (int g = 0; g < KX / C::P; ++g) {
+        const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
+        const uint32_t a = row ? lo[g] : 0u, b = row ? hi[g] : 0u;
+        red_shared_if(a, plane + col4[g * C::P], a);
+        red_shared_if(b, plane + col4[g * C::P + C::P - 1], b);
+      }
+    }
+    return (uint32_t)(__popc(okxb) * __popc(okyb));
+  }
   uint32_t m = 0;
 #pragma unroll
   for (int ky = 0; ky < KY; ++ky)
