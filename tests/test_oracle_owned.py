@@ -9,14 +9,14 @@ from oracle import owned as O
 from paper_2509_26279_gb300 import workloads as W
 
 
-def brute(id_lists):
+def brute(id_lists, n_keep=0):
     keep = []
     for i, ids in enumerate(id_lists):
         earlier = set()
         for j in range(i):
             earlier |= set(int(d) for d in id_lists[j])
         mine = [d for d in ids if int(d) not in earlier]
-        if 2 * len(mine) >= len(ids):
+        if 2 * len(mine) >= len(ids) or (n_keep > 0 and len(mine) >= n_keep):
             keep.append(i)
     return np.asarray(keep, np.int64)
 
@@ -26,7 +26,8 @@ def test_owned_equals_brute_force(seed):
     rng = np.random.default_rng(seed)
     m = int(rng.integers(0, 40))
     lists = [np.unique(rng.integers(0, 50, int(rng.integers(1, 12)))) for _ in range(m)]
-    assert np.array_equal(O.owned(lists), brute(lists))
+    n_keep = int(rng.integers(0, 6))
+    assert np.array_equal(O.owned(lists, n_keep), brute(lists, n_keep))
 
 
 def test_hand_built():
@@ -34,6 +35,17 @@ def test_hand_built():
     # 0 owns all; 1 owns only 5 (1 of 3) -> dropped; 2 owns 6 (5 belongs to 1) -> 1 of 2 kept;
     # 3 owns 9, 10 (2 of 4) -> kept; 4 owns 7 -> kept
     assert O.owned(lists).tolist() == [0, 2, 3, 4]
+
+
+def test_crossing_mover_keeps_its_cell():
+    """Two candidates sharing detections: the later one owns only 4 of its 10,
+    so the half rule drops it, but with n_keep = 4 (what it alone still holds
+    passes the threshold) it stays -- as the peel would find it again."""
+    a = list(range(0, 12))
+    b = list(range(6, 12)) + [100, 101, 102, 103]
+    assert O.owned([a, b]).tolist() == [0]
+    assert O.owned([a, b], n_keep=4).tolist() == [0, 1]
+    assert O.owned([a, b], n_keep=5).tolist() == [0]
 
 
 def test_one_clean_mover_keeps_one_cell():
@@ -46,3 +58,4 @@ def test_one_clean_mover_keeps_one_cell():
     lists = r.id_lists()
     kept = O.owned(lists)
     assert len(r.cands) > 1 and kept.tolist() == [0]
+    assert O.owned(lists, n_keep=3).tolist() == [0]   # ghosts hold none of their own
