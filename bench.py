@@ -160,7 +160,8 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     """fields/s on the batched uneven fields (60 CCDs, epochs U{20..150}, noise
     log-U[1e3, 8e3]): the plain form (one sas_stack per field at N_min =
     ceil(E/4)) against the batched + vetted form (one graph-captured batch
-    pass, then ownership selection, stamps and the CNN), at the plain
+    pass with the autotuner's per-size-class tiles, then ownership selection,
+    stamps and the CNN), at the plain
     threshold and at the lowered one (sas_batch_vet: ownership, stamps and CNN of
     all fields in one pass); recall per 0.5-mag bin and purity of each
     form's reported candidates.  The vetter is trained first (not timed) on
@@ -222,9 +223,21 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
         plain_out.append((c, i, None))
         r.free()
 
+    # autotuner: one measured sweep per size class (untimed), each field takes its class's options
+    from paper_2509_26279_gb300 import tuning
+    t1 = time.perf_counter()
+    cache = tuning.TuneCache(os.environ.get("SAS_TUNE_CACHE"))
+    gpu_name = torch.cuda.get_device_name(dev)
+    for f in fields:
+        cache.tune(f, gpu_name)
+    if cache.path:
+        cache.save()
+    tune_s = time.perf_counter() - t1
+    tuned_opts = [cache.opts_for(f) for f in fields]
+
     def make_batch(thr):
         return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
-                         stream=stream)
+                         opts=tuned_opts, stream=stream)
 
     def vetted_pass(batch, cap):
         fo = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -241,6 +254,9 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                           f"noise/epoch log-U[1e3,8e3], 200 movers each, 111x111 lattice, bin 2 px",
               "plain": {"form": "one sas_stack per field, N_min = ceil(E/4)", "ms": round(ms_plain, 3),
                         "fields_per_s": round(n_fields / (ms_plain * 1e-3), 2), **score(plain_out)},
+              "autotune": {"classes": len(cache.entries), "seconds": round(tune_s, 1),
+                           "choices": {k: [v["superbin"], v["velocity_block"]] for k, v in cache.entries.items()},
+                           "rule": "sas_autotune per size class (superbin x velocity_block sweep, median of 3)"},
               "vetter_training": {"fields": train_fields, "stamps": n_train, "epochs": epochs,
                                   "final_loss": round(hist[-1], 4), "seconds": round(train_s, 1),
                                   "threshold": round(tau, 4),
@@ -253,20 +269,24 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
         cap = sum(max(batch.field_info(k)["n_candidates"], 1) for k in range(len(fields))) + 1
         ms, (fo, co, lo) = timed(vetted_pass(batch, cap))
         fo, co, lo = fo.cpu().numpy(), co.cpu().numpy(), lo.cpu().numpy()
-        per_field = []
+        per_field, per_field_dedup = [], []
         for k in range(len(fields)):
             c, i = batch.candidates(k)
             sel = fo == k
             idx = co[sel]
-            mask = np.zeros(len(c), bool)
-            mask[idx[vetting.vetted_keep(c["count"][idx], lo[sel], fields[k].w.n_min, tau)]] = True
-            per_field.append((c, i, mask))
+            per_field.append((c, i, vetting.vetted_mask(c["count"], idx, lo[sel], fields[k].w.n_min, tau)))
+            dd = np.zeros(len(c), bool)
+            dd[idx[vetting.vetted_keep(c["count"][idx], lo[sel], fields[k].w.n_min, tau)]] = True
+            per_field_dedup.append((c, i, dd))
         _, fallbacks = batch.stats()
-        result[name] = {"form": desc + ", ownership selection; kept when count >= ceil(E/4) or the CNN "
-                                       "logit >= the calibrated threshold",
+        result[name] = {"form": desc + "; every candidate with count >= ceil(E/4) kept, plus the "
+                                       "ownership-selected candidates below it whose CNN logit >= the "
+                                       "calibrated threshold",
                         "ms": round(ms, 3),
                         "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
-                        **score(per_field)}
+                        **score(per_field),
+                        "dedup": {"form": "the same decision on the ownership-selected candidates only",
+                                  **score(per_field_dedup)}}
         batch.destroy()
     return result
 

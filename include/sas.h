@@ -230,13 +230,13 @@ int sas_batch_peaks(const sas_batch* batch, uint32_t field, uint32_t* idx, uint6
                     void* stream);
 int sas_batch_stamps(const sas_batch* batch, uint32_t field, const uint32_t* idx, uint64_t count,
                      uint16_t* out, void* stream);
-int sas_batch_owned(const sas_batch* batch, uint32_t field, uint32_t* idx, uint64_t* n_kept,
-                    void* stream);
+int sas_batch_owned(const sas_batch* batch, uint32_t field, uint32_t n_keep, uint32_t* idx,
+                    uint64_t* n_kept, void* stream);
 
 typedef struct sas_vet sas_vet;
 
 /* Vetting of every field of the last run in one pass: ownership selection
- * (as sas_owned), stamps of the kept candidates and their CNN logits (as
+ * (as sas_owned with n_keep = the field's n_min), stamps of the kept candidates and their CNN logits (as
  * sas_vet_forward).  Writes one item per kept candidate: field_out[i],
  * cand_out[i] (its index in the field's candidate list) and logit_out[i]
  * (device arrays with room for `cap` items; the batch's total candidate count
@@ -332,10 +332,14 @@ int sas_peaks(const sas_result* result, uint32_t* idx, uint64_t* n_peaks, void* 
  * paper's peeling of clusters (Sec. 2.1 step 3: the best cluster's detections
  * are removed before the next is taken).  Each detection belongs to the first
  * candidate, in output order, whose ids contain it; candidate i is kept when it
- * owns at least half of its ids.  A mover's ghost cells (nearby velocities and
- * bins that also collect its detections) lose their detections to its best
- * cell and drop out.  Output as sas_peaks.  Uses O(catalog size) scratch. */
-int sas_owned(const sas_result* result, uint32_t* idx, uint64_t* n_kept, void* stream);
+ * owns at least half of its ids, or, with n_keep > 0, at least n_keep of them
+ * (what it alone holds would still pass a threshold of n_keep after the peel:
+ * a fainter mover crossing a brighter one keeps its cell; pass the search's
+ * n_min).  A mover's ghost cells (nearby velocities and bins that also collect
+ * its detections) lose their detections to its best cell and drop out.
+ * Output as sas_peaks.  Uses O(catalog size) scratch. */
+int sas_owned(const sas_result* result, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept,
+              void* stream);
 
 /* The network (input = count / 16):
  *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),

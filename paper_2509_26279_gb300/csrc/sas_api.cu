@@ -507,10 +507,10 @@ int sas_stamps_indexed(const sas_result* r, const uint32_t* idx, uint64_t count,
   return SAS_OK;
 }
 
-int sas_owned(const sas_result* r, uint32_t* idx, uint64_t* n_kept, void* stream) {
+int sas_owned(const sas_result* r, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept, void* stream) {
   if (!r || !n_kept) return fail(SAS_ERR_ARG, "null argument");
   if (r->info.n_candidates && !idx) return fail(SAS_ERR_ARG, "null index buffer");
-  return select_owned(result_view(r), idx, n_kept, (cudaStream_t)stream);
+  return select_owned(result_view(r), n_keep, idx, n_kept, (cudaStream_t)stream);
 }
 
 int sas_peaks(const sas_result* r, uint32_t* idx, uint64_t* n_peaks, void* stream) {

@@ -439,11 +439,12 @@ int sas_batch_peaks(const sas_batch* b, uint32_t field, uint32_t* idx, uint64_t*
   return select_peaks(v, idx, n_peaks, (cudaStream_t)stream);
 }
 
-int sas_batch_owned(const sas_batch* b, uint32_t field, uint32_t* idx, uint64_t* n_kept, void* stream) {
+int sas_batch_owned(const sas_batch* b, uint32_t field, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept,
+                    void* stream) {
   if (!b || field >= b->n_fields || !n_kept) return set_error(SAS_ERR_ARG, "bad argument");
   const CandView v = batch_view(b, field);
   if (v.n && !idx) return set_error(SAS_ERR_ARG, "null index buffer");
-  return select_owned(v, idx, n_kept, (cudaStream_t)stream);
+  return select_owned(v, n_keep, idx, n_kept, (cudaStream_t)stream);
 }
 
 int sas_batch_stamps(const sas_batch* b, uint32_t field, const uint32_t* idx, uint64_t count, uint16_t* out,
@@ -535,7 +536,7 @@ int sas_batch_vet(const sas_batch* b, sas_vet* vt, uint32_t* field_out, uint32_t
     uint32_t* idx = nullptr;
     if ((e = sc.alloc(&idx, v.n)) != cudaSuccess) break;
     uint64_t k = 0;
-    if (int rc = select_owned(v, idx, &k, s)) return rc;
+    if (int rc = select_owned(v, b->n_min[f], idx, &k, s)) return rc;
     if (n + k > cap) return set_errorf(SAS_ERR_OVERFLOW, "room for %llu items, more needed", (unsigned long long)cap);
     if (k && (!field_out || !cand_out || !logit_out)) return set_error(SAS_ERR_ARG, "null output buffer");
     if (k) {

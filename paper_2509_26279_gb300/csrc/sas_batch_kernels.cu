@@ -326,7 +326,7 @@ __global__ void k_batch_owned_flag(const BatchField* __restrict__ F, const unsig
     uint32_t mine = 0;
     for (uint32_t j = lane; j < cd.id_len; j += 32) mine += own[bf.ids[cd.id_off + j]] == c;
     mine = __reduce_add_sync(0xffffffffu, mine);
-    if (lane == 0) flag[cand_off[f] + c] = 2ull * mine >= cd.id_len;
+    if (lane == 0) flag[cand_off[f] + c] = 2ull * mine >= cd.id_len || mine >= bf.args.n_min;
   }
 }
 

@@ -230,8 +230,9 @@ int select_peaks(const CandView& v, uint32_t* idx, uint64_t* n_peaks, cudaStream
 
 // sas_select.cu: ownership selection -- detection d belongs to the first
 // candidate (output order) whose ids contain it; candidate i is kept when it
-// owns at least half of its ids.  Same output convention as select_peaks.
-int select_owned(const CandView& v, uint32_t* idx, uint64_t* n_kept, cudaStream_t s);
+// owns at least half of its ids or (n_keep > 0) at least n_keep of them.  Same
+// output convention as select_peaks.
+int select_owned(const CandView& v, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept, cudaStream_t s);
 
 // sas_vet.cu: logits of n stamps (device), in batches of the vetter's
 // max_batch; the device a vetter lives on.

@@ -98,7 +98,7 @@ __global__ void k_owner_min(const sas_candidate* __restrict__ c, uint64_t n, con
 }
 
 __global__ void k_owned_flag(const sas_candidate* __restrict__ c, uint64_t n, const uint32_t* __restrict__ ids,
-                             const uint32_t* __restrict__ owner, uint32_t* __restrict__ flag) {
+                             const uint32_t* __restrict__ owner, uint32_t n_keep, uint32_t* __restrict__ flag) {
   const uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint32_t lane = threadIdx.x & 31;
   if (w >= n) return;
@@ -106,7 +106,7 @@ __global__ void k_owned_flag(const sas_candidate* __restrict__ c, uint64_t n, co
   uint32_t mine = 0;
   for (uint32_t j = lane; j < ci.id_len; j += 32) mine += owner[ids[ci.id_off + j]] == (uint32_t)w;
   mine = __reduce_add_sync(0xffffffffu, mine);
-  if (lane == 0) flag[w] = 2ull * mine >= ci.id_len;
+  if (lane == 0) flag[w] = 2ull * mine >= ci.id_len || (n_keep > 0 && mine >= n_keep);
 }
 
 unsigned blocks_for(uint64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -167,7 +167,7 @@ int select_peaks(const CandView& v, uint32_t* idx, uint64_t* n_peaks, cudaStream
   return sel.finish(e, v.n, idx, n_peaks, "peak selection");
 }
 
-int select_owned(const CandView& v, uint32_t* idx, uint64_t* n_kept, cudaStream_t s) {
+int select_owned(const CandView& v, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept, cudaStream_t s) {
   *n_kept = 0;
   if (v.n == 0) return SAS_OK;
   if (v.n >= (1ull << 31)) return set_error(SAS_ERR_RANGE, "too many candidates for ownership selection");
@@ -176,7 +176,7 @@ int select_owned(const CandView& v, uint32_t* idx, uint64_t* n_kept, cudaStream_
   if (e == cudaSuccess) {
     const unsigned blocks = blocks_for(v.n * 32, 256);
     k_owner_min<<<blocks, 256, 0, s>>>(v.cands, v.n, v.ids, sel.aux);
-    k_owned_flag<<<blocks, 256, 0, s>>>(v.cands, v.n, v.ids, sel.aux, sel.flag);
+    k_owned_flag<<<blocks, 256, 0, s>>>(v.cands, v.n, v.ids, sel.aux, n_keep, sel.flag);
     note_launch(2);
     e = cudaGetLastError();
   }

@@ -349,9 +349,9 @@ class Batch:
                                     _stream_handle(stream)))
         return n.value
 
-    def owned(self, f: int, idx_dev, stream=None) -> int:
+    def owned(self, f: int, idx_dev, n_keep: int = 0, stream=None) -> int:
         n = ctypes.c_uint64()
-        _check(_lib.sas_batch_owned(self._h, int(f), _opt_ptr(idx_dev), ctypes.byref(n),
+        _check(_lib.sas_batch_owned(self._h, int(f), int(n_keep), _opt_ptr(idx_dev), ctypes.byref(n),
                                     _stream_handle(stream)))
         return n.value
 
@@ -415,8 +415,8 @@ _lib.sas_stamps_indexed.argtypes = [_p, _p, ctypes.c_uint64, _p, _p]
 _lib.sas_peaks.argtypes = [_p, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 _lib.sas_batch_peaks.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 _lib.sas_batch_stamps.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64, _p, _p]
-_lib.sas_owned.argtypes = [_p, _p, ctypes.POINTER(ctypes.c_uint64), _p]
-_lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_owned.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
+_lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 _lib.sas_batch_vet.argtypes = [_p, _p, _p, _p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p]
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
              "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
@@ -454,12 +454,13 @@ def sas_peaks(result: Result, idx_dev, stream=None) -> int:
     return n.value
 
 
-def sas_owned(result: Result, idx_dev, stream=None) -> int:
+def sas_owned(result: Result, idx_dev, n_keep: int = 0, stream=None) -> int:
     """Ownership selection: ascending kept candidate indices into idx_dev
-    (device uint32, room for n_candidates); returns their number (synchronizes)."""
+    (device uint32, room for n_candidates); returns their number (synchronizes).
+    n_keep > 0 also keeps candidates that own at least n_keep detections."""
     n = ctypes.c_uint64()
-    _check(_lib.sas_owned(result._h, _dev_ptr(idx_dev) if idx_dev is not None else None, ctypes.byref(n),
-                          _stream_handle(stream)))
+    _check(_lib.sas_owned(result._h, int(n_keep), _dev_ptr(idx_dev) if idx_dev is not None else None,
+                          ctypes.byref(n), _stream_handle(stream)))
     return n.value
 
 

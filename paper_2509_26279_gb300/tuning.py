@@ -1,0 +1,75 @@
+"""Per-size-class tile choices from the autotuner, cached as JSON.
+
+sas_autotune times the whole search for each (super-bin size, velocity block)
+pair on one field and returns the fastest.  Fields of similar shape -- the same
+lattice and bin, similar epoch count, detection density and threshold -- share
+the answer, so a batch of many uneven fields is tuned once per size class and
+each field takes its class's options.  The cache is a JSON object
+{class key: {"superbin": s, "velocity_block": b, "ms": t, "device": name}}
+that can be written to disk and reused across runs on the same GPU model.
+
+Host logic only: the timing runs in the library (sas_autotune).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+
+def size_class(n_epochs: int, n_detections: int, grid, n_min: int) -> str:
+    """Class key: epochs in steps of 32, detections per epoch in octaves,
+    lattice shape, bin, threshold as a fraction of the epochs in eighths."""
+    e_cls = -(-n_epochs // 32)
+    d_cls = int(round(math.log2(max(1.0, n_detections / max(1, n_epochs)))))
+    f_cls = min(8, (8 * n_min) // max(1, n_epochs))
+    return f"E{e_cls}-d{d_cls}-v{grid.nvx}x{grid.nvy}-b{grid.bin}-f{f_cls}"
+
+
+class TuneCache:
+    """Autotuned options per size class, optionally backed by a JSON file."""
+
+    def __init__(self, path: Optional[str] = None):
+        self.path = path
+        self.entries: Dict[str, dict] = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.entries = json.load(f)
+
+    def save(self, path: Optional[str] = None):
+        path = path or self.path
+        if not path:
+            raise ValueError("no path to save the tuning cache to")
+        d = os.path.dirname(os.path.abspath(path))
+        os.makedirs(d, exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(self.entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+    def lookup(self, key: str):
+        return self.entries.get(key)
+
+    def tune(self, field, device_name: str = "", reps: int = 3) -> dict:
+        """Entry of field's class, measured with sas_autotune if missing.
+        field: an object with grid (sas.Grid), w (workload: grid spec, n_min),
+        cat, dx, dy, de (device catalog) and E -- e.g. vetting.Field."""
+        from . import sas
+        key = size_class(field.E, field.cat.n, field.w.grid, field.w.n_min)
+        if key not in self.entries:
+            best, ms = sas.sas_autotune(field.grid, field.dx, field.dy, field.de, field.cat.t,
+                                        field.cat.ticks_per_hour, field.w.n_min, reps=reps)
+            self.entries[key] = {"superbin": int(best.superbin), "velocity_block": int(best.velocity_block),
+                                 "ms": round(float(ms), 4), "device": device_name}
+        return self.entries[key]
+
+    def opts_for(self, field):
+        """sas_opts for a field from its class entry (planner defaults if none)."""
+        from . import sas
+        e = self.lookup(size_class(field.E, field.cat.n, field.w.grid, field.w.n_min))
+        if e is None:
+            return sas.make_opts()
+        return sas.make_opts(superbin=e["superbin"], velocity_block=e["velocity_block"])

@@ -9,10 +9,13 @@ Forms compared on the same fields, each reporting its candidate list:
              detection belongs to the first candidate containing it; a
              candidate stays when it owns at least half of its detections --
              the one-pass stand-in for the paper's peeling, Sec. 2.1 step 3);
-  vetted  -- the owned candidates that the plain threshold accepts (count >=
-             N_min: the plain form stays the fallback) plus those below it whose
-             CNN logit reaches a threshold chosen on separate calibration
-             fields for a target purity.
+  vetted  -- every candidate the plain threshold accepts (count >= N_min: the
+             plain form stays the fallback, so recall is at least plain's in
+             every bin) plus the owned candidates below it whose CNN logit
+             reaches a threshold chosen on separate calibration fields for a
+             target purity;
+  vetted_dedup -- the same decision applied to the owned candidates only (one
+             candidate per source, as the peel would report).
 
 Truth (never an input of the method): a candidate is matched to mover m when
 at least half of its contributing detection ids were made by m; otherwise it
@@ -121,14 +124,15 @@ class Field:
                              n_min, on_device=True, stream=stream)
 
 
-def owned_stamps(res, device, stream=None):
+def owned_stamps(res, device, n_keep: int = 0, stream=None):
     """(kept indices [k] int64 host, stamps [k, 9, 15, 15] device int16 view of
-    u16) of the candidates that survive ownership selection."""
+    u16) of the candidates that survive ownership selection (n_keep: the
+    search's threshold, see sas_owned)."""
     import torch
     from . import sas
     n = res.info()["n_candidates"]
     idx = torch.empty(max(n, 1), dtype=torch.int32, device=device)
-    k = sas.sas_owned(res, idx, stream=stream)
+    k = sas.sas_owned(res, idx, n_keep, stream=stream)
     st = torch.empty((max(k, 1), 9, 15, 15), dtype=torch.int16, device=device)
     sas.sas_stamps_indexed(res, idx, k, st, stream=stream)
     return idx[:k].cpu().numpy().astype(np.int64), st[:k]
@@ -143,7 +147,7 @@ def training_set(workloads: Sequence[W.Workload], device):
         f = Field(w, device)
         res = f.search(n_low(f.E))
         cands, ids = res.candidates()
-        pk, st = owned_stamps(res, device)
+        pk, st = owned_stamps(res, device, n_low(f.E))
         match = truth_match(cands, ids, f.cat.mover)
         stamps.append(st)
         labels.append((match[pk] >= 0).astype(np.float32))
@@ -175,9 +179,18 @@ def train(vetter, stamps, labels, epochs: int = 20, batch: int = 512, lr: float 
 
 
 def vetted_keep(counts, logits, plain_n_min: int, threshold: float) -> np.ndarray:
-    """The vetted form's decision for owned candidates: kept when the plain
+    """The vetted decision for owned candidates: kept when the plain
     threshold accepts them or the CNN scores them at or above threshold."""
     return (np.asarray(counts) >= plain_n_min) | (np.asarray(logits) >= threshold)
+
+
+def vetted_mask(counts, owned_idx, owned_logits, plain_n_min: int, threshold: float) -> np.ndarray:
+    """The vetted form over a whole candidate list: every candidate at or above
+    the plain threshold, plus the owned ones the CNN accepts."""
+    mask = np.asarray(counts) >= plain_n_min
+    owned_idx = np.asarray(owned_idx, np.int64)
+    mask[owned_idx[np.asarray(owned_logits) >= threshold]] = True
+    return mask
 
 
 def logits_of(vetter, stamps) -> np.ndarray:
@@ -203,12 +216,12 @@ def calibrate(logits: np.ndarray, labels: np.ndarray, target_purity: float) -> f
 
 
 def evaluate(vetter, workloads: Sequence[W.Workload], device, threshold: float = 0.0) -> dict:
-    """Recall per magnitude bin and purity of the plain, low, owned and vetted
-    forms."""
+    """Recall per magnitude bin and purity of the plain, low, owned, vetted and
+    vetted_dedup forms."""
     import torch
     nb = len(MAG_EDGES) - 1
     acc = {k: {"total": [0] * nb, "found": [0] * nb, "reported": 0, "matched": 0}
-           for k in ("plain", "low", "owned", "vetted")}
+           for k in ("plain", "low", "owned", "vetted", "vetted_dedup")}
     for w in workloads:
         f = Field(w, device)
         movers = f.cat.movers
@@ -218,11 +231,14 @@ def evaluate(vetter, workloads: Sequence[W.Workload], device, threshold: float =
         rl = f.search(n_low(f.E))
         cl, il = rl.candidates()
         ml = truth_match(cl, il, f.cat.mover)
-        pk, st = owned_stamps(rl, device)
+        pk, st = owned_stamps(rl, device, n_low(f.E))
         logits = torch.zeros(max(len(pk), 1), device=device)
         vetter.forward(st, len(pk), logits)
-        keep = vetted_keep(cl["count"][pk], logits[:len(pk)].cpu().numpy(), w.n_min, threshold)
-        sel = {"plain": (mp, None), "low": (ml, None), "owned": (ml[pk], None), "vetted": (ml[pk], keep)}
+        lg = logits[:len(pk)].cpu().numpy()
+        keep = vetted_keep(cl["count"][pk], lg, w.n_min, threshold)
+        sel = {"plain": (mp, None), "low": (ml, None), "owned": (ml[pk], None),
+               "vetted": (ml, vetted_mask(cl["count"], pk, lg, w.n_min, threshold)),
+               "vetted_dedup": (ml[pk], keep)}
         for k, (m, kp) in sel.items():
             r = recall_by_mag(_recovered(m, kp), movers)
             a = acc[k]

@@ -129,3 +129,25 @@ def test_autotune_returns_a_valid_faster_config():
     c, ids = r.candidates()
     c0, ids0, _ = _single(g, cat, 10)
     assert np.array_equal(c, c0) and np.array_equal(ids, ids0)
+
+
+def test_batch_with_per_field_tuned_options():
+    """Fields of one batch with different super-bin sizes and velocity blocks
+    (as the autotuner's per-size-class cache hands them out) still equal their
+    single-field searches."""
+    specs = _fields(6, 11)
+    fields, refs, opts = [], [], []
+    for i, (w, n_min) in enumerate(specs):
+        cat = W.load(w)
+        g = sas.Grid(w.grid)
+        x, y, e = _dev(cat)
+        fields.append((g, x, y, e, cat.t, cat.ticks_per_hour, n_min))
+        o = sas.make_opts(superbin=1 + i % 3, velocity_block=[1, 2, 4, 8][i % 4])
+        opts.append(o)
+        r = sas.stack_catalog(g, cat, n_min, opts=o)
+        refs.append(r.candidates())
+    b = sas.Batch(fields, opts=opts)
+    b.run()
+    for f, (c_ref, ids_ref) in enumerate(refs):
+        c, ids = b.candidates(f)
+        assert np.array_equal(c, c_ref) and np.array_equal(ids, ids_ref), f

@@ -346,10 +346,10 @@ def test_batch_peaks_and_stamps_equal_single_field():
 from oracle import owned as OO  # noqa: E402
 
 
-def gpu_owned(res):
+def gpu_owned(res, n_keep=0):
     n = res.info()["n_candidates"]
     idx = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
-    k = sas.sas_owned(res, idx)
+    k = sas.sas_owned(res, idx, n_keep)
     return idx[:k].cpu().numpy().astype(np.int64), idx
 
 
@@ -358,8 +358,9 @@ def test_owned_random_tiny(seed):
     cat, grid, n_min = cases.random_tiny(seed + 1300)
     res = sas.stack_catalog(sas.Grid(grid), cat, max(1, n_min - 1))
     ref = oracle.stack(cat, grid, max(1, n_min - 1))
-    got, _ = gpu_owned(res)
-    assert np.array_equal(got, OO.owned(ref.id_lists()))
+    for n_keep in (0, 1, max(1, n_min - 1), n_min + 2):
+        got, _ = gpu_owned(res, n_keep)
+        assert np.array_equal(got, OO.owned(ref.id_lists(), n_keep)), n_keep
 
 
 def test_owned_tno_like_and_batch():
@@ -376,13 +377,14 @@ def test_owned_tno_like_and_batch():
     for f, (cat, w) in enumerate(keep):
         res = sas.stack_catalog(sas.Grid(w.grid), cat, 8)
         ref = oracle.stack(cat, w.grid, 8)
-        got, _ = gpu_owned(res)
-        want = OO.owned(ref.id_lists())
-        assert np.array_equal(got, want) and 0 < len(want) < len(ref.cands)
-        n = res.info()["n_candidates"]
-        idx_b = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
-        kb = b.owned(f, idx_b)
-        assert np.array_equal(idx_b[:kb].cpu().numpy().astype(np.int64), want)
+        for n_keep in (0, 8):
+            got, _ = gpu_owned(res, n_keep)
+            want = OO.owned(ref.id_lists(), n_keep)
+            assert np.array_equal(got, want) and 0 < len(want) < len(ref.cands)
+            n = res.info()["n_candidates"]
+            idx_b = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+            kb = b.owned(f, idx_b, n_keep)
+            assert np.array_equal(idx_b[:kb].cpu().numpy().astype(np.int64), want)
 
 
 def test_batch_vet_equals_per_field_pipeline():
@@ -418,7 +420,7 @@ def test_batch_vet_equals_per_field_pipeline():
     for f in range(len(fields)):
         nc = b.field_info(f)["n_candidates"]
         idx = torch.zeros(max(nc, 1), dtype=torch.int32, device="cuda")
-        k = b.owned(f, idx)
+        k = b.owned(f, idx, fields[f][6])   # the batch vets with each field's own threshold
         st = torch.zeros((max(k, 1), 9, 15, 15), dtype=torch.int16, device="cuda")
         b.stamps(f, idx, k, st)
         lg = torch.zeros(max(k, 1), device="cuda")

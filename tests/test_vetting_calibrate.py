@@ -17,3 +17,9 @@ def test_calibrate_picks_lowest_threshold_meeting_purity():
 def test_vetted_keep_keeps_plain_threshold_candidates():
     keep = vetting.vetted_keep([30, 10, 10, 25], [-5.0, 2.0, -1.0, -9.0], 25, 0.5)
     assert keep.tolist() == [True, True, False, True]
+
+
+def test_vetted_mask_is_a_superset_of_the_plain_threshold():
+    counts = np.array([30, 10, 10, 25, 7])
+    m = vetting.vetted_mask(counts, [1, 2, 3], [2.0, -1.0, -9.0], 25, 0.5)
+    assert m.tolist() == [True, True, False, True, False]
