@@ -460,10 +460,15 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
     //     the counts, and reset them to the start value -----------------------
     auto finish = [&](int kx0, int ky0) {
       __syncthreads();
+      // counter sums of this thread's words: 32 bits suffice below 32-bit counters
+      // (the tile has at most 232448 / 16 uint4, so at most 15 per thread x 16 counters x 65535)
+      using Acc = typename std::conditional<CB <= 16, uint32_t, uint64_t>::type;
+      Acc acc = 0;
+      uint32_t n_vec = 0;
       for (uint32_t i = tid; i < n_words / 4; i += kNT) {
         const uint4 v = reinterpret_cast<const uint4*>(cells)[i];
-        balance += (int64_t)word_sum<CB>(v.x) + (int64_t)word_sum<CB>(v.y) +
-                   (int64_t)word_sum<CB>(v.z) + (int64_t)word_sum<CB>(v.w) - (int64_t)4 * P * start;
+        acc += (Acc)word_sum<CB>(v.x) + (Acc)word_sum<CB>(v.y) + (Acc)word_sum<CB>(v.z) + (Acc)word_sum<CB>(v.w);
+        ++n_vec;
         if ((v.x | v.y | v.z | v.w) & tmask) {
           const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
           for (int q = 0; q < 4; ++q) {
@@ -490,6 +495,7 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
         }
         reinterpret_cast<uint4*>(cells)[i] = start4;
       }
+      balance += (int64_t)acc - (int64_t)n_vec * 4 * P * start;
       __syncthreads();
       const uint32_t ne_tile = min(s_misc[43], (uint32_t)tc.emit_cap);
       if (ne_tile) {
