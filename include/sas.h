@@ -352,7 +352,7 @@ int sas_owned(const sas_result* result, uint32_t n_keep, uint32_t* idx, uint64_t
  *   fc2.w [64], fc2.b [1].
  * Arithmetic: the kernels use BF16 copies of the weights (round to nearest
  * even), round the input and every stored activation to BF16 and accumulate
- * in FP32; deltas and gradients are FP32; Adam updates the FP32 masters and
+ * in FP32 (the convolutions of the forward pass on the tensor cores, tcgen05); deltas and gradients are FP32; Adam updates the FP32 masters and
  * refreshes the BF16 copies.  Gradients are bit-reproducible for a batch.
  * A vetter lives on the device that was current at sas_vet_create; every call
  * makes that device current for its duration. */
@@ -367,6 +367,10 @@ uint64_t sas_vet_num_params(void);
  * Errors: SAS_ERR_ARG, SAS_ERR_OOM, SAS_ERR_CUDA. */
 int sas_vet_create(int device, uint32_t max_batch, sas_vet** out);
 int sas_vet_destroy(sas_vet* vetter);
+/* Synchronizes the vetter's device and reports SAS_ERR_TIMEOUT when a wait of
+ * the tensor-core forward gave up since the last check (the kernels never wait
+ * without a limit; a wait that runs out leaves that call's logits incomplete). */
+int sas_vet_check(sas_vet* vetter);
 int sas_vet_set_adam(sas_vet* vetter, float beta1, float beta2, float eps);
 
 /* Checkpoint: host arrays of sas_vet_num_params() floats.  set_state loads

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "sas_internal.cuh"
+#include "sas_tc.cuh"
 
 struct sas_vet {
   int device;
@@ -49,6 +50,7 @@ struct sas_vet {
   float* g1;             // [B][32][13][13]
   float* partial;        // per-block weight-gradient partial sums
   float* loss;           // [1]
+  uint32_t* status;      // [1] nonzero: a tensor-core wait gave up (sas_vet_check)
 };
 
 namespace sas {
@@ -70,90 +72,175 @@ static_assert(kPartialStride >= 3 * kCh * kQ * 9 + kCh, "partial stride");
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
-// ---- forward: the three convolutions of one stamp per block iteration ---------
+// ---- forward on the tensor cores: the three convolutions as implicit GEMMs ---
+//
+// Per stamp and layer: D[pixel][out channel] = sum_k A[pixel][k] * W[out][k]
+// with k = in_channel * 9 + tap, A the im2col of the layer's input (M = output
+// pixels padded to 128-row tiles, N = 32, K = 9 * channels padded to 16s).  A is
+// built in shared memory in the no-swizzle K-major core-matrix layout, W stays
+// resident in the same layout, one thread issues tcgen05.mma (BF16 x BF16 ->
+// FP32 in TMEM), and every warp reads its TMEM lanes back for bias + ReLU + BF16
+// rounding.  Same numerics as the CUDA-core form: exact products, FP32 sums.
 
-constexpr int kFwdThreads = 512;
+constexpr int kTcThreads = 256;
+constexpr int kTcKC1 = 12;  // conv1: K = 81 padded to 96 = 12 core matrices
+constexpr int kTcKC = 36;   // conv2, conv3: K = 288
+constexpr int kSmW1 = 0;
+constexpr int kSmW2 = kSmW1 + kCh * kTcKC1 * 8 * 2;
+constexpr int kSmW3 = kSmW2 + kCh * kTcKC * 8 * 2;
+constexpr int kSmA = kSmW3 + kCh * kTcKC * 8 * 2;
+constexpr int kSmX0 = kSmA + 128 * kTcKC * 8 * 2;             // 128 x 288 >= 256 x 96
+constexpr int kSmA1 = kSmX0 + 4096;                            // 9 x 225 bf16
+constexpr int kSmA2 = kSmA1 + 10880;                           // 32 x 169 bf16
+constexpr int kSmBias = kSmA2 + 7808;                          // 32 x 121 bf16
+constexpr int kSmTab = kSmBias + 3 * kCh * 4;
+constexpr int kSmBar = kSmTab + (kTcKC1 * 8 + 2 * kTcKC * 8) * 4;
+constexpr int kTcSmem = kSmBar + 16;
+static_assert(kSmA % 128 == 0 && kSmW2 % 128 == 0 && kSmW3 % 128 == 0, "operand alignment");
+static_assert(256 * kTcKC1 * 8 <= 128 * kTcKC * 8, "conv1 operand fits the A buffer");
+static_assert(kTcSmem <= 227 * 1024, "shared memory");
 
-// out[o][p] = relu(b[o] + sum_{c,tap} in[c][p + tap] * w[o][c][tap]), p over the
-// HO x HO output; a warp owns 8 output channels and 32 pixels at a time.
-template <int C, int HI>
-__device__ __forceinline__ void conv_fwd(const float* in, const float* ws, const float* bias,
-                                         float* out_s, __nv_bfloat16* out_g) {
-  constexpr int HO = HI - 2, P = HO * HO;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int o0 = (warp & 3) * 8;
-  const int pstride = (kFwdThreads / 128) * 32;
-  for (int p = (warp >> 2) * 32 + lane; p < P; p += pstride) {
-    const int y = p / HO, x = p - y * HO;
-    float acc[8];
+// Weights of a conv layer as the B operand: B[n][k] = w[n][k] (k < kreal), 0 after.
+__device__ void tc_load_w(const __nv_bfloat16* __restrict__ w, int kreal, int kc, unsigned char* dst) {
+  for (int i = threadIdx.x; i < kCh * kc * 8; i += blockDim.x) {
+    const int n = i / (kc * 8), k = i - n * kc * 8;
+    const __nv_bfloat16 v = k < kreal ? w[n * kreal + k] : __float2bfloat16_rn(0.f);
+    *reinterpret_cast<__nv_bfloat16*>(dst + tc::cm_offset(n, k, kc)) = v;
+  }
+}
+
+// im2col of one layer into A: chunk ci (16 bytes = 8 consecutive k of one row)
+// sits at byte ci * 16, so consecutive threads store consecutive chunks.
+template <int HI, int KC, int NTILE>
+__device__ __forceinline__ void tc_im2col(const __nv_bfloat16* act, const int* tab, unsigned char* A) {
+  constexpr int HO = HI - 2, P = HO * HO, CHUNKS = NTILE * 128 * KC;
+  const uint16_t* a16 = reinterpret_cast<const uint16_t*>(act);
+  for (int ci = threadIdx.x; ci < CHUNKS; ci += kTcThreads) {
+    const int mr = ci & 7, g = ci >> 3, kc = g % KC, m = (g / KC) * 8 + mr;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    if (m < P) {
+      const int y = m / HO, base = y * HI + (m - y * HO);
+      const int* t = tab + kc * 8;
+      uint32_t v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = bias[o0 + j];
-    for (int c = 0; c < C; ++c) {
-      const float* ip = in + c * HI * HI + y * HI + x;
-      const float* wp = ws + c * 9 * kCh + o0;
+      for (int j = 0; j < 8; ++j) v[j] = t[j] >= 0 ? (uint32_t)a16[base + t[j]] : 0u;
+      w0 = v[0] | (v[1] << 16); w1 = v[2] | (v[3] << 16); w2 = v[4] | (v[5] << 16); w3 = v[6] | (v[7] << 16);
+    }
+    *reinterpret_cast<uint4*>(A + ci * 16) = make_uint4(w0, w1, w2, w3);
+  }
+}
+
+// Bias, ReLU and BF16 rounding of D (NTILE tiles of 128 pixels x 32 channels at
+// TMEM column 32 * tile) into out_s[ch][p] (shared) and out_g (global, optional).
+template <int P, int NTILE>
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, const float* bias, __nv_bfloat16* out_s,
+                                            __nv_bfloat16* out_g) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const float a = ip[(tap / 3) * HI + tap % 3];
-        const float4 w0 = *reinterpret_cast<const float4*>(wp + tap * kCh);
-        const float4 w1 = *reinterpret_cast<const float4*>(wp + tap * kCh + 4);
-        acc[0] = fmaf(a, w0.x, acc[0]); acc[1] = fmaf(a, w0.y, acc[1]);
-        acc[2] = fmaf(a, w0.z, acc[2]); acc[3] = fmaf(a, w0.w, acc[3]);
-        acc[4] = fmaf(a, w1.x, acc[4]); acc[5] = fmaf(a, w1.y, acc[5]);
-        acc[6] = fmaf(a, w1.z, acc[6]); acc[7] = fmaf(a, w1.w, acc[7]);
+  for (int t = 0; t < NTILE; ++t) {
+    float v[16];
+    tc::ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32 + h * 16), v);
+    const int m = t * 128 + q * 32 + lane;
+    if (m < P) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int ch = h * 16 + j;
+        const __nv_bfloat16 r = __float2bfloat16_rn(fmaxf(v[j] + bias[ch], 0.f));
+        if (out_s) out_s[ch * P + m] = r;
+        if (out_g) out_g[ch * P + m] = r;
       }
     }
+  }
+}
+
+// One layer: im2col, MMAs by thread 0, bounded wait, epilogue.  Returns false
+// (block-uniform) when the wait gave up.
+template <int HI, int KC, int NTILE>
+__device__ __forceinline__ bool tc_layer(const __nv_bfloat16* act, const int* tab, unsigned char* A,
+                                         const unsigned char* W, uint32_t tmem, uint64_t* bar, uint32_t& phase,
+                                         const float* bias, __nv_bfloat16* out_s, __nv_bfloat16* out_g) {
+  constexpr int HO = HI - 2;
+  tc_im2col<HI, KC, NTILE>(act, tab, A);
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::fence_after_sync();
+    const uint32_t a0 = tc::smem_u32(A), w0 = tc::smem_u32(W);
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float r = bf(fmaxf(acc[j], 0.f));
-      if (out_s) out_s[(o0 + j) * P + p] = r;
-      if (out_g) out_g[(o0 + j) * P + p] = __float2bfloat16_rn(r);
-    }
+    for (int t = 0; t < NTILE; ++t)
+      for (int ks = 0; ks < KC / 2; ++ks)
+        tc::mma_bf16(tmem + (uint32_t)(t * 32), tc::smem_desc(a0 + (uint32_t)((t * 16 * KC + 2 * ks) * 128), KC),
+                     tc::smem_desc(w0 + (uint32_t)(2 * ks * 128), KC), idesc, ks > 0);
+    tc::commit(bar);
   }
+  const bool ok = tc::mbar_wait(bar, phase, 1u << 22);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) return false;
+  tc::fence_after_sync();
+  tc_epilogue<HO * HO, NTILE>(tmem, bias, out_s, out_g);
+  tc::fence_before_sync();
+  __syncthreads();
+  return true;
 }
 
-// Weights of a conv layer into shared memory as float [c][tap][o].
-template <int C>
-__device__ void load_conv_w(const __nv_bfloat16* w, float* ws) {
-  for (int i = threadIdx.x; i < kCh * C * 9; i += blockDim.x) {
-    const int o = i / (C * 9), r = i - o * C * 9;
-    ws[r * kCh + o] = ld(w + i);  // r = c * 9 + tap
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* __restrict__ stamps,
+                                                               const uint32_t* __restrict__ idx, uint32_t n,
+                                                               const __nv_bfloat16* __restrict__ wb,
+                                                               __nv_bfloat16* a1g, __nv_bfloat16* a2g,
+                                                               __nv_bfloat16* __restrict__ a3g,
+                                                               uint32_t* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smc[];
+  __nv_bfloat16* x0 = reinterpret_cast<__nv_bfloat16*>(smc + kSmX0);
+  __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(smc + kSmA1);
+  __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(smc + kSmA2);
+  float* bias = reinterpret_cast<float*>(smc + kSmBias);
+  int* tab1 = reinterpret_cast<int*>(smc + kSmTab);
+  int* tab2 = tab1 + kTcKC1 * 8;
+  int* tab3 = tab2 + kTcKC * 8;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smc + kSmBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smc + kSmBar + 8);
+  const int tid = threadIdx.x;
+  if (tid < 32) tc::tmem_alloc(tslot, 64);
+  if (tid == 0) tc::mbar_init(bar, 1);
+  tc_load_w(wb + kW1, kQ * 9, kTcKC1, smc + kSmW1);
+  tc_load_w(wb + kW2, kCh * 9, kTcKC, smc + kSmW2);
+  tc_load_w(wb + kW3, kCh * 9, kTcKC, smc + kSmW3);
+  if (tid < 3 * kCh) {
+    const int l = tid / kCh, o = tid % kCh;
+    bias[tid] = ld(wb + (l == 0 ? kB1 : l == 1 ? kB2 : kB3) + o);
   }
-}
-
-constexpr int kFwdSmemFloats = kCh * kQ * 9 + 2 * kCh * kCh * 9 + 3 * kCh + kQ * kS * kS +
-                               kCh * kH1 * kH1 + kCh * kH2 * kH2;
-
-__global__ void __launch_bounds__(kFwdThreads) k_conv_fwd(const uint16_t* __restrict__ stamps,
-                                                          const uint32_t* __restrict__ idx,
-                                                          uint32_t n, const __nv_bfloat16* __restrict__ wb,
-                                                          __nv_bfloat16* a1g, __nv_bfloat16* a2g,
-                                                          __nv_bfloat16* __restrict__ a3g) {
-  extern __shared__ __align__(16) float sm[];
-  float* w1s = sm;
-  float* w2s = w1s + kCh * kQ * 9;
-  float* w3s = w2s + kCh * kCh * 9;
-  float* bs = w3s + kCh * kCh * 9;
-  float* x0 = bs + 3 * kCh;
-  float* a1 = x0 + kQ * kS * kS;
-  float* a2 = a1 + kCh * kH1 * kH1;
-  load_conv_w<kQ>(wb + kW1, w1s);
-  load_conv_w<kCh>(wb + kW2, w2s);
-  load_conv_w<kCh>(wb + kW3, w3s);
-  if (threadIdx.x < 3 * kCh) {
-    const int l = threadIdx.x / kCh, o = threadIdx.x % kCh;
-    bs[threadIdx.x] = ld(wb + (l == 0 ? kB1 : l == 1 ? kB2 : kB3) + o);
+  // k -> offset of the input element in the layer's [C][HI][HI] activation
+  for (int k = tid; k < kTcKC1 * 8; k += kTcThreads)
+    tab1[k] = k < kQ * 9 ? (k / 9) * kS * kS + ((k % 9) / 3) * kS + (k % 3) : -1;
+  for (int k = tid; k < kTcKC * 8; k += kTcThreads) {
+    tab2[k] = (k / 9) * kH1 * kH1 + ((k % 9) / 3) * kH1 + (k % 3);
+    tab3[k] = (k / 9) * kH2 * kH2 + ((k % 9) / 3) * kH2 + (k % 3);
   }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  uint32_t phase = 0;
   for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
     const uint16_t* st = stamps + (size_t)(idx ? idx[b] : b) * kQ * kS * kS;
-    for (int i = threadIdx.x; i < kQ * kS * kS; i += blockDim.x) x0[i] = bf((float)st[i] * 0.0625f);
+    for (int i = tid; i < kQ * kS * kS; i += kTcThreads) x0[i] = __float2bfloat16_rn((float)st[i] * 0.0625f);
     __syncthreads();
-    conv_fwd<kQ, kS>(x0, w1s, bs, a1, a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr);
-    __syncthreads();
-    conv_fwd<kCh, kH1>(a1, w2s, bs + kCh, a2, a2g ? a2g + (size_t)b * kCh * kH2 * kH2 : nullptr);
-    __syncthreads();
-    conv_fwd<kCh, kH2>(a2, w3s, bs + 2 * kCh, nullptr, a3g + (size_t)b * kF);
-    __syncthreads();
+    if (!tc_layer<kS, kTcKC1, 2>(x0, tab1, smc + kSmA, smc + kSmW1, tmem, bar, phase, bias, a1,
+                                 a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr) ||
+        !tc_layer<kH1, kTcKC, 1>(a1, tab2, smc + kSmA, smc + kSmW2, tmem, bar, phase, bias + kCh, a2,
+                                 a2g ? a2g + (size_t)b * kCh * kH2 * kH2 : nullptr) ||
+        !tc_layer<kH2, kTcKC, 1>(a2, tab3, smc + kSmA, smc + kSmW3, tmem, bar, phase, bias + 2 * kCh, nullptr,
+                                 a3g + (size_t)b * kF)) {
+      if (tid == 0) atomicOr(status, 1u);
+      break;
+    }
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tc::tmem_free(tmem, 64);
 }
 
 // ---- forward: fc1 (+ReLU) and fc2 for 32 stamps per block --------------------
@@ -524,8 +611,7 @@ constexpr size_t back_smem() {
 cudaError_t set_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_conv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(kFwdSmemFloats * sizeof(float)));
+  cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_back<kCh, kH2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)back_smem<kCh, kH2, true>());
@@ -555,8 +641,8 @@ cudaError_t forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* idx, ui
                     float* logits, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
-  k_conv_fwd<<<blocks, kFwdThreads, kFwdSmemFloats * sizeof(float), s>>>(
-      stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr, keep ? vt->a2 : nullptr, vt->a3);
+  k_conv_fwd_tc<<<blocks, kTcThreads, kTcSmem, s>>>(stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr,
+                                                   keep ? vt->a2 : nullptr, vt->a3, vt->status);
   k_fc_fwd<<<(n + kFcTB - 1) / kFcTB, 256, 0, s>>>(vt->a3, n, vt->wf1t, vt->wb, keep ? vt->a4 : nullptr,
                                                     logits);
   note_launch(2);
@@ -636,7 +722,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void free_vet(sas_vet* vt) {
   void* ptrs[] = {vt->master, vt->m, vt->v, vt->grad, vt->wb, vt->wf1t, vt->a1, vt->a2, vt->a3,
-                  vt->a4, vt->logits, vt->glogit, vt->g4, vt->g3, vt->g2, vt->g1, vt->partial, vt->loss};
+                  vt->a4, vt->logits, vt->glogit, vt->g4, vt->g3, vt->g2, vt->g1, vt->partial, vt->loss,
+                  vt->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete vt;
@@ -674,6 +761,7 @@ int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
       {(void**)&vt->glogit, B * 4}, {(void**)&vt->g4, B * vet::kHid * 4}, {(void**)&vt->g3, B * vet::kF * 4},
       {(void**)&vt->g2, B * vet::kCh * vet::kH2 * vet::kH2 * 4}, {(void**)&vt->g1, B * vet::kCh * vet::kH1 * vet::kH1 * 4},
       {(void**)&vt->partial, (size_t)vet::kBackBlocks * vet::kPartialStride * 4}, {(void**)&vt->loss, 4},
+      {(void**)&vt->status, 4},
   };
   for (auto& r : reqs) {
     if (cudaError_t e = cudaMalloc(r.p, r.bytes); e != cudaSuccess) {
@@ -681,6 +769,7 @@ int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
       return cuda_fail(e, "sas_vet_create: cudaMalloc");
     }
   }
+  cudaMemset(vt->status, 0, 4);
   cudaMemset(vt->master, 0, N * 4);
   cudaMemset(vt->m, 0, N * 4);
   cudaMemset(vt->v, 0, N * 4);
@@ -699,6 +788,18 @@ int sas_vet_destroy(sas_vet* vt) {
   DeviceGuard guard(vt->device);
   cudaDeviceSynchronize();
   free_vet(vt);
+  return SAS_OK;
+}
+
+int sas_vet_check(sas_vet* vt) {
+  if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_check: NULL vetter");
+  DeviceGuard guard(vt->device);
+  uint32_t st = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&st, vt->status, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && st) e = cudaMemset(vt->status, 0, 4);
+  if (e != cudaSuccess) return cuda_fail(e, "sas_vet_check");
+  if (st) return set_error(SAS_ERR_TIMEOUT, "sas_vet_check: a tensor-core wait gave up; logits are incomplete");
   return SAS_OK;
 }
 

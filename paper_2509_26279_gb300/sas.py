@@ -404,6 +404,7 @@ _lib.sas_vet_num_params.restype = ctypes.c_uint64
 _lib.sas_vet_create.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(_p)]
 _lib.sas_vet_destroy.argtypes = [_p]
 _lib.sas_vet_set_adam.argtypes = [_p, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+_lib.sas_vet_check.argtypes = [_p]
 _lib.sas_vet_set_state.argtypes = [_p, _p, _p, _p, ctypes.c_uint64]
 _lib.sas_vet_get_state.argtypes = [_p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]
 _lib.sas_vet_get_bf16.argtypes = [_p, _p]
@@ -421,7 +422,7 @@ _lib.sas_batch_vet.argtypes = [_p, _p, _p, _p, _p, ctypes.c_uint64, ctypes.POINT
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
              "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
              "sas_vet_forward", "sas_vet_gradients", "sas_vet_apply_gradients",
-             "sas_vet_train_step", "sas_stamps_indexed", "sas_peaks", "sas_batch_peaks",
+             "sas_vet_train_step", "sas_vet_check", "sas_stamps_indexed", "sas_peaks", "sas_batch_peaks",
              "sas_batch_stamps", "sas_owned", "sas_batch_owned", "sas_batch_vet"]
 
 STAMP_SHAPE = (9, 15, 15)
@@ -483,6 +484,10 @@ class Vetter:
         self._h = h
         self.max_batch = int(max_batch)
         self.n_params = vet_num_params()
+
+    def check(self):
+        """Synchronize; raise if a tensor-core wait gave up since the last check."""
+        _check(_lib.sas_vet_check(self._h))
 
     def set_adam(self, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(_lib.sas_vet_set_adam(self._h, beta1, beta2, eps))

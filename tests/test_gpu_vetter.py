@@ -127,6 +127,7 @@ def test_forward_within_bf16_bound(n, big):
     st = rand_stamps(rng, n, big)
     logits = torch.zeros(n, dtype=torch.float32, device="cuda")
     vt.forward(to_dev_stamps(st), n, logits)
+    vt.check()
     got = logits.cpu().numpy().astype(np.float64)
     wb = V.bf16_round(params).astype(np.float64)
     want = V.forward(wb, st)[0]
