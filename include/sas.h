@@ -341,6 +341,21 @@ int sas_peaks(const sas_result* result, uint32_t* idx, uint64_t* n_peaks, void* 
 int sas_owned(const sas_result* result, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept,
               void* stream);
 
+/* Cluster finding (Sec. 2.1 step 3): repeatedly take the cell with the largest
+ * count (the search's total order on the current counts: distinct desc, raw
+ * desc, v_idx, by, bx), stop when it is below n_min, else report its remaining
+ * detections as a cluster and remove them from every cell; at most
+ * max_clusters clusters (0: 1000, the paper's cut).  Removing detections only
+ * lowers counts, so the loop runs over the search's candidate list; n_min must
+ * be at least the search's threshold and the search must not have been cut to
+ * its top candidates.  On success *out is a new result (free it with
+ * sas_result_free) whose candidates are the clusters in the order found, with
+ * their current counts and ids (disjoint across clusters, ascending);
+ * sas_stamps does not apply to it.  Synchronizes the stream.
+ * Errors: SAS_ERR_ARG, SAS_ERR_RANGE, SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_peel(const sas_result* result, uint32_t n_min, uint32_t max_clusters, void* stream,
+             sas_result** out);
+
 /* The network (input = count / 16):
  *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),
  *   ReLU; conv3 32 -> 32 (11 -> 9), ReLU; flatten in (channel, row, column)

@@ -37,7 +37,9 @@ struct sas_result {
   int32_t* d_syt;
   SearchGeom g;
   CoarseGeom cg;
-  uint64_t n_det;  // catalog size (detection ids are < n_det)
+  uint64_t n_det;     // catalog size (detection ids are < n_det)
+  uint32_t n_min;     // the search's threshold
+  int complete;       // every cell >= n_min is in the list (no top-K cut)
 };
 
 namespace {
@@ -204,9 +206,11 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   memset(res, 0, sizeof(*res));
   res->device = dev;
   res->n_det = n;
+  res->n_min = n_min;
 
   if (n == 0 || v_begin == v_end) {
     res->info.t0 = 0;
+    res->complete = 1;
     *out = res;
     return SAS_OK;
   }
@@ -418,6 +422,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       tr.mark("ids done");
       if (h_small[0] & kFlagInternal) { rc = fail(SAS_ERR_INTERNAL, "id gather invariant"); goto done; }
       res->info.n_candidates = n_out;
+      res->complete = n_out == h_small[2];
       res->info.n_ids = n_ids;
       res->info.n_pairs = h_small64[0];
       res->info.n_emitted = n_emit;
@@ -486,6 +491,7 @@ int sas_candidates(const sas_result* r, sas_candidate* out, uint64_t cap, uint64
 
 int sas_stamps(const sas_result* r, uint64_t first, uint64_t count, uint16_t* out, void* stream) {
   if (!r) return fail(SAS_ERR_ARG, "null result");
+  if (!r->d_dets && count) return fail(SAS_ERR_ARG, "this result keeps no catalog (a cluster list)");
   const uint64_t nc = r->info.n_candidates;
   if (first > nc || count > nc - first)
     return fail(SAS_ERR_ARG, "candidates [%llu, %llu) outside the result's %llu", (unsigned long long)first,
@@ -500,10 +506,40 @@ int sas_stamps(const sas_result* r, uint64_t first, uint64_t count, uint16_t* ou
 int sas_stamps_indexed(const sas_result* r, const uint32_t* idx, uint64_t count, uint16_t* out,
                        void* stream) {
   if (!r) return fail(SAS_ERR_ARG, "null result");
+  if (!r->d_dets && count) return fail(SAS_ERR_ARG, "this result keeps no catalog (a cluster list)");
   if (count == 0) return SAS_OK;
   if (!idx || !out) return fail(SAS_ERR_ARG, "null index or stamp buffer");
   cudaError_t e = launch_stamps(result_view(r), idx, 0, count, out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "stamps");
+  return SAS_OK;
+}
+
+int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, void* stream, sas_result** out) {
+  if (!r || !out) return fail(SAS_ERR_ARG, "null argument");
+  if (!r->d_dets && r->info.n_candidates)
+    return fail(SAS_ERR_ARG, "cluster finding needs a search result (this one is a cluster list)");
+  if (n_min < r->n_min || n_min == 0)
+    return fail(SAS_ERR_ARG, "n_min %u is below the search's threshold %u (cells under it are not in the list)",
+                n_min, r->n_min);
+  if (!r->complete) return fail(SAS_ERR_ARG, "the search kept only its top candidates (max_candidates)");
+  if (max_clusters == 0) max_clusters = 1000;
+  cudaStream_t s = (cudaStream_t)stream;
+  PeelOut po;
+  if (int rc = peel_clusters(result_view(r), n_min, max_clusters, s, &po)) return rc;
+  sas_result* res = new sas_result();
+  std::memset(res, 0, sizeof(*res));
+  res->device = r->device;
+  res->d_cands = po.cands;
+  res->d_ids = po.ids;
+  res->info = r->info;
+  res->info.n_candidates = po.n;
+  res->info.n_ids = po.n_ids;
+  res->g = r->g;
+  res->cg = r->cg;
+  res->n_det = r->n_det;
+  res->n_min = n_min;
+  res->complete = 0;
+  *out = res;
   return SAS_OK;
 }
 

@@ -239,6 +239,16 @@ int select_owned(const CandView& v, uint32_t n_keep, uint32_t* idx, uint64_t* n_
 cudaError_t vet_forward_all(sas_vet* vt, const uint16_t* stamps, uint64_t n, float* logits, cudaStream_t s);
 int vet_device(const sas_vet* vt);
 
+// sas_peel.cu: cluster finding (Sec. 2.1 step 3) over v's candidates with
+// threshold n_min, at most max_clusters clusters; on success out holds device
+// arrays (owned by the caller) of the clusters and their ids.
+struct PeelOut {
+  sas_candidate* cands = nullptr;
+  uint32_t* ids = nullptr;
+  uint64_t n = 0, n_ids = 0;
+};
+int peel_clusters(const CandView& v, uint32_t n_min, uint32_t max_clusters, cudaStream_t s, PeelOut* out);
+
 // sas_api.cu: the candidate view of a finished search.
 CandView result_view(const sas_result* r);
 
