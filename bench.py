@@ -291,6 +291,56 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     return result
 
 
+def peel_section(grid, dx, dy, de, cat, w, stream, reps: int = 5) -> dict:
+    """Cluster finding (Sec. 2.1 step 3) on one search result of the bench
+    workload: time per sas_peel call (setup + the loop + output records), the
+    clusters it returns and how they map onto the injected movers."""
+    import torch
+    from paper_2509_26279_gb300 import sas
+
+    res = sas.sas_stack(grid, dx, dy, de, cat.t, cat.ticks_per_hour, w.n_min, on_device=True, stream=stream)
+    n_cand = int(res.info()["n_candidates"])
+    ms = []
+    for i in range(reps + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pl = sas.sas_peel(res, w.n_min, 1000, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            ms.append(a.elapsed_time(b))
+        if i < reps + 1:
+            pl.free()
+    cands, ids = pl.candidates()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sq = sas.sas_peel(res, w.n_min, 1000, stream=stream, sequential=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(b)
+    same = len(sq.candidates()[0]) == len(cands)
+    sq.free()
+    found, pure = set(), 0
+    for c in cands:
+        m = cat.mover[ids[int(c["id_off"]): int(c["id_off"]) + int(c["id_len"])]]
+        top = np.bincount(m[m >= 0]).argmax() if (m >= 0).any() else -1
+        if top >= 0 and 2 * int((m == top).sum()) >= len(m):
+            pure += 1
+            found.add(int(top))
+    ep = {}
+    for e, mv in zip(cat.epoch[cat.mover >= 0], cat.mover[cat.mover >= 0]):
+        ep.setdefault(int(mv), set()).add(int(e))
+    findable = sum(len(v) >= w.n_min for v in ep.values())
+    pl.free()
+    res.free()
+    return {"form": "greedy peel over the search's candidates, N_min as the search, at most 1000 clusters; "
+                    "rounds of local maxima",
+            "ms": round(statistics.median(ms), 4), "ms_one_cluster_per_step": round(ms_seq, 4),
+            "same_count_both_forms": same, "candidates_in": n_cand, "clusters": int(len(cands)),
+            "clusters_one_mover": pure, "movers_found": len(found), "movers_findable": findable,
+            "timing": f"CUDA events around sas_peel on the launching stream, median of {reps}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -455,6 +505,8 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(launches), "roofline": roof}
+    if world == 1:
+        out["peel"] = peel_section(grid, dx, dy, de, cat, w, stream)
     if world == 1 and not args.no_fields:
         out["fields"] = fields_section(dev, stream)
     if world == 1 and not args.no_cpu_baseline:

@@ -348,12 +348,22 @@ int sas_owned(const sas_result* result, uint32_t n_keep, uint32_t* idx, uint64_t
  * max_clusters clusters (0: 1000, the paper's cut).  Removing detections only
  * lowers counts, so the loop runs over the search's candidate list; n_min must
  * be at least the search's threshold and the search must not have been cut to
- * its top candidates.  On success *out is a new result (free it with
- * sas_result_free) whose candidates are the clusters in the order found, with
- * their current counts and ids (disjoint across clusters, ascending);
- * sas_stamps does not apply to it.  Synchronizes the stream.
- * Errors: SAS_ERR_ARG, SAS_ERR_RANGE, SAS_ERR_OOM, SAS_ERR_CUDA. */
-int sas_peel(const sas_result* result, uint32_t n_min, uint32_t max_clusters, void* stream,
+ * its top candidates.
+ * By default the loop runs as rounds that pick every local maximum at once (a
+ * candidate whose key beats every live candidate it shares a detection with is
+ * certain to be picked with its current detections); flags =
+ * SAS_PEEL_SEQUENTIAL runs it one cluster at a time in a single block.  Both
+ * give the same clusters in the same order.
+ * On success *out is a new result (free it with sas_result_free) whose
+ * candidates are the clusters in the order found, with their current counts
+ * and ids (disjoint across clusters, ascending); sas_stamps and sas_peel do not
+ * apply to it.  Synchronizes the stream.  Device scratch: about 30 bytes per
+ * detection plus 40 per candidate.
+ * Errors: SAS_ERR_ARG (null pointers, n_min below the search's, a top-K or
+ * cluster result, unknown flags), SAS_ERR_RANGE (2^31 or more candidates or
+ * detections), SAS_ERR_OOM, SAS_ERR_CUDA. */
+#define SAS_PEEL_SEQUENTIAL 1u
+int sas_peel(const sas_result* result, uint32_t n_min, uint32_t max_clusters, uint32_t flags, void* stream,
              sas_result** out);
 
 /* The network (input = count / 16):

@@ -514,7 +514,8 @@ int sas_stamps_indexed(const sas_result* r, const uint32_t* idx, uint64_t count,
   return SAS_OK;
 }
 
-int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, void* stream, sas_result** out) {
+int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, uint32_t flags, void* stream,
+             sas_result** out) {
   if (!r || !out) return fail(SAS_ERR_ARG, "null argument");
   if (!r->d_dets && r->info.n_candidates)
     return fail(SAS_ERR_ARG, "cluster finding needs a search result (this one is a cluster list)");
@@ -522,10 +523,12 @@ int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, void* s
     return fail(SAS_ERR_ARG, "n_min %u is below the search's threshold %u (cells under it are not in the list)",
                 n_min, r->n_min);
   if (!r->complete) return fail(SAS_ERR_ARG, "the search kept only its top candidates (max_candidates)");
+  if (flags & ~SAS_PEEL_SEQUENTIAL) return fail(SAS_ERR_ARG, "unknown flags 0x%x", flags);
   if (max_clusters == 0) max_clusters = 1000;
   cudaStream_t s = (cudaStream_t)stream;
   PeelOut po;
-  if (int rc = peel_clusters(result_view(r), n_min, max_clusters, s, &po)) return rc;
+  if (int rc = peel_clusters(result_view(r), n_min, max_clusters, (flags & SAS_PEEL_SEQUENTIAL) != 0, s, &po))
+    return rc;
   sas_result* res = new sas_result();
   std::memset(res, 0, sizeof(*res));
   res->device = r->device;

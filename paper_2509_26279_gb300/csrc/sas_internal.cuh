@@ -247,7 +247,9 @@ struct PeelOut {
   uint32_t* ids = nullptr;
   uint64_t n = 0, n_ids = 0;
 };
-int peel_clusters(const CandView& v, uint32_t n_min, uint32_t max_clusters, cudaStream_t s, PeelOut* out);
+// sequential: run the loop as stated in one block instead of rounds of local maxima
+int peel_clusters(const CandView& v, uint32_t n_min, uint32_t max_clusters, bool sequential, cudaStream_t s,
+                  PeelOut* out);
 
 // sas_api.cu: the candidate view of a finished search.
 CandView result_view(const sas_result* r);

@@ -418,7 +418,7 @@ _lib.sas_batch_peaks.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.
 _lib.sas_batch_stamps.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64, _p, _p]
 _lib.sas_owned.argtypes = [_p, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
 _lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_uint64), _p]
-_lib.sas_peel.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, _p, ctypes.POINTER(_p)]
+_lib.sas_peel.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _p, ctypes.POINTER(_p)]
 _lib.sas_batch_vet.argtypes = [_p, _p, _p, _p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p]
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
              "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
@@ -466,11 +466,16 @@ def sas_owned(result: Result, idx_dev, n_keep: int = 0, stream=None) -> int:
     return n.value
 
 
-def sas_peel(result: Result, n_min: int, max_clusters: int = 1000, stream=None) -> Result:
+PEEL_SEQUENTIAL = 1
+
+
+def sas_peel(result: Result, n_min: int, max_clusters: int = 1000, stream=None, sequential: bool = False) -> Result:
     """Cluster finding (Sec. 2.1 step 3) over a search result: a new Result
     whose candidates are the clusters in the order found."""
     h = _p()
-    _check(_lib.sas_peel(result._h, int(n_min), int(max_clusters), _stream_handle(stream), ctypes.byref(h)))
+    flags = PEEL_SEQUENTIAL if sequential else 0
+    _check(_lib.sas_peel(result._h, int(n_min), int(max_clusters), flags, _stream_handle(stream),
+                         ctypes.byref(h)))
     return Result(h)
 
 
