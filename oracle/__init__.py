@@ -9,6 +9,10 @@ its binding) never touches it; the two share no code.
 * ``brute.py``      a second, independent formulation in pure Python
                     (dict of epoch sets) for tiny inputs; pins the C oracle.
 * ``vetter.py``     float64 NumPy forward/backward of the candidate-vetting CNN.
+* ``peel.py``       cluster finding (Sec. 2.1 step 3), over the candidate list and
+                    as the literal rerun-the-search loop.
+* ``refine.py``     refinement and gathering (Sec. 2.1 steps 4-6): MCD regression
+                    by FAST-MCD with counter-based draws, gathering, iteration.
 
 Parity status: the stack oracle is pinned (brute force, hand-built movers,
 invariants, noise statistics; see tests/test_oracle_*.py).
