@@ -366,6 +366,80 @@ int sas_owned(const sas_result* result, uint32_t n_keep, uint32_t* idx, uint64_t
 int sas_peel(const sas_result* result, uint32_t n_min, uint32_t max_clusters, uint32_t flags, void* stream,
              sas_result** out);
 
+/* ---- Refinement and gathering (Sec. 2.1 steps 4-6) -------------------------
+ *
+ * For each cluster (a candidate and its ids): fit a linear trajectory by
+ * multivariate regression of (x, y) on t with the mean and covariance of the
+ * Minimum Covariance Determinant subset of the points (t, x, y), found by
+ * FAST-MCD (Rousseeuw & Van Driessen 1999); gather every detection of the
+ * search's catalog whose distance to the line's position at its own epoch is at
+ * most `radius`; repeat on the gathered set until it equals the fitted set.
+ *   Points: t = epoch time - t0 in ticks, x and y in mpx.  h = floor((n + 4)/2);
+ *   fewer than 5 points are fitted by least squares on all of them.  FAST-MCD:
+ *   n_starts random 4-subsets (extended one point at a time while singular,
+ *   up to h), the h nearest points, two C-steps (stopping at the first that
+ *   does not lower det); the n_best lowest determinants continue for up to
+ *   max_csteps C-steps; lowest determinant wins, ties to the lower start.
+ *   Draws: start s of cluster k in round it uses key = mix(mix(mix(seed +
+ *   (k+1)g) + (it+1)g) + (s+1)g) and draw j = mix(key + (j+1)g), SplitMix64's
+ *   mix and g = 0x9E3779B97F4A7C15, mod 2^64; step j of the start's partial
+ *   Fisher-Yates shuffle swaps positions j and j + draw_j mod (n - j).
+ *   Arithmetic: exact integer moment sums; the scatter matrix rounded once to
+ *   double; then fixed IEEE double expressions, so the result does not depend
+ *   on how the GPU orders its reductions.
+ * Output per cluster (in the clusters' order): the line (vx, vy in mpx/h; x0,
+ * y0 in mpx at t0), the subset's residual covariance, det of its scatter
+ * matrix (subset size^2 x covariance), status, and the ids (ascending) of the
+ * last gathering -- of the fitted set for SAS_TRACK_TOO_MANY, of the cluster
+ * when nothing was fitted.
+ */
+#define SAS_REFINE_MAX_POINTS 1024u
+#define SAS_TRACK_CONVERGED 0u   /* the gathered set is the fitted set           */
+#define SAS_TRACK_MAX_ITER 1u    /* max_iter fits without a fixed point          */
+#define SAS_TRACK_DEGENERATE 2u  /* one epoch only (no slope), or < 2 gathered   */
+#define SAS_TRACK_TOO_MANY 3u    /* more than SAS_REFINE_MAX_POINTS points        */
+
+typedef struct sas_refine_opts {
+  uint64_t seed;
+  uint32_t n_starts;    /* 0: 500 (at most 4096)                           */
+  uint32_t n_best;      /* 0: 10 (at most n_starts)                        */
+  uint32_t max_csteps;  /* 0: 100                                          */
+  uint32_t max_iter;    /* fits per cluster, 0: 10                         */
+  int32_t radius;       /* gather radius in mpx, 0: the search's bin       */
+  uint32_t reserved;
+} sas_refine_opts;
+
+typedef struct sas_track {
+  double vx, vy;                  /* mpx per hour (NaN when no line)          */
+  double x0, y0;                  /* mpx at t0                                */
+  double res_xx, res_xy, res_yy;  /* residual covariance of the subset, mpx^2 */
+  double det;                     /* det of the subset's scatter matrix       */
+  uint32_t status;                /* SAS_TRACK_*                              */
+  uint32_t iterations;            /* fits made                                */
+  uint32_t h;                     /* points in the MCD subset                 */
+  uint32_t n_points;              /* points of the last fit                   */
+  uint64_t id_off;
+  uint32_t id_len;
+  uint32_t cluster;               /* index in the cluster list                */
+} sas_track;
+
+typedef struct sas_tracks sas_tracks;
+
+/* search: a search result (its catalog is gathered from); clusters: a result
+ * whose candidates are the clusters -- the output of sas_peel on `search`, or
+ * `search` itself.  opts may be NULL (all defaults, seed 0).  Synchronizes the
+ * stream.  Device scratch: about 8 KB per cluster plus 16 bytes per detection.
+ * Errors: SAS_ERR_ARG (null pointers, a cluster list as `search`, catalogs of
+ * different sizes, n_starts > 4096), SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_refine(const sas_result* search, const sas_result* clusters, const sas_refine_opts* opts, void* stream,
+               sas_tracks** out);
+
+/* Copy up to cap tracks and ids_cap ids (host or device buffers, on_device
+ * selects); totals written when the pointers are non-NULL. */
+int sas_tracks_get(const sas_tracks* tracks, sas_track* out, uint64_t cap, uint64_t* n_total, uint32_t* ids,
+                   uint64_t ids_cap, uint64_t* n_ids_total, int on_device);
+void sas_tracks_free(sas_tracks* tracks);
+
 /* The network (input = count / 16):
  *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),
  *   ReLU; conv3 32 -> 32 (11 -> 9), ReLU; flatten in (channel, row, column)

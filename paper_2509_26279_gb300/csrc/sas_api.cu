@@ -35,6 +35,7 @@ struct sas_result {
   uint32_t* d_ecount;
   int32_t* d_sxt;
   int32_t* d_syt;
+  int64_t* d_dt;      // per-epoch time minus t0, ticks
   SearchGeom g;
   CoarseGeom cg;
   uint64_t n_det;     // catalog size (detection ids are < n_det)
@@ -250,7 +251,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     const uint16_t* dep = cat->epoch;
     int32_t *hx = nullptr, *hy = nullptr;
     uint16_t* hep = nullptr;
-    int64_t *d_t = nullptr, *d_dt = nullptr, *d_t0 = nullptr;
+    int64_t *d_t = nullptr, *d_dt = nullptr, *d_t0 = nullptr;  // d_dt is kept by the result
     uint32_t *d_ecount = nullptr, *d_bcount = nullptr, *d_boff = nullptr, *d_cursor = nullptr,
              *d_bof = nullptr, *d_scan = nullptr;
     Det* d_dets = nullptr;
@@ -282,16 +283,18 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       dx = hx; dy = hy; dep = hep;
     }
     CK(sc.alloc(&d_t, E), "alloc t");
-    CK(sc.alloc(&d_dt, E), "alloc dt");
+    CK(cudaMallocAsync((void**)&d_dt, (size_t)E * 8, s), "alloc dt");
+    res->d_dt = d_dt;
     CK(sc.alloc(&d_t0, 1), "alloc t0");
     CK(cudaMemcpyAsync(d_t, cat->t, E * 8, cudaMemcpyHostToDevice, s), "copy t");
     CK(cudaMallocAsync((void**)&d_ecount, (size_t)E * 4, s), "alloc ecount");
     res->d_ecount = d_ecount;
-    CK(sc.alloc(&d_bcount, nb), "alloc bucket counts");
-    CK(cudaMallocAsync((void**)&d_boff, (nb + 1) * 4, s), "alloc bucket offsets");
+    // nb grid buckets plus one overflow bucket (detections outside the grid)
+    CK(sc.alloc(&d_bcount, nb + 1), "alloc bucket counts");
+    CK(cudaMallocAsync((void**)&d_boff, (nb + 2) * 4, s), "alloc bucket offsets");
     res->d_boff = d_boff;
-    CK(sc.alloc(&d_cursor, nb), "alloc cursor");
-    CK(sc.alloc(&d_scan, scan_scratch_elems(nb)), "alloc scan scratch");
+    CK(sc.alloc(&d_cursor, nb + 1), "alloc cursor");
+    CK(sc.alloc(&d_scan, scan_scratch_elems(nb + 1)), "alloc scan scratch");
     CK(sc.alloc(&d_bof, n), "alloc bucket_of");
     CK(cudaMallocAsync((void**)&d_dets, n * sizeof(Det), s), "alloc dets");
     res->d_dets = d_dets;
@@ -304,15 +307,15 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     CK(sc.alloc(&d_small, 4), "alloc counters");
     CK(sc.alloc(&d_small64, 4), "alloc counters64");
     CK(cudaMemsetAsync(d_ecount, 0, E * 4, s), "memset");
-    CK(cudaMemsetAsync(d_bcount, 0, nb * 4, s), "memset");
+    CK(cudaMemsetAsync(d_bcount, 0, (nb + 1) * 4, s), "memset");
     CK(cudaMemsetAsync(d_small, 0, 16, s), "memset");
     CK(cudaMemsetAsync(d_small64, 0, 32, s), "memset");
     tr.mark("allocated");
 
     // a1-a3: ingest and validate, bucket, reference epoch, shift tables
     CK(launch_ingest(dx, dy, dep, n, E, cg, d_bcount, d_ecount, d_bof, &d_small[0], s), "ingest");
-    CK(launch_scan_u32(d_bcount, d_boff, nb, d_scan, s), "bucket scan");
-    CK(cudaMemcpyAsync(d_cursor, d_boff, nb * 4, cudaMemcpyDeviceToDevice, s), "cursor");
+    CK(launch_scan_u32(d_bcount, d_boff, nb + 1, d_scan, s), "bucket scan");
+    CK(cudaMemcpyAsync(d_cursor, d_boff, (nb + 1) * 4, cudaMemcpyDeviceToDevice, s), "cursor");
     CK(launch_scatter(dx, dy, dep, n, d_bof, d_cursor, d_dets, s), "scatter");
     CK(launch_epoch_setup(E, d_t, d_ecount, d_dt, d_t0, s), "epoch setup");
     CK(launch_shift_tables(g, d_dt, d_ecount, d_sxt, d_syt, &d_small[0], s), "shift tables");
@@ -449,7 +452,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     if (res->d_ids) cudaFreeAsync(res->d_ids, s);
     if (res->d_cands) cudaFreeAsync(res->d_cands, s);
     for (void* p : {(void*)res->d_dets, (void*)res->d_boff, (void*)res->d_ecount, (void*)res->d_sxt,
-                    (void*)res->d_syt})
+                    (void*)res->d_syt, (void*)res->d_dt})
       if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);
     delete res;
@@ -546,6 +549,84 @@ int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, uint32_
   return SAS_OK;
 }
 
+struct sas_tracks {
+  int device;
+  sas_track* d_tracks;
+  uint32_t* d_ids;
+  uint64_t n, n_ids;
+};
+
+int sas_refine(const sas_result* search, const sas_result* clusters, const sas_refine_opts* opts, void* stream,
+               sas_tracks** out) {
+  if (!search || !clusters || !out) return fail(SAS_ERR_ARG, "null argument");
+  const bool empty = clusters->info.n_candidates == 0;
+  if ((!search->d_dets || !search->d_dt) && !(empty && search->complete))
+    return fail(SAS_ERR_ARG, "`search` must be a search result");
+  if (clusters->n_det != search->n_det)
+    return fail(SAS_ERR_ARG, "clusters come from a catalog of %llu detections, the search has %llu",
+                (unsigned long long)clusters->n_det, (unsigned long long)search->n_det);
+  sas_refine_opts o = opts ? *opts : sas_refine_opts{};
+  if (o.n_starts == 0) o.n_starts = 500;
+  if (o.n_best == 0) o.n_best = 10;
+  if (o.max_csteps == 0) o.max_csteps = 100;
+  if (o.max_iter == 0) o.max_iter = 10;
+  if (o.radius == 0) o.radius = search->g.bin;
+  if (o.n_starts > 4096) return fail(SAS_ERR_ARG, "n_starts %u above 4096", o.n_starts);
+  if (o.radius < 0 || o.radius > (1 << 26)) return fail(SAS_ERR_ARG, "radius %d outside [0, 2^26]", o.radius);
+  o.n_best = std::min(o.n_best, o.n_starts);
+  RefineIn in;
+  in.search.dets = search->d_dets;
+  in.search.boff = search->d_boff;
+  in.search.dt = search->d_dt;
+  in.search.g = search->g;
+  in.search.cg = search->cg;
+  in.search.n_det = search->n_det;
+  in.clusters.cands = clusters->d_cands;
+  in.clusters.n = clusters->info.n_candidates;
+  in.clusters.ids = clusters->d_ids;
+  RefineOut ro;
+  if (!empty)
+    if (int rc = refine_tracks(in, o, (cudaStream_t)stream, &ro)) return rc;
+  sas_tracks* t = new sas_tracks();
+  t->device = search->device;
+  t->d_tracks = ro.tracks;
+  t->d_ids = ro.ids;
+  t->n = ro.n;
+  t->n_ids = ro.n_ids;
+  *out = t;
+  return SAS_OK;
+}
+
+int sas_tracks_get(const sas_tracks* t, sas_track* out, uint64_t cap, uint64_t* n_total, uint32_t* ids,
+                   uint64_t ids_cap, uint64_t* n_ids_total, int on_device) {
+  if (!t) return fail(SAS_ERR_ARG, "null tracks");
+  if (n_total) *n_total = t->n;
+  if (n_ids_total) *n_ids_total = t->n_ids;
+  const uint64_t c1 = std::min(cap, t->n), i1 = std::min(ids_cap, t->n_ids);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c1) {
+    if (!out) return fail(SAS_ERR_ARG, "null track buffer");
+    cudaError_t e = cudaMemcpy(out, t->d_tracks, c1 * sizeof(sas_track), kind);
+    if (e != cudaSuccess) return cuda_fail(e, "copy tracks");
+  }
+  if (i1) {
+    if (!ids) return fail(SAS_ERR_ARG, "null id buffer");
+    cudaError_t e = cudaMemcpy(ids, t->d_ids, i1 * sizeof(uint32_t), kind);
+    if (e != cudaSuccess) return cuda_fail(e, "copy ids");
+  }
+  if (cap < t->n || ids_cap < t->n_ids)
+    return fail(SAS_ERR_OVERFLOW, "buffers too small: need %llu tracks and %llu ids", (unsigned long long)t->n,
+                (unsigned long long)t->n_ids);
+  return SAS_OK;
+}
+
+void sas_tracks_free(sas_tracks* t) {
+  if (!t) return;
+  if (t->d_tracks) cudaFree(t->d_tracks);
+  if (t->d_ids) cudaFree(t->d_ids);
+  delete t;
+}
+
 int sas_owned(const sas_result* r, uint32_t n_keep, uint32_t* idx, uint64_t* n_kept, void* stream) {
   if (!r || !n_kept) return fail(SAS_ERR_ARG, "null argument");
   if (r->info.n_candidates && !idx) return fail(SAS_ERR_ARG, "null index buffer");
@@ -561,7 +642,7 @@ int sas_peaks(const sas_result* r, uint32_t* idx, uint64_t* n_peaks, void* strea
 void sas_result_free(sas_result* r) {
   if (!r) return;
   for (void* p : {(void*)r->d_cands, (void*)r->d_ids, (void*)r->d_dets, (void*)r->d_boff,
-                  (void*)r->d_ecount, (void*)r->d_sxt, (void*)r->d_syt})
+                  (void*)r->d_ecount, (void*)r->d_sxt, (void*)r->d_syt, (void*)r->d_dt})
     if (p) cudaFree(p);
   delete r;
 }

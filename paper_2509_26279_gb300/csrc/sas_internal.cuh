@@ -251,6 +251,29 @@ struct PeelOut {
 int peel_clusters(const CandView& v, uint32_t n_min, uint32_t max_clusters, bool sequential, cudaStream_t s,
                   PeelOut* out);
 
+// sas_refine.cu: refinement and gathering (Sec. 2.1 steps 4-6).
+struct RefineIn {
+  struct {
+    const Det* dets;       // bucketed catalog, overflow bucket last
+    const uint32_t* boff;  // [nb + 2]
+    const int64_t* dt;     // [E] epoch time - t0, ticks
+    SearchGeom g;
+    CoarseGeom cg;
+    uint64_t n_det;
+  } search;
+  struct {
+    const sas_candidate* cands;
+    uint64_t n;
+    const uint32_t* ids;
+  } clusters;
+};
+struct RefineOut {
+  sas_track* tracks = nullptr;
+  uint32_t* ids = nullptr;
+  uint32_t n = 0, n_ids = 0;
+};
+int refine_tracks(const RefineIn& in, const sas_refine_opts& o, cudaStream_t s, RefineOut* out);
+
 // sas_api.cu: the candidate view of a finished search.
 CandView result_view(const sas_result* r);
 

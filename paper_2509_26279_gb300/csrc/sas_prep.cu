@@ -38,8 +38,10 @@ __global__ void k_ingest(const int32_t* __restrict__ x, const int32_t* __restric
         const int64_t cy = floor_div64((int64_t)yi - cg.gy0, cg.cell);
         if (cx >= 0 && cx < cg.ncx && cy >= 0 && cy < cg.ncy) {
           b = (uint32_t)(((uint64_t)e * cg.ncy + (uint64_t)cy) * cg.ncx + (uint64_t)cx);
-          atomicAdd(&bucket_count[b], 1u);
+        } else {
+          b = (uint32_t)((uint64_t)E * cg.ncy * cg.ncx);  // overflow bucket: outside the grid
         }
+        atomicAdd(&bucket_count[b], 1u);
       }
     }
     bucket_of[i] = b;

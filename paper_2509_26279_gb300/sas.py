@@ -479,6 +479,69 @@ def sas_peel(result: Result, n_min: int, max_clusters: int = 1000, stream=None, 
     return Result(h)
 
 
+TRACK_DTYPE = np.dtype([("vx", "<f8"), ("vy", "<f8"), ("x0", "<f8"), ("y0", "<f8"), ("res_xx", "<f8"),
+                        ("res_xy", "<f8"), ("res_yy", "<f8"), ("det", "<f8"), ("status", "<u4"),
+                        ("iterations", "<u4"), ("h", "<u4"), ("n_points", "<u4"), ("id_off", "<u8"),
+                        ("id_len", "<u4"), ("cluster", "<u4")])
+assert TRACK_DTYPE.itemsize == 96
+TRACK_CONVERGED, TRACK_MAX_ITER, TRACK_DEGENERATE, TRACK_TOO_MANY = 0, 1, 2, 3
+REFINE_MAX_POINTS = 1024
+
+
+class sas_refine_opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_starts", ctypes.c_uint32), ("n_best", ctypes.c_uint32),
+                ("max_csteps", ctypes.c_uint32), ("max_iter", ctypes.c_uint32), ("radius", ctypes.c_int32),
+                ("reserved", ctypes.c_uint32)]
+
+
+_lib.sas_refine.argtypes = [_p, _p, ctypes.POINTER(sas_refine_opts), _p, ctypes.POINTER(_p)]
+_lib.sas_tracks_get.argtypes = [_p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p, ctypes.c_uint64,
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+_lib.sas_tracks_free.argtypes = [_p]
+_lib.sas_tracks_free.restype = None
+EXPORTED += ["sas_refine", "sas_tracks_get", "sas_tracks_free"]
+
+
+class Tracks:
+    """Refined trajectories (sas_tracks); owns device memory until freed."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def tracks(self):
+        """(tracks: structured array of TRACK_DTYPE, ids: uint32 array)."""
+        nt, ni = ctypes.c_uint64(), ctypes.c_uint64()
+        _lib.sas_tracks_get(self._h, None, 0, ctypes.byref(nt), None, 0, ctypes.byref(ni), 0)
+        tr = np.zeros(nt.value, TRACK_DTYPE)
+        ids = np.zeros(ni.value, np.uint32)
+        _check(_lib.sas_tracks_get(self._h, tr.ctypes.data if nt.value else None, nt.value, ctypes.byref(nt),
+                                   ids.ctypes.data if ni.value else None, ni.value, ctypes.byref(ni), 0))
+        return tr, ids
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.sas_tracks_free(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sas_refine(search: Result, clusters: Result | None = None, seed: int = 0, n_starts: int = 0, n_best: int = 0,
+               max_csteps: int = 0, max_iter: int = 0, radius: int = 0, stream=None) -> Tracks:
+    """Refinement and gathering (Sec. 2.1 steps 4-6) of every cluster of
+    `clusters` (default: the search's own candidates); zeros take the
+    library's defaults."""
+    o = sas_refine_opts(seed & ((1 << 64) - 1), n_starts, n_best, max_csteps, max_iter, radius, 0)
+    h = _p()
+    _check(_lib.sas_refine(search._h, (clusters or search)._h, ctypes.byref(o), _stream_handle(stream),
+                           ctypes.byref(h)))
+    return Tracks(h)
+
+
 def _opt_ptr(a):
     return None if a is None else _dev_ptr(a)
 
