@@ -106,7 +106,7 @@ struct Pts {
 };
 
 // Exact moments of the subset (bits: lane's membership word), then S, adj, det.
-__device__ WFit wfit(const Pts& p, uint32_t bits, int lane) {
+__device__ __noinline__ WFit wfit(const Pts& p, uint32_t bits, int lane) {
   int64_t T = 0, X = 0, Y = 0;
   __int128 tt = 0, tx = 0, ty = 0, xx = 0, xy = 0, yy = 0;
   for (uint32_t c = 0; c < p.nc; ++c) {
@@ -166,7 +166,9 @@ __device__ __forceinline__ uint64_t order_key(double q) {
 }
 
 // C-step: the h points of smallest (q, index) under the fit's (mean, adj).
-__device__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h, uint64_t* keys, int lane) {
+// Up to 256 points: each point's rank is counted against every key (no
+// dependent reductions); more: the h-th smallest key by binary descent.
+__device__ __noinline__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h, uint64_t* keys, int lane) {
   const int64_t m = f.m;
   for (uint32_t c = 0; c < p.nc; ++c) {
     const uint32_t i = c * 32 + lane;
@@ -180,7 +182,32 @@ __device__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h, uint64_t* k
     keys[i] = order_key(add(add(mul(u0, w0), mul(u1, w1)), mul(u2, w2)));
   }
   __syncwarp();
-  // the h-th smallest key K, by binary descent on its bits
+  uint32_t bits = 0;
+  if (p.n <= 256) {
+    uint64_t mine[8];
+    uint32_t rank[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t i = c * 32 + lane;
+      mine[c] = (c < (int)p.nc && i < p.n) ? keys[i] : ~0ull;
+      rank[c] = 0;
+    }
+    for (uint32_t j = 0; j < p.n; ++j) {
+      const uint64_t kj = keys[j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t i = c * 32 + lane;
+        rank[c] += (kj < mine[c] || (kj == mine[c] && j < i)) ? 1u : 0u;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t i = c * 32 + lane;
+      if (c < (int)p.nc && i < p.n && rank[c] < h) bits |= 1u << c;
+    }
+    __syncwarp();
+    return bits;
+  }
   uint64_t K = 0;
   for (int b = 63; b >= 0; --b) {
     const uint64_t test = K | (1ull << b);
@@ -198,7 +225,6 @@ __device__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h, uint64_t* k
     if (i < p.n) below += keys[i] < K;
   }
   int32_t need = (int32_t)h - (int32_t)__reduce_add_sync(0xffffffffu, below);
-  uint32_t bits = 0;
   for (uint32_t c = 0; c < p.nc; ++c) {
     const uint32_t i = c * 32 + lane;
     const uint64_t k = i < p.n ? keys[i] : ~0ull;
@@ -219,8 +245,8 @@ struct StartOut {
 
 // One FAST-MCD start: draws while singular (up to h points), the h nearest,
 // then C-steps while det decreases (at most max_steps).
-__device__ StartOut run_start(const Pts& p, uint32_t h, uint64_t key, uint32_t max_steps, uint64_t* keys,
-                              uint16_t* perm, int lane) {
+__device__ __noinline__ StartOut run_start(const Pts& p, uint32_t h, uint64_t key, uint32_t max_steps,
+                                           uint64_t* keys, uint16_t* perm, int lane) {
   for (uint32_t i = lane; i < p.n; i += 32) perm[i] = (uint16_t)i;
   __syncwarp();
   uint32_t bits = 0, j = 0;
@@ -250,6 +276,7 @@ __device__ StartOut run_start(const Pts& p, uint32_t h, uint64_t key, uint32_t m
   for (uint32_t step = 0; step < max_steps; ++step) {
     if (f.det <= 0.0) break;
     const uint32_t b2 = wselect(p, f, h, keys, lane);
+    if (__all_sync(0xffffffffu, b2 == bits)) break;  // same subset: same det, no decrease
     const WFit f2 = wfit(p, b2, lane);
     if (!(f2.det < f.det)) break;
     bits = b2;
@@ -262,112 +289,151 @@ __device__ __forceinline__ bool det_before(double da, uint32_t sa, double db, ui
   return da < db || (da == db && sa < sb);
 }
 
+struct BestOut {
+  double det;
+  uint32_t s;
+  uint32_t bits[32];
+  uint32_t pad;
+};
+
 struct FitArgs {
   const Det* pt;        // [n_det] by detection id (x, y, e)
   const int64_t* dt;    // [E] epoch time - t0, ticks
   const uint32_t* P;    // [k][cap] current point ids
   const uint32_t* Pn;
-  uint32_t cap, n_clusters, iter;
+  uint32_t cap, iter;
   uint64_t seed;
   uint32_t n_starts, n_best, max_csteps, npad;
+  double* det3;         // [k][n_starts] det after the first two C-steps
+  BestOut* best;        // [k][n_best]
   sas_track* tracks;
   uint32_t* status;
 };
 
-// Step 4 for every running cluster (one block each).
-__global__ void __launch_bounds__(kFitThreads) k_fit(FitArgs a) {
+// Shared layout of the fit kernels: points, then per-warp keys and shuffles.
+struct FitSmem {
+  int64_t* t;
+  int32_t* x;
+  int32_t* y;
+  uint64_t* keys;
+  uint16_t* perm;
+  uint32_t* best;  // n_best selected starts
+};
+
+__device__ FitSmem carve(unsigned char* smem, uint32_t npad, uint32_t n_best) {
+  FitSmem m;
+  m.t = (int64_t*)smem;
+  m.keys = (uint64_t*)(m.t + npad);
+  m.x = (int32_t*)(m.keys + (size_t)kFitWarps * npad);
+  m.y = m.x + npad;
+  m.best = (uint32_t*)(m.y + npad);
+  m.perm = (uint16_t*)(m.best + n_best);
+  return m;
+}
+
+__device__ uint32_t load_points(const FitArgs& a, uint32_t k, const FitSmem& m, int tid, int nthreads) {
+  const uint32_t n = a.Pn[k];
+  for (uint32_t i = tid; i < n; i += nthreads) {
+    const Det d = a.pt[a.P[(size_t)k * a.cap + i]];
+    m.t[i] = a.dt[d.e];
+    m.x[i] = d.x;
+    m.y[i] = d.y;
+  }
+  return n;
+}
+
+// Phase 1: every start takes two C-steps; blockIdx.x splits a cluster's starts.
+__global__ void __launch_bounds__(kFitThreads) k_fit_starts(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t k = blockIdx.y;
+  if (a.status[k] != kRunning) return;
+  if (a.Pn[k] < (uint32_t)kDim + 2) return;
+  const FitSmem m = carve(smem, a.npad, a.n_best);
+  const uint32_t n = load_points(a, k, m, threadIdx.x, kFitThreads);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const Pts p{m.t, m.x, m.y, n, (n + 31) / 32};
+  const uint32_t h = (n + kDim + 1) / 2;
+  const uint32_t stride = gridDim.x * kFitWarps;
+  for (uint32_t s = blockIdx.x * kFitWarps + warp; s < a.n_starts; s += stride) {
+    const StartOut o = run_start(p, h, start_key(a.seed, k, a.iter, s), 2, m.keys + (size_t)warp * a.npad,
+                                 m.perm + (size_t)warp * a.npad, lane);
+    if (lane == 0) a.det3[(size_t)k * a.n_starts + s] = o.det;
+  }
+}
+
+// Phase 2: the n_best lowest (det, start) continue for up to max_csteps.
+__global__ void __launch_bounds__(kFitThreads) k_fit_best(FitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t k = blockIdx.y;
+  if (a.status[k] != kRunning) return;
+  if (a.Pn[k] < (uint32_t)kDim + 2) return;
+  const FitSmem m = carve(smem, a.npad, a.n_best);
+  const uint32_t n = load_points(a, k, m, threadIdx.x, kFitThreads);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* det3 = a.det3 + (size_t)k * a.n_starts;
+  if (warp == 0) {  // the n_best lowest (det, start), in order
+    for (uint32_t b = 0; b < a.n_best; ++b) {
+      double bd = 0.0;
+      uint32_t bs = 0xFFFFFFFFu;
+      for (uint32_t s = lane; s < a.n_starts; s += 32) {
+        const double d = det3[s];
+        bool taken = false;
+        for (uint32_t q = 0; q < b; ++q) taken |= m.best[q] == s;
+        if (!taken && (bs == 0xFFFFFFFFu || det_before(d, s, bd, bs))) {
+          bd = d;
+          bs = s;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+        const uint32_t os = __shfl_xor_sync(0xffffffffu, bs, o);
+        if (os != 0xFFFFFFFFu && (bs == 0xFFFFFFFFu || det_before(od, os, bd, bs))) {
+          bd = od;
+          bs = os;
+        }
+      }
+      if (lane == 0) m.best[b] = bs;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const Pts p{m.t, m.x, m.y, n, (n + 31) / 32};
+  const uint32_t h = (n + kDim + 1) / 2;
+  const uint32_t b = blockIdx.x * kFitWarps + warp;
+  if (b >= a.n_best) return;
+  const uint32_t s = m.best[b];
+  const StartOut o = run_start(p, h, start_key(a.seed, k, a.iter, s), a.max_csteps, m.keys + (size_t)warp * a.npad,
+                               m.perm + (size_t)warp * a.npad, lane);
+  BestOut& r = a.best[(size_t)k * a.n_best + b];
+  r.bits[lane] = o.bits;
+  if (lane == 0) {
+    r.det = o.det;
+    r.s = s;
+  }
+}
+
+// Phase 3 (one warp per cluster): the winning subset and its line.
+__global__ void __launch_bounds__(32) k_fit_final(FitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t k = blockIdx.x;
   if (a.status[k] != kRunning) return;
-  const uint32_t n = a.Pn[k];
-  const uint32_t npad = a.npad;
-  // 8-byte arrays first, then 4-byte, then 2-byte (layout of refine_fit_smem)
-  int64_t* s_t = (int64_t*)smem;                           // [npad]
-  uint64_t* s_keys = (uint64_t*)(s_t + npad);              // [kFitWarps][npad]
-  double* s_det = (double*)(s_keys + (size_t)kFitWarps * npad);  // [n_starts]
-  double* s_wdet = s_det + a.n_starts;                     // [kFitWarps]
-  uint32_t* s_best = (uint32_t*)(s_wdet + kFitWarps);      // [n_best]
-  uint32_t* s_wbits = s_best + a.n_best;                   // [kFitWarps][32]
-  uint32_t* s_ws = s_wbits + kFitWarps * 32;               // [kFitWarps]
-  int32_t* s_x = (int32_t*)(s_ws + kFitWarps);             // [npad]
-  int32_t* s_y = s_x + npad;                               // [npad]
-  uint16_t* s_perm = (uint16_t*)(s_y + npad);              // [kFitWarps][npad]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t i = threadIdx.x; i < n; i += kFitThreads) {
-    const Det d = a.pt[a.P[(size_t)k * a.cap + i]];
-    s_t[i] = a.dt[d.e];
-    s_x[i] = d.x;
-    s_y[i] = d.y;
-  }
-  __syncthreads();
-  const Pts p{s_t, s_x, s_y, n, (n + 31) / 32};
-  uint64_t* keys = s_keys + (size_t)warp * npad;
-  uint16_t* perm = s_perm + (size_t)warp * npad;
-  uint32_t final_bits = 0;
+  const FitSmem m = carve(smem, a.npad, 0);
+  const uint32_t n = load_points(a, k, m, threadIdx.x, 32);
+  __syncwarp();
+  const int lane = threadIdx.x;
+  const Pts p{m.t, m.x, m.y, n, (n + 31) / 32};
+  uint32_t bits;
   if (n < (uint32_t)kDim + 2) {
-    final_bits = lane < (int)n ? 1u : 0u;  // n < 32: every point, one chunk
+    bits = lane < (int)n ? 1u : 0u;  // n < 32: every point, one chunk
   } else {
-    const uint32_t h = (n + kDim + 1) / 2;
-    for (uint32_t s = warp; s < a.n_starts; s += kFitWarps) {
-      const StartOut o = run_start(p, h, start_key(a.seed, k, a.iter, s), 2, keys, perm, lane);
-      if (lane == 0) s_det[s] = o.det;
-    }
-    __syncthreads();
-    const uint32_t nb = min(a.n_best, a.n_starts);
-    if (warp == 0) {  // the nb lowest (det, start), in order
-      for (uint32_t b = 0; b < nb; ++b) {
-        double bd = 0.0;
-        uint32_t bs = 0xFFFFFFFFu;
-        for (uint32_t s = lane; s < a.n_starts; s += 32) {
-          const double d = s_det[s];
-          bool taken = false;
-          for (uint32_t q = 0; q < b; ++q) taken |= s_best[q] == s;
-          if (!taken && (bs == 0xFFFFFFFFu || det_before(d, s, bd, bs))) {
-            bd = d;
-            bs = s;
-          }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-          const uint32_t os = __shfl_xor_sync(0xffffffffu, bs, o);
-          if (os != 0xFFFFFFFFu && (bs == 0xFFFFFFFFu || det_before(od, os, bd, bs))) {
-            bd = od;
-            bs = os;
-          }
-        }
-        if (lane == 0) s_best[b] = bs;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    double wd = 0.0;
-    uint32_t ws = 0xFFFFFFFFu, wbits = 0;
-    for (uint32_t b = warp; b < nb; b += kFitWarps) {
-      const uint32_t s = s_best[b];
-      const StartOut o = run_start(p, h, start_key(a.seed, k, a.iter, s), a.max_csteps, keys, perm, lane);
-      if (ws == 0xFFFFFFFFu || det_before(o.det, s, wd, ws)) {
-        wd = o.det;
-        ws = s;
-        wbits = o.bits;
-      }
-    }
-    s_wbits[warp * 32 + lane] = wbits;
-    if (lane == 0) {
-      s_wdet[warp] = wd;
-      s_ws[warp] = ws;
-    }
-    __syncthreads();
-    if (warp != 0) return;
-    int bw = -1;
-    for (int w = 0; w < kFitWarps; ++w) {
-      if (s_ws[w] == 0xFFFFFFFFu) continue;
-      if (bw < 0 || det_before(s_wdet[w], s_ws[w], s_wdet[bw], s_ws[bw])) bw = w;
-    }
-    final_bits = s_wbits[bw * 32 + lane];
+    const BestOut* bo = a.best + (size_t)k * a.n_best;
+    uint32_t w = 0;
+    for (uint32_t b = 1; b < a.n_best; ++b)
+      if (det_before(bo[b].det, bo[b].s, bo[w].det, bo[w].s)) w = b;
+    bits = bo[w].bits[lane];
   }
-  if (warp != 0) return;
-  // the line of the final subset (warp 0)
-  const WFit f = wfit(p, final_bits, lane);
+  const WFit f = wfit(p, bits, lane);
   if (lane != 0) return;
   sas_track& tr = a.tracks[k];
   tr.iterations = a.iter + 1;
@@ -557,9 +623,8 @@ unsigned nblocks(uint64_t n, unsigned per) { return (unsigned)std::max<uint64_t>
 
 }  // namespace
 
-size_t refine_fit_smem(uint32_t npad, uint32_t n_starts, uint32_t n_best) {
-  return (size_t)npad * 8 + (size_t)kFitWarps * npad * 8 + (size_t)n_starts * 8 + kFitWarps * 8 +
-         (size_t)n_best * 4 + kFitWarps * 32 * 4 + kFitWarps * 4 + (size_t)npad * 8 +
+size_t refine_fit_smem(uint32_t npad, uint32_t n_best) {
+  return (size_t)npad * 8 + (size_t)kFitWarps * npad * 8 + (size_t)npad * 8 + (size_t)n_best * 4 +
          (size_t)kFitWarps * npad * 2;
 }
 
@@ -581,7 +646,11 @@ int refine_tracks(const RefineIn& in, const sas_refine_opts& o, cudaStream_t s, 
            *len = nullptr, *off = nullptr, *scr = nullptr;
   sas_track* tracks = nullptr;
   uint32_t* out_ids = nullptr;
+  double* det3 = nullptr;
+  BestOut* best = nullptr;
   cudaError_t e = get(&pt, nd * sizeof(Det));
+  if (e == cudaSuccess) e = get(&det3, (uint64_t)nc * o.n_starts * 8);
+  if (e == cudaSuccess) e = get(&best, (uint64_t)nc * o.n_best * sizeof(BestOut));
   if (e == cudaSuccess) e = get(&P, (uint64_t)nc * cap * 4);
   if (e == cudaSuccess) e = get(&G, (uint64_t)nc * cap * 4);
   if (e == cudaSuccess) e = get(&Pn, nc * 4ull);
@@ -612,24 +681,33 @@ int refine_tracks(const RefineIn& in, const sas_refine_opts& o, cudaStream_t s, 
     fa.P = P;
     fa.Pn = Pn;
     fa.cap = cap;
-    fa.n_clusters = nc;
     fa.iter = it;
     fa.seed = o.seed;
     fa.n_starts = o.n_starts;
     fa.n_best = o.n_best;
     fa.max_csteps = o.max_csteps;
     fa.npad = std::max<uint32_t>(32, (max_n + 31) / 32 * 32);
+    fa.det3 = det3;
+    fa.best = best;
     fa.tracks = tracks;
     fa.status = status;
-    const size_t smem = refine_fit_smem(fa.npad, o.n_starts, o.n_best);
-    e = cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = refine_fit_smem(fa.npad, o.n_best);
+    // split each cluster's starts over enough blocks to fill the GPU twice
+    const uint32_t split = std::max<uint32_t>(
+        1, std::min<uint32_t>((o.n_starts + kFitWarps - 1) / kFitWarps, (4 * 152 + running - 1) / running));
+    e = cudaFuncSetAttribute(k_fit_starts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_best, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fit_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) break;
-    k_fit<<<nc, kFitThreads, smem, s>>>(fa);
+    k_fit_starts<<<dim3(split, nc), kFitThreads, smem, s>>>(fa);
+    k_fit_best<<<dim3((o.n_best + kFitWarps - 1) / kFitWarps, nc), kFitThreads, smem, s>>>(fa);
+    k_fit_final<<<nc, 32, smem, s>>>(fa);
+    note_launch(3);
     k_gather<<<dim3((in.search.g.E + 1 + 3) / 4, nc), 128, 0, s>>>(tracks, status, in.search.dets, in.search.boff,
                                                                    in.search.dt, in.search.g, in.search.cg, o.radius,
                                                                    cap, G, Gn);
     k_settle<<<nc, 512, 0, s>>>(status, tracks, P, Pn, G, Gn, cap, it, o.max_iter);
-    note_launch(3);
+    note_launch(2);
     if ((e = cudaMemsetAsync(ctl, 0, 8, s)) != cudaSuccess) break;
     k_refine_count<<<nblocks(nc, 256), 256, 0, s>>>(status, Pn, nc, ctl);
     note_launch();
