@@ -440,6 +440,50 @@ int sas_tracks_get(const sas_tracks* tracks, sas_track* out, uint64_t cap, uint6
                    uint64_t ids_cap, uint64_t* n_ids_total, int on_device);
 void sas_tracks_free(sas_tracks* tracks);
 
+/* ---- Search parameters (Sec. 2.2) ------------------------------------------
+ *
+ * Host functions (no device): the relations the paper uses to choose the bin
+ * size dx and the threshold N_min.  Lengths in one unit throughout (pixels or
+ * arcsec), times in hours, velocities in length per hour, omega in length^2.
+ * Each returns SAS_OK and writes its result, or SAS_ERR_ARG for a null output
+ * or an argument outside its domain (non-positive dx, dt, a; negative rate).
+ *
+ * velocity_count: |V| = ((vmax_x - vmin_x) / dv)((vmax_y - vmin_y) / dv) with
+ *   dv = dx / dt (Eq. v_size).
+ * n_stacks: |V| omega / dx^2 (Eq. N_stacks).
+ * peak_density(z, a): noise peaks per unit area per unit detection statistic
+ *   for white noise under a Gaussian window of width a -- the Kac-Rice density
+ *   of maxima of that Gaussian field (the paper's printed closed form is
+ *   garbled; this is the quantity it stands for).  Integrates over z to
+ *   1 / (4 sqrt(3) pi a^2).
+ * peaks_above(nu_th, a): its integral above nu_th (Eq. n_pk_above).
+ * noise_rate: Lambda = sum over epochs of peaks_above(nu_th, 1) (dx / a_i)^2,
+ *   the mean noise count of a square bin of side dx.
+ * poisson_sf: P(N >= k), N ~ Pois(lambda).
+ * choose_n_min: the smallest N_min with P(N_noise >= N_min) <= eps.
+ * p_signal: one epoch's probability that a source of S/N nu is detected above
+ *   nu_th and falls in the bin of side dx centred on it:
+ *   erfc((nu_th - nu) / sqrt 2) / 2 * erf(dx nu / (4 a))^2.
+ * signal_tail: P(N_signal >= k) for independent epochs with probabilities p.
+ * dx_scan: for each dx[j]: E[N_signal], E[N_noise] and the N_min that the
+ *   budget eps = n_false / N_stacks requires, N_stacks from |V| = (dt dv / dx)^2
+ *   (equal axis ranges dv) and the area omega.  An object is recoverable where
+ *   E[N_signal] > E[N_noise] and E[N_signal] + E[N_noise] >= N_min.
+ */
+int sas_param_velocity_count(double vmin_x, double vmax_x, double vmin_y, double vmax_y, double dx, double dt,
+                             double* out);
+int sas_param_n_stacks(double n_velocities, double omega, double dx, double* out);
+int sas_param_peak_density(double z, double a, double* out);
+int sas_param_peaks_above(double nu_th, double a, double* out);
+int sas_param_noise_rate(double nu_th, const double* a, uint32_t n_epochs, double dx, double* out);
+int sas_param_poisson_sf(uint32_t k, double lambda, double* out);
+int sas_param_choose_n_min(double lambda, double eps, uint32_t* out);
+int sas_param_p_signal(double nu, double nu_th, double a, double dx, double* out);
+int sas_param_signal_tail(const double* p, uint32_t n, uint32_t k, double* out);
+int sas_param_dx_scan(double nu, double nu_th, const double* a, uint32_t n_epochs, const double* dx, uint32_t n_dx,
+                      double dv, double dt, double omega, double n_false, double* e_signal, double* e_noise,
+                      uint32_t* n_min);
+
 /* The network (input = count / 16):
  *   conv1 9 -> 32 channels, 3x3 valid (15 -> 13), ReLU; conv2 32 -> 32 (13 -> 11),
  *   ReLU; conv3 32 -> 32 (11 -> 9), ReLU; flatten in (channel, row, column)

@@ -91,7 +91,7 @@ def poisson_sf(k, lam):
         while True:
             t = math.exp(logpmf(j))
             total += t
-            if t < total * 1e-17 and j > lam:
+            if t == 0.0 or (t < total * 1e-17 and j > lam):   # terms only shrink past lam
                 break
             j += 1
         return total

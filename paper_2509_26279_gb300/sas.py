@@ -542,6 +542,85 @@ def sas_refine(search: Result, clusters: Result | None = None, seed: int = 0, n_
     return Tracks(h)
 
 
+# ---- search parameters (Sec. 2.2): host functions of the library ----------
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_lib.sas_param_velocity_count.argtypes = [_D] * 6 + [_PD]
+_lib.sas_param_n_stacks.argtypes = [_D] * 3 + [_PD]
+_lib.sas_param_peak_density.argtypes = [_D, _D, _PD]
+_lib.sas_param_peaks_above.argtypes = [_D, _D, _PD]
+_lib.sas_param_noise_rate.argtypes = [_D, _p, ctypes.c_uint32, _D, _PD]
+_lib.sas_param_poisson_sf.argtypes = [ctypes.c_uint32, _D, _PD]
+_lib.sas_param_choose_n_min.argtypes = [_D, _D, ctypes.POINTER(ctypes.c_uint32)]
+_lib.sas_param_p_signal.argtypes = [_D] * 4 + [_PD]
+_lib.sas_param_signal_tail.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, _PD]
+_lib.sas_param_dx_scan.argtypes = [_D, _D, _p, ctypes.c_uint32, _p, ctypes.c_uint32, _D, _D, _D, _D, _p, _p, _p]
+EXPORTED += ["sas_param_velocity_count", "sas_param_n_stacks", "sas_param_peak_density", "sas_param_peaks_above",
+             "sas_param_noise_rate", "sas_param_poisson_sf", "sas_param_choose_n_min", "sas_param_p_signal",
+             "sas_param_signal_tail", "sas_param_dx_scan"]
+
+
+def _d_call(fn, *args) -> float:
+    out = ctypes.c_double()
+    _check(fn(*args, ctypes.byref(out)))
+    return out.value
+
+
+class params:
+    """sas_param_*: the parameter relations of Sec. 2.2 (host computation)."""
+
+    @staticmethod
+    def velocity_count(vmin_x, vmax_x, vmin_y, vmax_y, dx, dt) -> float:
+        return _d_call(_lib.sas_param_velocity_count, vmin_x, vmax_x, vmin_y, vmax_y, dx, dt)
+
+    @staticmethod
+    def n_stacks(n_velocities, omega, dx) -> float:
+        return _d_call(_lib.sas_param_n_stacks, n_velocities, omega, dx)
+
+    @staticmethod
+    def peak_density(z, a=1.0) -> float:
+        return _d_call(_lib.sas_param_peak_density, z, a)
+
+    @staticmethod
+    def peaks_above(nu_th, a=1.0) -> float:
+        return _d_call(_lib.sas_param_peaks_above, nu_th, a)
+
+    @staticmethod
+    def noise_rate(nu_th, a_list, dx) -> float:
+        a = np.ascontiguousarray(a_list, np.float64)
+        return _d_call(_lib.sas_param_noise_rate, nu_th, a.ctypes.data if len(a) else None, len(a), dx)
+
+    @staticmethod
+    def poisson_sf(k, lam) -> float:
+        return _d_call(_lib.sas_param_poisson_sf, int(k), lam)
+
+    @staticmethod
+    def choose_n_min(lam, eps) -> int:
+        out = ctypes.c_uint32()
+        _check(_lib.sas_param_choose_n_min(lam, eps, ctypes.byref(out)))
+        return out.value
+
+    @staticmethod
+    def p_signal(nu, nu_th, a, dx) -> float:
+        return _d_call(_lib.sas_param_p_signal, nu, nu_th, a, dx)
+
+    @staticmethod
+    def signal_tail(p_list, k) -> float:
+        p = np.ascontiguousarray(p_list, np.float64)
+        return _d_call(_lib.sas_param_signal_tail, p.ctypes.data if len(p) else None, len(p), int(k))
+
+    @staticmethod
+    def dx_scan(nu, nu_th, a_list, dx_list, dv, dt, omega, n_false):
+        a = np.ascontiguousarray(a_list, np.float64)
+        dx = np.ascontiguousarray(dx_list, np.float64)
+        es, en = np.zeros(len(dx)), np.zeros(len(dx))
+        nm = np.zeros(len(dx), np.uint32)
+        _check(_lib.sas_param_dx_scan(nu, nu_th, a.ctypes.data if len(a) else None, len(a),
+                                      dx.ctypes.data if len(dx) else None, len(dx), dv, dt, omega, n_false,
+                                      es.ctypes.data, en.ctypes.data, nm.ctypes.data))
+        return [(float(d), float(s), float(n), int(m)) for d, s, n, m in zip(dx, es, en, nm)]
+
+
 def _opt_ptr(a):
     return None if a is None else _dev_ptr(a)
 

@@ -57,6 +57,7 @@ def test_poisson_tail_against_scipy(lam):
     for k in range(0, int(lam * 2 + 30), 3):
         want = stats.poisson.sf(k - 1, lam) if lam > 0 else float(k <= 0)
         assert P.poisson_sf(k, lam) == pytest.approx(want, rel=1e-9, abs=1e-300)
+    assert P.poisson_sf(2000, lam) == pytest.approx(stats.poisson.sf(1999, lam), abs=1e-300)   # underflowing tail
     if lam > 0:
         for eps in (1e-3, 1e-9):
             n = P.choose_n_min(lam, eps)
