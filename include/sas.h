@@ -169,6 +169,20 @@ int sas_create_grid(const sas_grid_desc* desc, sas_grid** out);
 void sas_destroy_grid(sas_grid* grid);
 int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc);
 
+/* Weighted stacking -- the likelihood accumulation the paper proposes for
+ * future work (Sec. 4): detection i carries an integer weight w[i] in
+ * [0, 255] (a fixed-point likelihood or S/N; uint8, in host or device memory
+ * like the catalog arrays, indexed like them).  A cell's score is the sum over
+ * epochs of the largest weight among that epoch's detections in the cell
+ * (all weights 1: the distinct-epoch count); candidates are the cells with
+ * score >= s_min, in the order (score desc, raw desc, v_idx, by, bx), and
+ * sas_candidate.count holds the score.  Everything else as sas_stack; the
+ * result supports sas_candidates, sas_stamps and sas_refine (not sas_peel,
+ * whose recounts are distinct epochs).  s_min in [1, 2^31].
+ * Errors: as sas_stack; SAS_ERR_ARG for null weights with n > 0. */
+int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weights, uint32_t s_min,
+                       const sas_opts* opts, void* stream, sas_result** out);
+
 /* Run the search (Sec. 2.1 steps 1-3) on the current CUDA device.
  * grid, cat: see above.  n_min >= 1.  opts may be NULL.  stream: a
  * cudaStream_t (NULL = legacy default).  On success *out holds a new result

@@ -39,8 +39,9 @@ struct sas_result {
   SearchGeom g;
   CoarseGeom cg;
   uint64_t n_det;     // catalog size (detection ids are < n_det)
-  uint32_t n_min;     // the search's threshold
+  uint32_t n_min;     // the search's threshold (the score threshold when weighted)
   int complete;       // every cell >= n_min is in the list (no top-K cut)
+  int weighted;       // counts are weighted scores
 };
 
 namespace {
@@ -167,8 +168,13 @@ int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc) {
   return SAS_OK;
 }
 
-int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* opts,
-              void* stream, sas_result** out) {
+namespace {
+
+// The search (Sec. 2.1 steps 1-3); with weights (one uint8 per detection, in
+// host or device memory like the catalog) cells are scored by the sum over
+// epochs of their largest weight and n_min is the score threshold.
+int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weights, uint32_t n_min,
+               const sas_opts* opts, void* stream, sas_result** out) {
   if (!grid || !cat || !out) return fail(SAS_ERR_ARG, "null argument");
   const Tracer tr;
   const sas_grid_desc& d = grid->d;
@@ -216,6 +222,25 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     return SAS_OK;
   }
 
+  res->weighted = weights != nullptr;
+  if (weights && o.superbin == 0) {
+    // the super-bin heuristic models unit increments: give it the distinct-epoch
+    // count that a score of n_min needs at the largest weight
+    uint32_t wmax = 0;
+    if (cat->on_device) {
+      std::vector<uint8_t> hw(n);
+      ce = cudaMemcpy(hw.data(), weights, n, cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess) {
+        delete res;
+        return cuda_fail(ce, "copy weights");
+      }
+      for (uint8_t v : hw) wmax = std::max<uint32_t>(wmax, v);
+    } else {
+      for (uint64_t i = 0; i < n; ++i) wmax = std::max<uint32_t>(wmax, weights[i]);
+    }
+    o.superbin = (uint32_t)choose_superbin(d, n, (n_min + std::max(wmax, 1u) - 1) / std::max(wmax, 1u), v_end - v_begin);
+  }
+
   FieldPlan plan;
   if (int rc = plan_field(d, n, E, cat->t, tph, n_min, v_begin, v_end, o, di, &plan)) {
     delete res;
@@ -252,6 +277,8 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
     int32_t *hx = nullptr, *hy = nullptr;
     uint16_t* hep = nullptr;
     int64_t *d_t = nullptr, *d_dt = nullptr, *d_t0 = nullptr;  // d_dt is kept by the result
+    const uint8_t* d_w = nullptr;
+    uint8_t* hw_dev = nullptr;
     uint32_t *d_ecount = nullptr, *d_bcount = nullptr, *d_boff = nullptr, *d_cursor = nullptr,
              *d_bof = nullptr, *d_scan = nullptr;
     Det* d_dets = nullptr;
@@ -281,6 +308,15 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       CK(cudaMemcpyAsync(hy, cat->y, n * 4, cudaMemcpyHostToDevice, s), "copy y");
       CK(cudaMemcpyAsync(hep, cat->epoch, n * 2, cudaMemcpyHostToDevice, s), "copy epoch");
       dx = hx; dy = hy; dep = hep;
+    }
+    if (weights) {
+      if (cat->on_device) {
+        d_w = weights;
+      } else {
+        CK(sc.alloc(&hw_dev, n), "alloc weights");
+        CK(cudaMemcpyAsync(hw_dev, weights, n, cudaMemcpyHostToDevice, s), "copy weights");
+        d_w = hw_dev;
+      }
     }
     CK(sc.alloc(&d_t, E), "alloc t");
     CK(cudaMallocAsync((void**)&d_dt, (size_t)E * 8, s), "alloc dt");
@@ -328,6 +364,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       CK(sc.alloc(&d_emits, emit_cap), "alloc emissions");
       CK(stack_set_smem_attr(tc.kx, tc.ky, tc.cb, tc.smem), "smem attribute");
       fill_stack_args(plan, n_min, &sa);
+      sa.w = d_w;
       sa.dets = d_dets;
       sa.boff = d_boff;
       sa.ecount = d_ecount;
@@ -384,7 +421,7 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
       // a5/a7: exact distinct and raw counts of every bin of the emitted super-bins
       cudaEventRecord(evc0, s);
       CK(launch_cell_count(d_emits, n_emit, plan.tc.s, g, cg, d_dets, d_boff, d_ecount, d_sxt,
-                           d_syt, n_min, d_keys, &d_small[2], &d_small64[2], s), "cell count");
+                           d_syt, n_min, d_keys, &d_small[2], &d_small64[2], d_w, s), "cell count");
       CK(cudaMemcpyAsync(&h_small[2], &d_small[2], 4, cudaMemcpyDeviceToHost, s), "read n_valid");
       CK(cudaMemcpyAsync(&h_small64[2], &d_small64[2], 8, cudaMemcpyDeviceToHost, s), "read raw");
       CK(cudaStreamSynchronize(s), "count sync");
@@ -462,6 +499,19 @@ int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, cons
   return SAS_OK;
 }
 
+}  // namespace
+
+int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, const sas_opts* opts,
+              void* stream, sas_result** out) {
+  return stack_impl(grid, cat, nullptr, n_min, opts, stream, out);
+}
+
+int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weights, uint32_t s_min,
+                       const sas_opts* opts, void* stream, sas_result** out) {
+  if (!weights && cat && cat->n) return fail(SAS_ERR_ARG, "null weights");
+  return stack_impl(grid, cat, weights ? weights : (const uint8_t*)"", s_min, opts, stream, out);
+}
+
 int sas_result_get_info(const sas_result* r, sas_result_info* info) {
   if (!r || !info) return fail(SAS_ERR_ARG, "null argument");
   *info = r->info;
@@ -526,6 +576,7 @@ int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, uint32_
     return fail(SAS_ERR_ARG, "n_min %u is below the search's threshold %u (cells under it are not in the list)",
                 n_min, r->n_min);
   if (!r->complete) return fail(SAS_ERR_ARG, "the search kept only its top candidates (max_candidates)");
+  if (r->weighted) return fail(SAS_ERR_ARG, "cluster finding counts distinct epochs; this search is weighted");
   if (flags & ~SAS_PEEL_SEQUENTIAL) return fail(SAS_ERR_ARG, "unknown flags 0x%x", flags);
   if (max_clusters == 0) max_clusters = 1000;
   cudaStream_t s = (cudaStream_t)stream;

@@ -26,16 +26,19 @@ __device__ __forceinline__ void bucket_range(int32_t o, int32_t span, uint64_t c
 // One warp per emitted super-bin of sb x sb bins: lane l handles epochs l,
 // l + 32, ...  For every bin q the epochs with at least one detection in it
 // form one bitmask per 32-epoch block (ballot) whose popcounts add up to the
-// exact distinct-epoch count.  Raw detection counts are taken afterwards, only
-// for the bins in the domain that reach n_min; lane 0 then calls
-// out(q, bx, by, distinct, raw) for each of them.
-template <typename Out>
+// exact distinct-epoch count.  Weighted (W): each lane keeps, per bin, the
+// largest weight among its epoch's detections there, and the warp sums of
+// those maxima add up to the bin's score instead.  Raw detection counts are
+// taken afterwards, only for the bins in the domain that reach n_min; lane 0
+// then calls out(q, bx, by, distinct or score, raw) for each of them.
+template <bool W = false, typename Out>
 __device__ __forceinline__ void count_superbin(const Emit& em, int sb, const SearchGeom& g, const CoarseGeom& cg,
                                                uint64_t cell_m, uint64_t bin_m, const Det* __restrict__ dets,
                                                const uint32_t* __restrict__ boff,
                                                const uint32_t* __restrict__ ecount,
                                                const int32_t* __restrict__ sxt, const int32_t* __restrict__ syt,
-                                               uint32_t n_min, int lane, Out out) {
+                                               uint32_t n_min, int lane, Out out,
+                                               const uint8_t* __restrict__ wts = nullptr) {
   constexpr int kMaxQ = 16;  // super-bins up to 4 x 4 bins
   const uint32_t kx = em.v_idx % (uint32_t)g.nvx, ky = em.v_idx / (uint32_t)g.nvx;
   const int nq = sb * sb;
@@ -46,6 +49,9 @@ __device__ __forceinline__ void count_superbin(const Emit& em, int sb, const Sea
   for (uint32_t eb = 0; eb < g.E; eb += 32) {
     const uint32_t e = eb + lane;
     uint32_t hit = 0;
+    uint32_t wmax[W ? kMaxQ : 1];
+#pragma unroll
+    for (int q = 0; q < (W ? kMaxQ : 1); ++q) wmax[q] = 0;
     if (e < g.E && ecount[e] > 0) {
       const int32_t ox = g.x_min + (int32_t)em.bx * g.bin + sxt[(size_t)kx * g.E + e];
       const int32_t oy = g.y_min + (int32_t)em.by * g.bin + syt[(size_t)ky * g.E + e];
@@ -58,14 +64,27 @@ __device__ __forceinline__ void count_superbin(const Emit& em, int sb, const Sea
         for (uint32_t k = boff[b0 + cxa]; k < k1; ++k) {
           const Det d = dets[k];
           const uint32_t X = (uint32_t)(d.x - ox), Y = (uint32_t)(d.y - oy);
-          if (X < (uint32_t)span && Y < (uint32_t)span)
-            hit |= 1u << ((int)div_by(Y, bin_m) * sb + (int)div_by(X, bin_m));
+          if (X < (uint32_t)span && Y < (uint32_t)span) {
+            const int qd = (int)div_by(Y, bin_m) * sb + (int)div_by(X, bin_m);
+            hit |= 1u << qd;
+            if constexpr (W) {
+              const uint32_t wd = wts[d.id];
+#pragma unroll
+              for (int q = 0; q < kMaxQ; ++q)
+                if (q == qd) wmax[q] = max(wmax[q], wd);
+            }
+          }
         }
       }
     }
 #pragma unroll
-    for (int q = 0; q < kMaxQ; ++q)
-      if (q < nq) distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
+    for (int q = 0; q < kMaxQ; ++q) {
+      if (q >= nq) continue;
+      if constexpr (W)
+        distinct[q] += __reduce_add_sync(0xffffffffu, wmax[q]);
+      else
+        distinct[q] += __popc(__ballot_sync(0xffffffffu, (hit >> q) & 1u));
+    }
   }
   // bins that become candidates (warp-uniform: the counts are)
   uint32_t need = 0;

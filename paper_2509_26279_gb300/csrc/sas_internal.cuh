@@ -97,6 +97,7 @@ struct StackArgs {
   int32_t nst_x, nst_y;      // spatial tiles
   uint64_t n_tiles;          // work units = velocity blocks x spatial tiles
   const Det* dets;
+  const uint8_t* w;          // [n] weight per detection id (weighted stacking), or null: all 1
   const uint32_t* boff;      // [E*ncy*ncx + 1]
   const uint32_t* ecount;    // [E] detections per epoch
   const int32_t* sxt;        // [nvx][E] shift in x
@@ -139,6 +140,8 @@ struct FieldPlan {
   uint64_t nb;  // buckets: E * ncy * ncx
   int64_t dT;   // max(t) - min(t)
 };
+// Super-bin side (1..4) for a search at threshold n_min (unit increments).
+int choose_superbin(const sas_grid_desc& d, uint64_t n, uint32_t n_min, uint64_t nv);
 int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t, int64_t tph,
                uint32_t n_min, uint64_t v_begin, uint64_t v_end, const sas_opts& o,
                const DevInfo& di, FieldPlan* fp);
@@ -182,12 +185,13 @@ cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
 
 // sas_post.cu
 // Appends one key per bin of an emitted super-bin that lies in the domain and
-// has >= n_min distinct epochs (keys needs room for s*s keys per emission).
+// has >= n_min distinct epochs -- or, with weights wts (by detection id), a
+// score >= n_min (keys needs room for s*s keys per emission).
 cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, const SearchGeom& g,
                               const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
                               const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
                               uint32_t n_min, Key* keys, uint32_t* n_valid,
-                              unsigned long long* raw_total, cudaStream_t s);
+                              unsigned long long* raw_total, const uint8_t* wts, cudaStream_t s);
 cudaError_t launch_sort_keys(Key* keys, uint32_t n, uint32_t n_pad, cudaStream_t s);
 // Sorts every aligned segment of `seg` keys (a power of two) of keys[0..n_total)
 // ascending; n_total is a multiple of seg.

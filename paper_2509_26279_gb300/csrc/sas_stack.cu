@@ -17,6 +17,11 @@
 // per-bin distinct-epoch counts (epoch bitmasks + popcount) are taken afterwards
 // in sas_post.cu, which also discards the rest.
 //
+// Weighted stacking: every detection carries an integer weight w (1 without
+// weights) and adds w instead of 1, so a super-bin's counter holds the sum of
+// its weights, which bounds every bin's score (sum over epochs of the largest
+// weight) from above; N_min is then the score threshold.
+//
 // A counter starts at 2^(CB-1) - N_min, so its top bit is set exactly when its
 // count reaches N_min.  The hot loop therefore only adds (the atomics' old
 // values are never read).  The pass that resets a tile's counters after its
@@ -125,14 +130,15 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t b) {
   else return b;
 }
 
-template <int KX, int KY, int CB, bool MASKED, bool MERGE>
+template <int KX, int KY, int CB, bool MASKED, bool MERGE, bool WT>
 __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 const int32_t* __restrict__ ox,
                                                 const int32_t* __restrict__ oy,
                                                 uint32_t cells_s, uint32_t tw_x,
                                                 uint32_t tw_y, uint32_t magic, bool one, int tx,
-                                                int txty, uint32_t act) {
+                                                int txty, uint32_t act, uint32_t w_in) {
   using C = Counter<CB>;
+  const uint32_t w = WT ? w_in : 1u;  // unweighted: a compile-time 1
   int32_t oxv[KX], oyv[KY];
   if constexpr (KX % 4 == 0) {
 #pragma unroll
@@ -180,8 +186,8 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
 #pragma unroll
       for (int q = 0; q < C::P; ++q) e |= (uint32_t)(col4[g * C::P + q] == col4[g * C::P]) << q;
       const uint32_t xb = (okxb >> (g * C::P)) & gmask;
-      lo[g] = spread_bits<CB>(xb & e);
-      hi[g] = spread_bits<CB>(xb & ~e);
+      lo[g] = spread_bits<CB>(xb & e) * w;
+      hi[g] = spread_bits<CB>(xb & ~e) * w;
     }
 #pragma unroll
     for (int ky = 0; ky < KY; ++ky) {
@@ -221,7 +227,7 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
 #pragma unroll
       for (int g = 0; g < KX / C::P; ++g) {
         const uint32_t rb = (m >> (ky * KX + g * C::P)) & gmask;
-        const uint32_t lo = spread_bits<CB>(rb & eqm[g]), hi = spread_bits<CB>(rb & ~eqm[g]);
+        const uint32_t lo = spread_bits<CB>(rb & eqm[g]) * w, hi = spread_bits<CB>(rb & ~eqm[g]) * w;
         const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
         red_shared_if(lo, plane + col4[g * C::P], lo);
         red_shared_if(hi, plane + col4[g * C::P + C::P - 1], hi);
@@ -233,7 +239,7 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
 #pragma unroll
       for (int kx = 0; kx < KX; ++kx) {
         const uint32_t addr = rbase4[ky] + col4[kx] + (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty * 4);
-        red_shared_if(m & (1u << (ky * KX + kx)), addr, 1u << (CB * (kx % C::P)));
+        red_shared_if(m & (1u << (ky * KX + kx)), addr, w << (CB * (kx % C::P)));
       }
     }
   }
@@ -320,7 +326,8 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
           xw = max(s0, s1) - min(s0, s1) + (int32_t)tw_x;
           ylo = Y0 + min(t0, t1);
           yw = max(t0, t1) - min(t0, t1) + (int32_t)tw_y;
-          if (xw >= (1 << 24)) my_flags |= kFlagInternal;  // staged x must fit 24 bits
+          // staged x fits 24 bits (the chunk epoch rides above it), and so does a weighted search's y
+          if (xw >= (1 << 24) || (a.w && yw >= (1 << 24))) my_flags |= kFlagInternal;
         }
         s_win[tid * 4 + 0] = xlo;
         s_win[tid * 4 + 1] = xw;
@@ -393,7 +400,8 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
           const uint32_t xr = (uint32_t)(d.x - s_win[el * 4]);
           const uint32_t yr = (uint32_t)(d.y - s_win[el * 4 + 2]);
           keep = xr < (uint32_t)s_win[el * 4 + 1] && yr < (uint32_t)s_win[el * 4 + 3];
-          rec = make_uint2(xr | ((uint32_t)el << 24), yr);
+          // weighted: the detection's weight rides in the top byte of y
+          rec = make_uint2(xr | ((uint32_t)el << 24), a.w ? (yr | ((uint32_t)a.w[d.id] << 24)) : yr);
         }
         uint32_t total;
         const uint32_t pos = block_scan(keep, s_misc, total);
@@ -434,25 +442,32 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
     auto compute = [&](int vtx, int vty, uint32_t act, uint32_t n_staged) {
       const uint32_t full = (KX * KY == 32) ? 0xffffffffu : ((1u << (KX * KY)) - 1u);
       const int oxo = vtx * KX, oyo = vty * KY;
-      uint32_t pairs = 0;
-      auto run = [&](auto masked, auto merge) {
+      uint32_t pairs = 0, added = 0;  // pairs, and the weight they added
+      auto run = [&](auto masked, auto merge, auto weighted) {
+        constexpr bool WT = decltype(weighted)::value;
         for (uint32_t j = tid; j < n_staged; j += kNT) {
           const uint2 r = staged[j];
           const int el = (int)(r.x >> 24);
-          pairs += process_rec<KX, KY, CB, decltype(masked)::value, decltype(merge)::value>(
-              r.x & 0xffffffu, r.y, s_ox + el * bxk + oxo, s_oy + el * byk + oyo, cells_s, tw_x, tw_y,
-              a.magic, a.bin_is_one, tc.tx, txty, act);
+          const uint32_t w = WT ? r.y >> 24 : 1u;
+          const uint32_t p = process_rec<KX, KY, CB, decltype(masked)::value, decltype(merge)::value, WT>(
+              r.x & 0xffffffu, WT ? r.y & 0xffffffu : r.y, s_ox + el * bxk + oxo, s_oy + el * byk + oyo, cells_s,
+              tw_x, tw_y, a.magic, a.bin_is_one, tc.tx, txty, act, w);
+          pairs += p;
+          added += WT ? p * w : p;
         }
       };
       using T = std::true_type;
       using F = std::false_type;
-      if (act == full) {
-        if (a.merge) run(F{}, T{}); else run(F{}, F{});
-      } else {
-        if (a.merge) run(T{}, T{}); else run(T{}, F{});
-      }
+      auto run_w = [&](auto weighted) {
+        if (act == full) {
+          if (a.merge) run(F{}, T{}, weighted); else run(F{}, F{}, weighted);
+        } else {
+          if (a.merge) run(T{}, T{}, weighted); else run(T{}, F{}, weighted);
+        }
+      };
+      if (a.w) run_w(T{}); else run_w(F{});
       pairs64 += pairs;
-      balance -= pairs;
+      balance -= added;
       __syncthreads();  // the reductions above are asm: order them before any reader
     };
 

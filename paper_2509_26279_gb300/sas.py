@@ -234,6 +234,40 @@ def sas_stack(grid: Grid, x, y, epoch, t, ticks_per_hour: int, n_min: int, *,
     return Result(h)
 
 
+_lib.sas_stack_weighted.argtypes = [_p, ctypes.POINTER(sas_catalog), _p, ctypes.c_uint32,
+                                    ctypes.POINTER(sas_opts), _p, ctypes.POINTER(_p)]
+EXPORTED.append("sas_stack_weighted")
+
+
+def sas_stack_weighted(grid: Grid, x, y, epoch, weights, t, ticks_per_hour: int, s_min: int, *,
+                       on_device: bool = False, opts: sas_opts | None = None, stream=None) -> Result:
+    """Weighted stacking: weights (uint8 per detection, host or device like x)
+    score each cell by the sum over epochs of its largest weight; candidates
+    have score >= s_min and their `count` is the score."""
+    t = np.ascontiguousarray(t, np.int64)
+    if on_device:
+        n = int(x.numel() if hasattr(x, "numel") else len(x))
+        px, py, pe, pw = _dev_ptr(x), _dev_ptr(y), _dev_ptr(epoch), _dev_ptr(weights)
+        keep = ()
+    else:
+        x = np.ascontiguousarray(x, np.int32)
+        y = np.ascontiguousarray(y, np.int32)
+        epoch = np.ascontiguousarray(epoch, np.uint16)
+        weights = np.ascontiguousarray(weights, np.uint8)
+        n = int(x.shape[0])
+        px, py, pe = x.ctypes.data, y.ctypes.data, epoch.ctypes.data
+        pw = weights.ctypes.data if n else None
+        keep = (x, y, epoch, weights)
+    cat = sas_catalog(n=n, x=px, y=py, epoch=pe, n_epochs=int(t.shape[0]), t=t.ctypes.data,
+                      ticks_per_hour=int(ticks_per_hour), on_device=1 if on_device else 0)
+    h = _p()
+    _check(_lib.sas_stack_weighted(grid.handle, ctypes.byref(cat), pw, int(s_min),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   _stream_handle(stream), ctypes.byref(h)))
+    del keep
+    return Result(h)
+
+
 def stack_catalog(grid: Grid, cat, n_min: int, **kw) -> Result:
     """sas_stack on a workloads.Catalog held in host memory."""
     return sas_stack(grid, cat.x, cat.y, cat.epoch, cat.t, cat.ticks_per_hour, n_min, **kw)
