@@ -280,5 +280,29 @@ def scaled(w: Workload, frac_noise: float = 1.0, n_epochs: Optional[int] = None,
     return Workload(w.name + "_scaled", r2, g2, w.n_min, w.seed if seed is None else seed)
 
 
+def snr_weights(cat: Catalog, nu_th: float = 5.0, scale: float = 8.0, seed: int = BASE_SEED + 6) -> np.ndarray:
+    """Synthetic detection weights for weighted stacking: round(scale * S/N),
+    clipped to [0, 255].  A mover detected with probability p has true S/N
+    nu = nu_th + sqrt(2) erfcinv(2 (1 - p)) (so that P(observed >= nu_th) = p)
+    and observed S/N nu + N(0, 1) redrawn until it is >= nu_th; a noise peak's
+    observed S/N is nu_th + an exponential tail with rate nu_th (the shape of
+    a Gaussian field's peak heights far above nu_th).  Inputs only."""
+    from scipy.special import erfcinv
+    rng = np.random.default_rng(seed)
+    n = len(cat.x)
+    nu_obs = nu_th + rng.exponential(1.0 / nu_th, n)
+    mv = np.nonzero(cat.mover >= 0)[0]
+    if len(mv) and len(cat.movers):
+        p = np.clip(cat.movers["p"][cat.mover[mv]], 1e-6, 1 - 1e-6)
+        nu = nu_th + np.sqrt(2.0) * erfcinv(2.0 * (1.0 - p))
+        obs = nu + rng.standard_normal(len(mv))
+        bad = obs < nu_th
+        while bad.any():
+            obs[bad] = nu[bad] + rng.standard_normal(int(bad.sum()))
+            bad = obs < nu_th
+        nu_obs[mv] = obs
+    return np.clip(np.rint(scale * nu_obs), 0, 255).astype(np.uint8)
+
+
 def load(w: Workload) -> Catalog:
     return make_catalog(w.recipe, w.seed)
