@@ -195,3 +195,31 @@ def test_refine_errors():
     empty = sas.stack_catalog(g, cases.catalog([], [], [], cat.t), 6)
     tracks, ids = sas.sas_refine(empty).tracks()
     assert len(tracks) == 0 and len(ids) == 0
+
+
+def test_refine_large_cluster_uses_the_radix_selection():
+    """A track buried in close noise: its cluster holds ~600 points, above the
+    256 where the C-step switches from rank counting to the binary descent."""
+    rng = np.random.default_rng(12)
+    E = 100
+    t = np.sort(rng.integers(0, 4 * 3600, E)).astype(np.int64)
+    xs, ys, es = [], [], []
+    for e in range(E):
+        bx, by = 50_000 + 1200 * t[e] / 3600, 60_000 - 800 * t[e] / 3600
+        xs.append(int(bx + rng.normal(0, 150))); ys.append(int(by + rng.normal(0, 150))); es.append(e)
+        for _ in range(6):
+            xs.append(int(bx + rng.uniform(-1900, 1900))); ys.append(int(by + rng.uniform(-1900, 1900)))
+            es.append(e)
+        for _ in range(30):
+            xs.append(int(rng.integers(0, 120_000))); ys.append(int(rng.integers(0, 120_000))); es.append(e)
+    cat = cases.catalog(xs, ys, es, t)
+    grid = W.GridSpec(vx0=-2000, vy0=-2000, dvx=400, dvy=400, nvx=11, nvy=11, x_min=0, y_min=0, nbx=30, nby=30,
+                      bin=4000, speed_min=0, speed_max=0)
+    res = sas.stack_catalog(sas.Grid(grid), cat, 30)
+    pl = sas.sas_peel(res, 30)
+    cl = clusters_of(pl)
+    assert len(cl[0][1]) > 256
+    kw = dict(n_starts=30, n_best=3, max_iter=3)
+    tracks, ids = sas.sas_refine(res, pl, seed=1, **kw).tracks()
+    compare(cat, 3600, cl, tracks, ids, range(len(cl)), grid.bin, 1, **kw)
+    assert tracks[0]["n_points"] > 256
