@@ -82,7 +82,7 @@ __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162
 // FP32 in TMEM), and every warp reads its TMEM lanes back for bias + ReLU + BF16
 // rounding.  Same numerics as the CUDA-core form: exact products, FP32 sums.
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;  // 16 warps: 4 TMEM lane quadrants x 4 column quarters
 constexpr int kTcKC1 = 12;  // conv1: K = 81 padded to 96 = 12 core matrices
 constexpr int kTcKC = 36;   // conv2, conv3: K = 288
 constexpr int kSmW1 = 0;
@@ -138,13 +138,13 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, const float* bias, __
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
 #pragma unroll
   for (int t = 0; t < NTILE; ++t) {
-    float v[16];
-    tc::ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32 + h * 16), v);
+    float v[8];
+    tc::ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32 + h * 8), v);
     const int m = t * 128 + q * 32 + lane;
     if (m < P) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int ch = h * 16 + j;
+      for (int j = 0; j < 8; ++j) {
+        const int ch = h * 8 + j;
         const __nv_bfloat16 r = __float2bfloat16_rn(fmaxf(v[j] + bias[ch], 0.f));
         if (out_s) out_s[ch * P + m] = r;
         if (out_g) out_g[ch * P + m] = r;
