@@ -36,7 +36,6 @@ struct sas_vet {
   float* v;
   float* grad;
   __nv_bfloat16* wb;     // BF16 copy in the flat order
-  __nv_bfloat16* wf1t;   // BF16 copy of fc1.w transposed to [2592][64]
   // activations and deltas of one batch
   __nv_bfloat16* a1;     // [B][32][13][13]
   __nv_bfloat16* a2;     // [B][32][11][11]
@@ -243,56 +242,115 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* _
   if (tid < 32) tc::tmem_free(tmem, 64);
 }
 
-// ---- forward: fc1 (+ReLU) and fc2 for 32 stamps per block --------------------
+// ---- forward: fc1 on the tensor cores, fc2 in the epilogue --------------------
+//
+// D[stamp][j] = sum_k a3[stamp][k] * fc1.w[j][k]: M = 128 stamps per block,
+// N = 64, K = 2592 in 27 blocks of 96.  Both operands are K-contiguous in
+// global memory; every thread copies 16-byte rows of core matrices into the
+// no-swizzle K-major layout of one of three stages while the MMAs of the
+// others run (one mbarrier per stage, bounded waits).  The epilogue (one TMEM
+// lane = one stamp; warps w and w + 4 share lane quadrant w, each takes 32 of
+// the 64 columns) adds the bias, applies ReLU, rounds to BF16, stores a4, and
+// forms the logit with fc2: two 32-column partial dots added in a fixed order.
+constexpr int kFcTcRows = 128, kFcTcKB = 96, kFcTcKC = kFcTcKB / 8, kFcTcNB = kF / kFcTcKB;
+constexpr int kFcTcThreads = 256, kFcTcStages = 3;
+constexpr int kFcTcA = kFcTcRows * kFcTcKB * 2, kFcTcB = kHid * kFcTcKB * 2;
+constexpr int kFcTcStage = kFcTcA + kFcTcB;
+constexpr int kFcTcSmem = kFcTcStages * kFcTcStage + 2 * kHid * 4 + 8 * kFcTcStages + 16;
+static_assert(kF % kFcTcKB == 0, "fc1 K blocks");
 
-constexpr int kFcTB = 32, kFcKC = 64;
-
-__global__ void __launch_bounds__(256) k_fc_fwd(const __nv_bfloat16* __restrict__ a3g, uint32_t n,
-                                                const __nv_bfloat16* __restrict__ wf1t,
-                                                const __nv_bfloat16* __restrict__ wb,
-                                                __nv_bfloat16* a4g, float* __restrict__ logits) {
-  __shared__ __align__(16) float As[kFcTB][kFcKC + 1];
-  __shared__ __align__(16) float Bs[kFcKC][kHid];
-  const int t = threadIdx.x, jq = t & 15, sg = t >> 4;
-  const uint32_t b0 = blockIdx.x * kFcTB;
-  float acc[2][4] = {};
-  for (int k0 = 0; k0 < kF; k0 += kFcKC) {
-    const int kc = min(kFcKC, kF - k0);
-    for (int i = t; i < kFcTB * kFcKC; i += 256) {
-      const int s = i / kFcKC, k = i % kFcKC;
-      As[s][k] = (b0 + s < n && k < kc) ? ld(a3g + (size_t)(b0 + s) * kF + k0 + k) : 0.f;
+__global__ void __launch_bounds__(kFcTcThreads) k_fc_fwd_tc(const __nv_bfloat16* __restrict__ a3g, uint32_t n,
+                                                            const __nv_bfloat16* __restrict__ wb,
+                                                            __nv_bfloat16* a4g, float* __restrict__ logits,
+                                                            uint32_t* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smf[];
+  float* b1 = reinterpret_cast<float*>(smf + kFcTcStages * kFcTcStage);
+  float* w2 = b1 + kHid;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(w2 + kHid);  // [kFcTcStages]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kFcTcStages);
+  float* part = reinterpret_cast<float*>(smf);               // epilogue: [128] (stage 0 is free by then)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t b0 = blockIdx.x * kFcTcRows;
+  if (tid < 32) tc::tmem_alloc(tslot, kHid);
+  if (tid == 0)
+    for (int st = 0; st < kFcTcStages; ++st) tc::mbar_init(bar + st, 1);
+  if (tid < kHid) {
+    b1[tid] = ld(wb + kBf1 + tid);
+    w2[tid] = ld(wb + kWf2 + tid);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint4* a3v = reinterpret_cast<const uint4*>(a3g);
+  const uint4* w1v = reinterpret_cast<const uint4*>(wb + kWf1);
+  constexpr uint32_t idesc = tc::idesc_bf16(kFcTcRows, kHid);
+  uint32_t ph[kFcTcStages] = {};
+  bool ok = true;
+  for (int kb = 0; kb < kFcTcNB && ok; ++kb) {
+    const int st = kb % kFcTcStages;
+    unsigned char* A = smf + st * kFcTcStage;
+    unsigned char* B = A + kFcTcA;
+    if (kb >= kFcTcStages) {  // the MMAs that read this stage kFcTcStages blocks ago are done
+      ok = tc::mbar_wait(bar + st, ph[st], 1u << 22);
+      ph[st] ^= 1u;
+      if (__syncthreads_or(!ok)) break;
     }
-    for (int i = t; i < kFcKC * kHid; i += 256) {
-      const int k = i / kHid;
-      Bs[k][i % kHid] = k < kc ? ld(wf1t + (size_t)(k0 + k) * kHid + i % kHid) : 0.f;
+    const int k8 = kb * kFcTcKC;  // first 16-byte chunk of the block along K
+    for (int i = tid; i < kFcTcRows * kFcTcKC; i += kFcTcThreads) {
+      const int r = i / kFcTcKC, c = i - r * kFcTcKC;
+      const uint4 v = b0 + r < n ? a3v[(size_t)(b0 + r) * (kF / 8) + k8 + c] : make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(A + tc::cm_offset(r, c * 8, kFcTcKC)) = v;
     }
+    for (int i = tid; i < kHid * kFcTcKC; i += kFcTcThreads) {
+      const int r = i / kFcTcKC, c = i - r * kFcTcKC;
+      *reinterpret_cast<uint4*>(B + tc::cm_offset(r, c * 8, kFcTcKC)) = w1v[(size_t)r * (kF / 8) + k8 + c];
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
     __syncthreads();
-    for (int k = 0; k < kc; ++k) {
-      const float4 w = *reinterpret_cast<const float4*>(&Bs[k][jq * 4]);
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(A), w0 = tc::smem_u32(B);
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const float a = As[sg * 2 + s][k];
-        acc[s][0] = fmaf(a, w.x, acc[s][0]); acc[s][1] = fmaf(a, w.y, acc[s][1]);
-        acc[s][2] = fmaf(a, w.z, acc[s][2]); acc[s][3] = fmaf(a, w.w, acc[s][3]);
+      for (int ks = 0; ks < kFcTcKC / 2; ++ks)
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + (uint32_t)(2 * ks * 128), kFcTcKC),
+                     tc::smem_desc(w0 + (uint32_t)(2 * ks * 128), kFcTcKC), idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+      tc::commit(bar + st);
+    }
+  }
+  if (ok) {  // the last blocks' commits (one outstanding per stage)
+    for (int st = 0; st < kFcTcStages && ok; ++st) {
+      ok = tc::mbar_wait(bar + st, ph[st], 1u << 22);
+      ph[st] ^= 1u;
+    }
+    ok = !__syncthreads_or(!ok);
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1u);
+  } else {
+    tc::fence_after_sync();
+    const int q = warp & 3, h = warp >> 2;  // lane quadrant, column half
+    const uint32_t r = (uint32_t)(q * 32 + lane), b = b0 + r;
+    float dot = 0.f;
+#pragma unroll
+    for (int c = h * 32; c < h * 32 + 32; c += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float a = bf(fmaxf(v[j] + b1[c + j], 0.f));
+        if (a4g && b < n) a4g[(size_t)b * kHid + c + j] = __float2bfloat16_rn(a);
+        dot = fmaf(a, w2[c + j], dot);
       }
     }
+    if (h == 1) part[r] = dot;
     __syncthreads();
+    if (h == 0 && b < n) logits[b] = (dot + part[r]) + ld(wb + kBf2);
   }
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const uint32_t b = b0 + sg * 2 + s;
-    float part = 0.f;
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = jq * 4 + jj;
-      const float a = bf(fmaxf(acc[s][jj] + ld(wb + kBf1 + j), 0.f));
-      if (a4g && b < n) a4g[(size_t)b * kHid + j] = __float2bfloat16_rn(a);
-      part = fmaf(a, ld(wb + kWf2 + j), part);
-    }
-    // the 16 threads of a stamp are 16 consecutive lanes
-    for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (jq == 0 && b < n) logits[b] = part + ld(wb + kBf2);
-  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid < 32) tc::tmem_free(tmem, kHid);
 }
 
 // ---- loss, fc2 gradients, fc1 output deltas ------------------------------------
@@ -567,23 +625,16 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_block
 
 // ---- parameters --------------------------------------------------------------
 
-__global__ void k_cast(const float* __restrict__ master, __nv_bfloat16* __restrict__ wb,
-                       __nv_bfloat16* __restrict__ wf1t) {
+__global__ void k_cast(const float* __restrict__ master, __nv_bfloat16* __restrict__ wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
-  const __nv_bfloat16 h = __float2bfloat16_rn(master[i]);
-  wb[i] = h;
-  if (i >= kWf1 && i < kBf1) {
-    const int r = i - kWf1, j = r / kF, k = r - j * kF;
-    wf1t[(size_t)k * kHid + j] = h;
-  }
+  wb[i] = __float2bfloat16_rn(master[i]);
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 master values; refreshes the BF16 copies.
 __global__ void k_adam(float* __restrict__ master, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ grad, float lr, float beta1, float beta2, float eps,
-                       float bc1, float bc2, __nv_bfloat16* __restrict__ wb,
-                       __nv_bfloat16* __restrict__ wf1t) {
+                       float bc1, float bc2, __nv_bfloat16* __restrict__ wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParams) return;
   const float g = grad[i];
@@ -593,12 +644,7 @@ __global__ void k_adam(float* __restrict__ master, float* __restrict__ m, float*
   v[i] = vi;
   const float p = master[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   master[i] = p;
-  const __nv_bfloat16 h = __float2bfloat16_rn(p);
-  wb[i] = h;
-  if (i >= kWf1 && i < kBf1) {
-    const int r = i - kWf1, j = r / kF, k = r - j * kF;
-    wf1t[(size_t)k * kHid + j] = h;
-  }
+  wb[i] = __float2bfloat16_rn(p);
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -612,6 +658,8 @@ cudaError_t set_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fc_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFcTcSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_back<kCh, kH2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)back_smem<kCh, kH2, true>());
@@ -643,8 +691,9 @@ cudaError_t forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* idx, ui
   const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
   k_conv_fwd_tc<<<blocks, kTcThreads, kTcSmem, s>>>(stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr,
                                                    keep ? vt->a2 : nullptr, vt->a3, vt->status);
-  k_fc_fwd<<<(n + kFcTB - 1) / kFcTB, 256, 0, s>>>(vt->a3, n, vt->wf1t, vt->wb, keep ? vt->a4 : nullptr,
-                                                    logits);
+  k_fc_fwd_tc<<<(n + kFcTcRows - 1) / kFcTcRows, kFcTcThreads, kFcTcSmem, s>>>(vt->a3, n, vt->wb,
+                                                                            keep ? vt->a4 : nullptr, logits,
+                                                                            vt->status);
   note_launch(2);
   return cudaGetLastError();
 }
@@ -679,7 +728,7 @@ cudaError_t adam(sas_vet* vt, const float* grad, float lr, cudaStream_t s) {
   const double bc1 = 1.0 - std::pow((double)vt->beta1, (double)vt->step);
   const double bc2 = 1.0 - std::pow((double)vt->beta2, (double)vt->step);
   k_adam<<<(kNParams + 255) / 256, 256, 0, s>>>(vt->master, vt->m, vt->v, grad, lr, vt->beta1, vt->beta2,
-                                               vt->eps, (float)bc1, (float)bc2, vt->wb, vt->wf1t);
+                                               vt->eps, (float)bc1, (float)bc2, vt->wb);
   note_launch();
   return cudaGetLastError();
 }
@@ -721,7 +770,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 void free_vet(sas_vet* vt) {
-  void* ptrs[] = {vt->master, vt->m, vt->v, vt->grad, vt->wb, vt->wf1t, vt->a1, vt->a2, vt->a3,
+  void* ptrs[] = {vt->master, vt->m, vt->v, vt->grad, vt->wb, vt->a1, vt->a2, vt->a3,
                   vt->a4, vt->logits, vt->glogit, vt->g4, vt->g3, vt->g2, vt->g1, vt->partial, vt->loss,
                   vt->status};
   for (void* p : ptrs)
@@ -755,7 +804,7 @@ int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
     size_t bytes;
   } reqs[] = {
       {(void**)&vt->master, N * 4}, {(void**)&vt->m, N * 4}, {(void**)&vt->v, N * 4},
-      {(void**)&vt->grad, N * 4}, {(void**)&vt->wb, N * 2}, {(void**)&vt->wf1t, (size_t)vet::kF * vet::kHid * 2},
+      {(void**)&vt->grad, N * 4}, {(void**)&vt->wb, N * 2},
       {(void**)&vt->a1, B * vet::kCh * vet::kH1 * vet::kH1 * 2}, {(void**)&vt->a2, B * vet::kCh * vet::kH2 * vet::kH2 * 2},
       {(void**)&vt->a3, B * vet::kF * 2}, {(void**)&vt->a4, B * vet::kHid * 2}, {(void**)&vt->logits, B * 4},
       {(void**)&vt->glogit, B * 4}, {(void**)&vt->g4, B * vet::kHid * 4}, {(void**)&vt->g3, B * vet::kF * 4},
@@ -773,7 +822,7 @@ int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
   cudaMemset(vt->master, 0, N * 4);
   cudaMemset(vt->m, 0, N * 4);
   cudaMemset(vt->v, 0, N * 4);
-  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb, vt->wf1t);
+  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb);
   note_launch();
   if (cudaError_t e = cudaDeviceSynchronize(); e != cudaSuccess) {
     free_vet(vt);
@@ -824,7 +873,7 @@ int sas_vet_set_state(sas_vet* vt, const float* params, const float* m, const fl
   if (e == cudaSuccess) e = v ? cudaMemcpy(vt->v, v, bytes, cudaMemcpyHostToDevice) : cudaMemset(vt->v, 0, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "sas_vet_set_state");
   vt->step = m ? step : 0;
-  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb, vt->wf1t);
+  vet::k_cast<<<(vet::kNParams + 255) / 256, 256>>>(vt->master, vt->wb);
   note_launch();
   e = cudaDeviceSynchronize();
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_set_state");
