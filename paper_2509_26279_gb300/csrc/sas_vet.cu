@@ -42,6 +42,7 @@ struct sas_vet {
   __nv_bfloat16* a3;     // [B][2592]
   __nv_bfloat16* a4;     // [B][64]
   float* logits;         // [B]
+  float* fcpart;         // [kFcSplit][64][B rounded up to 128] fc1 partial sums
   float* glogit;         // [B]
   float* g4;             // [B][64]
   float* g3;             // [B][2592]
@@ -223,9 +224,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* _
   tc::fence_after_sync();
   const uint32_t tmem = *tslot;
   uint32_t phase = 0;
-  for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+  // each thread holds its share of the next stamp while the current one runs
+  constexpr int kPer = (kQ * kS * kS + kTcThreads - 1) / kTcThreads;
+  uint16_t nxt[kPer];
+  auto fetch = [&](uint32_t b) {
+    if (b >= n) return;
     const uint16_t* st = stamps + (size_t)(idx ? idx[b] : b) * kQ * kS * kS;
-    for (int i = tid; i < kQ * kS * kS; i += kTcThreads) x0[i] = __float2bfloat16_rn((float)st[i] * 0.0625f);
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int i = tid + r * kTcThreads;
+      nxt[r] = i < kQ * kS * kS ? st[i] : (uint16_t)0;
+    }
+  };
+  fetch(blockIdx.x);
+  for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int i = tid + r * kTcThreads;
+      if (i < kQ * kS * kS) x0[i] = __float2bfloat16_rn((float)nxt[r] * 0.0625f);
+    }
+    fetch(b + gridDim.x);
     __syncthreads();
     if (!tc_layer<kS, kTcKC1, 2>(x0, tab1, smc + kSmA, smc + kSmW1, tmem, bar, phase, bias, a1,
                                  a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr) ||
@@ -245,39 +263,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* _
 // ---- forward: fc1 on the tensor cores, fc2 in the epilogue --------------------
 //
 // D[stamp][j] = sum_k a3[stamp][k] * fc1.w[j][k]: M = 128 stamps per block,
-// N = 64, K = 2592 in 27 blocks of 96.  Both operands are K-contiguous in
-// global memory; every thread copies 16-byte rows of core matrices into the
-// no-swizzle K-major layout of one of three stages while the MMAs of the
-// others run (one mbarrier per stage, bounded waits).  The epilogue (one TMEM
-// lane = one stamp; warps w and w + 4 share lane quadrant w, each takes 32 of
-// the 64 columns) adds the bias, applies ReLU, rounds to BF16, stores a4, and
-// forms the logit with fc2: two 32-column partial dots added in a fixed order.
+// N = 64, K = 2592 in 27 blocks of 96, split over kFcSplit blocks along K so
+// that a batch of 4096 stamps keeps 128 SMs busy.  Both operands are
+// K-contiguous in global memory; every thread copies 16-byte rows of core
+// matrices into the no-swizzle K-major layout of one of three stages while the
+// MMAs of the others run (one mbarrier per stage, bounded waits).  Each block
+// writes its FP32 partial D column-major; k_fc_epi adds the kFcSplit partials
+// in a fixed order, adds the bias, applies ReLU, rounds to BF16, stores a4 and
+// forms the logit with fc2 in a fixed order.
 constexpr int kFcTcRows = 128, kFcTcKB = 96, kFcTcKC = kFcTcKB / 8, kFcTcNB = kF / kFcTcKB;
-constexpr int kFcTcThreads = 256, kFcTcStages = 3;
+constexpr int kFcTcThreads = 256, kFcTcStages = 3, kFcSplit = 4;
 constexpr int kFcTcA = kFcTcRows * kFcTcKB * 2, kFcTcB = kHid * kFcTcKB * 2;
 constexpr int kFcTcStage = kFcTcA + kFcTcB;
-constexpr int kFcTcSmem = kFcTcStages * kFcTcStage + 2 * kHid * 4 + 8 * kFcTcStages + 16;
+constexpr int kFcTcSmem = kFcTcStages * kFcTcStage + 8 * kFcTcStages + 16;
 static_assert(kF % kFcTcKB == 0, "fc1 K blocks");
 
+// part[s][j][stamp] (stamps padded to whole 128-row tiles: ld = tiles * 128)
 __global__ void __launch_bounds__(kFcTcThreads) k_fc_fwd_tc(const __nv_bfloat16* __restrict__ a3g, uint32_t n,
                                                             const __nv_bfloat16* __restrict__ wb,
-                                                            __nv_bfloat16* a4g, float* __restrict__ logits,
+                                                            float* __restrict__ part, uint32_t ldp,
                                                             uint32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smf[];
-  float* b1 = reinterpret_cast<float*>(smf + kFcTcStages * kFcTcStage);
-  float* w2 = b1 + kHid;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(w2 + kHid);  // [kFcTcStages]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smf + kFcTcStages * kFcTcStage);  // [kFcTcStages]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + kFcTcStages);
-  float* part = reinterpret_cast<float*>(smf);               // epilogue: [128] (stage 0 is free by then)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t b0 = blockIdx.x * kFcTcRows;
+  const int sp = blockIdx.y;
+  const int kb_lo = sp * kFcTcNB / kFcSplit, kb_hi = (sp + 1) * kFcTcNB / kFcSplit;
   if (tid < 32) tc::tmem_alloc(tslot, kHid);
   if (tid == 0)
     for (int st = 0; st < kFcTcStages; ++st) tc::mbar_init(bar + st, 1);
-  if (tid < kHid) {
-    b1[tid] = ld(wb + kBf1 + tid);
-    w2[tid] = ld(wb + kWf2 + tid);
-  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -287,11 +302,11 @@ __global__ void __launch_bounds__(kFcTcThreads) k_fc_fwd_tc(const __nv_bfloat16*
   constexpr uint32_t idesc = tc::idesc_bf16(kFcTcRows, kHid);
   uint32_t ph[kFcTcStages] = {};
   bool ok = true;
-  for (int kb = 0; kb < kFcTcNB && ok; ++kb) {
-    const int st = kb % kFcTcStages;
+  for (int kb = kb_lo; kb < kb_hi && ok; ++kb) {
+    const int l = kb - kb_lo, st = l % kFcTcStages;
     unsigned char* A = smf + st * kFcTcStage;
     unsigned char* B = A + kFcTcA;
-    if (kb >= kFcTcStages) {  // the MMAs that read this stage kFcTcStages blocks ago are done
+    if (l >= kFcTcStages) {  // the MMAs that read this stage kFcTcStages blocks ago are done
       ok = tc::mbar_wait(bar + st, ph[st], 1u << 22);
       ph[st] ^= 1u;
       if (__syncthreads_or(!ok)) break;
@@ -315,12 +330,13 @@ __global__ void __launch_bounds__(kFcTcThreads) k_fc_fwd_tc(const __nv_bfloat16*
 #pragma unroll
       for (int ks = 0; ks < kFcTcKC / 2; ++ks)
         tc::mma_bf16(tmem, tc::smem_desc(a0 + (uint32_t)(2 * ks * 128), kFcTcKC),
-                     tc::smem_desc(w0 + (uint32_t)(2 * ks * 128), kFcTcKC), idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                     tc::smem_desc(w0 + (uint32_t)(2 * ks * 128), kFcTcKC), idesc, (l > 0 || ks > 0) ? 1u : 0u);
       tc::commit(bar + st);
     }
   }
-  if (ok) {  // the last blocks' commits (one outstanding per stage)
-    for (int st = 0; st < kFcTcStages && ok; ++st) {
+  if (ok) {  // one commit outstanding on every stage that was used
+    const int used = min(kb_hi - kb_lo, kFcTcStages);
+    for (int st = 0; st < used && ok; ++st) {
       ok = tc::mbar_wait(bar + st, ph[st], 1u << 22);
       ph[st] ^= 1u;
     }
@@ -331,26 +347,44 @@ __global__ void __launch_bounds__(kFcTcThreads) k_fc_fwd_tc(const __nv_bfloat16*
   } else {
     tc::fence_after_sync();
     const int q = warp & 3, h = warp >> 2;  // lane quadrant, column half
-    const uint32_t r = (uint32_t)(q * 32 + lane), b = b0 + r;
-    float dot = 0.f;
+    const uint32_t b = b0 + (uint32_t)(q * 32 + lane);
+    float* out = part + (size_t)sp * kHid * ldp;
 #pragma unroll
     for (int c = h * 32; c < h * 32 + 32; c += 16) {
       float v[16];
       tc::ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float a = bf(fmaxf(v[j] + b1[c + j], 0.f));
-        if (a4g && b < n) a4g[(size_t)b * kHid + c + j] = __float2bfloat16_rn(a);
-        dot = fmaf(a, w2[c + j], dot);
-      }
+      for (int jj = 0; jj < 16; ++jj) out[(size_t)(c + jj) * ldp + b] = v[jj];
     }
-    if (h == 1) part[r] = dot;
-    __syncthreads();
-    if (h == 0 && b < n) logits[b] = (dot + part[r]) + ld(wb + kBf2);
   }
   tc::fence_before_sync();
   __syncthreads();
   if (tid < 32) tc::tmem_free(tmem, kHid);
+}
+
+// One thread per stamp: the partial sums in split order, bias, ReLU, BF16,
+// then fc2 in j order.
+__global__ void __launch_bounds__(256) k_fc_epi(const float* __restrict__ part, uint32_t ldp, uint32_t n,
+                                                const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* a4g,
+                                                float* __restrict__ logits) {
+  __shared__ float b1[kHid], w2[kHid];
+  if (threadIdx.x < kHid) {
+    b1[threadIdx.x] = ld(wb + kBf1 + threadIdx.x);
+    w2[threadIdx.x] = ld(wb + kWf2 + threadIdx.x);
+  }
+  __syncthreads();
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  float logit = 0.f;
+  for (int j = 0; j < kHid; ++j) {
+    float acc = part[(size_t)j * ldp + b];
+#pragma unroll
+    for (int sp = 1; sp < kFcSplit; ++sp) acc += part[((size_t)sp * kHid + j) * ldp + b];
+    const float a = bf(fmaxf(acc + b1[j], 0.f));
+    if (a4g) a4g[(size_t)b * kHid + j] = __float2bfloat16_rn(a);
+    logit = fmaf(a, w2[j], logit);
+  }
+  logits[b] = logit + ld(wb + kBf2);
 }
 
 // ---- loss, fc2 gradients, fc1 output deltas ------------------------------------
@@ -691,9 +725,11 @@ cudaError_t forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* idx, ui
   const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
   k_conv_fwd_tc<<<blocks, kTcThreads, kTcSmem, s>>>(stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr,
                                                    keep ? vt->a2 : nullptr, vt->a3, vt->status);
-  k_fc_fwd_tc<<<(n + kFcTcRows - 1) / kFcTcRows, kFcTcThreads, kFcTcSmem, s>>>(vt->a3, n, vt->wb,
-                                                                            keep ? vt->a4 : nullptr, logits,
-                                                                            vt->status);
+  const uint32_t tiles = (n + kFcTcRows - 1) / kFcTcRows, ldp = tiles * kFcTcRows;
+  k_fc_fwd_tc<<<dim3(tiles, kFcSplit), kFcTcThreads, kFcTcSmem, s>>>(vt->a3, n, vt->wb, vt->fcpart, ldp,
+                                                                     vt->status);
+  k_fc_epi<<<(n + 255) / 256, 256, 0, s>>>(vt->fcpart, ldp, n, vt->wb, keep ? vt->a4 : nullptr, logits);
+  note_launch();
   note_launch(2);
   return cudaGetLastError();
 }
@@ -772,7 +808,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 void free_vet(sas_vet* vt) {
   void* ptrs[] = {vt->master, vt->m, vt->v, vt->grad, vt->wb, vt->a1, vt->a2, vt->a3,
                   vt->a4, vt->logits, vt->glogit, vt->g4, vt->g3, vt->g2, vt->g1, vt->partial, vt->loss,
-                  vt->status};
+                  vt->status, vt->fcpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete vt;
@@ -811,6 +847,7 @@ int sas_vet_create(int device, uint32_t max_batch, sas_vet** out) {
       {(void**)&vt->g2, B * vet::kCh * vet::kH2 * vet::kH2 * 4}, {(void**)&vt->g1, B * vet::kCh * vet::kH1 * vet::kH1 * 4},
       {(void**)&vt->partial, (size_t)vet::kBackBlocks * vet::kPartialStride * 4}, {(void**)&vt->loss, 4},
       {(void**)&vt->status, 4},
+      {(void**)&vt->fcpart, (size_t)vet::kFcSplit * vet::kHid * ((B + 127) / 128 * 128) * 4},
   };
   for (auto& r : reqs) {
     if (cudaError_t e = cudaMalloc(r.p, r.bytes); e != cudaSuccess) {
