@@ -460,7 +460,9 @@ void sas_tracks_free(sas_tracks* tracks);
  * size dx and the threshold N_min.  Lengths in one unit throughout (pixels or
  * arcsec), times in hours, velocities in length per hour, omega in length^2.
  * Each returns SAS_OK and writes its result, or SAS_ERR_ARG for a null output
- * or an argument outside its domain (non-positive dx, dt, a; negative rate).
+ * or an argument outside its domain (non-positive dx, dt, a; negative rate),
+ * or SAS_ERR_RANGE for a noise rate above 1e7 (choose_n_min, dx_scan) or more
+ * than 65536 epochs (signal_tail).
  *
  * velocity_count: |V| = ((vmax_x - vmin_x) / dv)((vmax_y - vmin_y) / dv) with
  *   dv = dx / dt (Eq. v_size).

@@ -100,10 +100,16 @@ double poisson_sf(uint32_t k, double lam) {
   return 1.0 - below;
 }
 
+// Smallest k with P(N >= k) <= eps: P(N >= k) falls with k, so a binary search
+// over [0, hi], hi far enough into the tail that it holds there.
 uint32_t choose_n_min(double lam, double eps) {
-  uint32_t k = 0;
-  while (k < (1u << 30) && poisson_sf(k, lam) > eps) ++k;
-  return k;
+  if (poisson_sf(0, lam) <= eps) return 0;
+  uint32_t lo = 0, hi = (uint32_t)(lam + 60.0 * std::sqrt(lam) + 1000.0);  // sf(hi) < 1e-300
+  while (hi - lo > 1) {  // sf(lo) > eps >= sf(hi)
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (poisson_sf(mid, lam) > eps) lo = mid; else hi = mid;
+  }
+  return hi;
 }
 
 double p_signal(double nu, double nu_th, double a, double dx) {
@@ -172,6 +178,7 @@ int sas_param_poisson_sf(uint32_t k, double lambda, double* out) {
 int sas_param_choose_n_min(double lambda, double eps, uint32_t* out) {
   if (!out) return set_error(SAS_ERR_ARG, "null output");
   if (!std::isfinite(lambda) || lambda < 0 || !(eps > 0)) return set_error(SAS_ERR_ARG, "need lambda >= 0, eps > 0");
+  if (lambda > 1e7) return set_error(SAS_ERR_RANGE, "lambda above 1e7");
   *out = choose_n_min(lambda, eps);
   return SAS_OK;
 }
@@ -186,6 +193,7 @@ int sas_param_p_signal(double nu, double nu_th, double a, double dx, double* out
 
 int sas_param_signal_tail(const double* p, uint32_t n, uint32_t k, double* out) {
   if (!out || (n && !p)) return set_error(SAS_ERR_ARG, "null argument");
+  if (n > 65536) return set_error(SAS_ERR_RANGE, "more than 65536 epochs");
   std::vector<double> dist(1, 1.0);
   for (uint32_t i = 0; i < n; ++i) {
     if (!(p[i] >= 0.0 && p[i] <= 1.0)) return set_error(SAS_ERR_ARG, "probabilities must lie in [0, 1]");
@@ -215,6 +223,11 @@ int sas_param_dx_scan(double nu, double nu_th, const double* a, uint32_t n_epoch
   for (uint32_t j = 0; j < n_dx; ++j)
     if (!finite_pos(dx[j])) return set_error(SAS_ERR_ARG, "bin sizes must be > 0");
   const double lam1 = peaks_above(nu_th, 1.0);
+  for (uint32_t j = 0; j < n_dx; ++j) {
+    double en = 0.0;
+    for (uint32_t i = 0; i < n_epochs; ++i) en += lam1 * (dx[j] / a[i]) * (dx[j] / a[i]);
+    if (!(en <= 1e7)) return set_error(SAS_ERR_RANGE, "noise rate above 1e7 for a bin size");
+  }
   for (uint32_t j = 0; j < n_dx; ++j) {
     double es = 0.0, en = 0.0;
     for (uint32_t i = 0; i < n_epochs; ++i) {

@@ -48,6 +48,18 @@ def test_signal_terms_and_scan():
         assert g[1] == pytest.approx(w[1], rel=1e-13) and g[2] == pytest.approx(w[2], rel=1e-8)
 
 
+def test_n_min_far_into_the_tail_and_range_limits():
+    # binary search: large rates finish quickly and agree with scipy's tail
+    from scipy import stats
+    for lam, eps in [(5e4, 1e-12), (3e6, 1e-9)]:
+        k = L.choose_n_min(lam, eps)
+        assert stats.poisson.sf(k - 1, lam) <= eps < stats.poisson.sf(k - 2, lam)
+    with pytest.raises(sas.SasError):
+        L.choose_n_min(2e7, 0.1)
+    with pytest.raises(sas.SasError):
+        L.signal_tail(np.full(70000, 0.5), 3)
+
+
 def test_argument_errors():
     with pytest.raises(sas.SasError):
         L.peaks_above(1.0, 0.0)
