@@ -148,6 +148,23 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     b->plans.push_back(fp);
   }
   if (rc != SAS_OK) { free_batch(b); return rc; }
+  // one launch needs one tile shape: where the default 8 x 8 tile fell back to
+  // 8 x 4 for some fields, plan every field with 8 x 4
+  bool mixed = false;
+  for (const FieldPlan& fp : b->plans) mixed |= fp.tc.ky != b->plans[0].tc.ky;
+  if (mixed) {
+    for (uint32_t f = 0; f < n_fields && rc == SAS_OK; ++f) {
+      if (b->opts[f].tile_ky) continue;  // chosen by the caller: left as is (checked below)
+      b->opts[f].tile_ky = 4;
+      sas_grid_desc desc;
+      rc = sas_grid_get_desc(b->grids[f], &desc);
+      const sas_catalog& c = b->cats[f];
+      if (rc == SAS_OK)
+        rc = plan_field(desc, c.n, c.n_epochs, c.t, c.ticks_per_hour, b->n_min[f], 0,
+                        (uint64_t)desc.nvx * desc.nvy, b->opts[f], di, &b->plans[f]);
+    }
+    if (rc != SAS_OK) { free_batch(b); return rc; }
+  }
   b->kx = b->plans[0].tc.kx;
   b->ky = b->plans[0].tc.ky;
   b->cb = 8;

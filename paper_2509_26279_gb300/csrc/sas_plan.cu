@@ -123,7 +123,12 @@ int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int
       spread_bound((int64_t)(ky - 1) * std::llabs((int64_t)d.dvy), dT, tph) >= (1 << 23))
     return set_error(SAS_ERR_RANGE, "lattice step x time span too large (shift spread >= 2^23 mpx)");
   double cells_frac = 0.62;
-  int bv_cap = 8;
+  // 8 x 8 velocity tiles share each record's column projections over 8 rows;
+  // with them, blocks of up to 4 x 4 tiles whose union window stays within
+  // ~20 % of the tile per axis measured best (decam_tno and fast_movers).
+  const bool tall = kx * ky > 32;
+  int bv_cap = tall ? 4 : 8;
+  const int64_t win_pct = tall ? 20 : 15;
   for (int iter = 0; iter < 200; ++iter) {
     const int64_t cells_bytes = (int64_t)(budget * cells_frac);
     int side = (int)std::sqrt((double)cells_bytes * 8.0 / ((double)kx * ky * cb));
@@ -141,8 +146,8 @@ int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int
     if (((int64_t)tc.tx * tc.ty) % 4 != 0)
       return set_error(SAS_ERR_ARG, "tile_bx * tile_by must be a multiple of 4");
     const int64_t tw = (int64_t)tc.tx * sbin, th = (int64_t)tc.ty * sbin;
-    int bvx = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (tw * 15 / 100) / std::max<int64_t>(1, step_x * kx)));
-    int bvy = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (th * 15 / 100) / std::max<int64_t>(1, step_y * ky)));
+    int bvx = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (tw * win_pct / 100) / std::max<int64_t>(1, step_x * kx)));
+    int bvy = (int)std::max<int64_t>(1, std::min<int64_t>(bv_cap, (th * win_pct / 100) / std::max<int64_t>(1, step_y * ky)));
     if (o.velocity_block) bvx = bvy = (int)std::min<uint32_t>(o.velocity_block, 8);
     // enough work units to fill the GPU: shrink the velocity block, then the tile
     const uint64_t units = (uint64_t)div_ceil_u32(d.nvx, kx * bvx) * div_ceil_u32(n_rows, ky * bvy) *
@@ -233,12 +238,18 @@ int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t,
   if (cb == 8 && n_min > 128) cb = 16;
   if (cb == 16 && n_min > 32768) cb = 32;
   const int kx = o.tile_kx ? (int)o.tile_kx : 8;
-  const int ky = o.tile_ky ? (int)o.tile_ky : 4;
+  int ky = o.tile_ky ? (int)o.tile_ky : 8;
   if (o.superbin > 4) return set_error(SAS_ERR_ARG, "superbin must be 0..4");
   const int sb = o.superbin ? (int)o.superbin : choose_superbin(d, n, n_min, v_end - v_begin);
   const int n_rows = (int)((v_end - 1) / d.nvx - v_begin / d.nvx + 1);
   Plan plan;
-  if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, nullptr, &plan)) return rc;
+  if (int rc = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, nullptr, &plan)) {
+    // the default 8 x 8 tile can exceed the staged coordinates' shift spread
+    // where 8 x 4 does not: fall back to it unless the caller chose the tile
+    if (o.tile_ky || ky != 8) return rc;
+    ky = 4;
+    if (int rc2 = choose_tiles(d, E, n, dT, tph, kx, ky, cb, sb, o, di, n_rows, nullptr, &plan)) return rc2;
+  }
   // Bucket grid: every detection that can project into the domain for some
   // lattice velocity and some dt in [0, dT] lies inside it.
   const int64_t vxa = d.vx0, vxb = (int64_t)d.vx0 + (int64_t)(d.nvx - 1) * d.dvx;

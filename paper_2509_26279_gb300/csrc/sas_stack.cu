@@ -102,6 +102,10 @@ __device__ inline uint32_t block_scan(uint32_t v, uint32_t* s_tmp, uint32_t& tot
   return r;
 }
 
+// Bit set of the lattice points of a velocity tile (bit ky * KX + kx).
+template <int KX, int KY>
+using Mask = typename std::conditional<(KX * KY > 32), uint64_t, uint32_t>::type;
+
 template <int CB>
 struct Counter {
   static constexpr int P = 32 / CB;  // counters per word
@@ -136,7 +140,7 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 const int32_t* __restrict__ oy,
                                                 uint32_t cells_s, uint32_t tw_x,
                                                 uint32_t tw_y, uint32_t magic, bool one, int tx,
-                                                int txty, uint32_t act, uint32_t w_in) {
+                                                int txty, Mask<KX, KY> act, uint32_t w_in) {
   using C = Counter<CB>;
   const uint32_t w = WT ? w_in : 1u;  // unweighted: a compile-time 1
   int32_t oxv[KX], oyv[KY];
@@ -202,10 +206,11 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
     }
     return (uint32_t)(__popc(okxb) * __popc(okyb));
   }
-  uint32_t m = 0;
+  using M = Mask<KX, KY>;
+  M m = 0;
 #pragma unroll
   for (int ky = 0; ky < KY; ++ky)
-    if ((okyb >> ky) & 1u) m |= okxb << (ky * KX);
+    if ((okyb >> ky) & 1u) m |= (M)okxb << (ky * KX);
   if (MASKED) m &= act;
   if constexpr (MERGE && C::P >= 2) {
     // The columns of one counter word project into at most two adjacent
@@ -226,7 +231,7 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
     for (int ky = 0; ky < KY; ++ky) {
 #pragma unroll
       for (int g = 0; g < KX / C::P; ++g) {
-        const uint32_t rb = (m >> (ky * KX + g * C::P)) & gmask;
+        const uint32_t rb = (uint32_t)(m >> (ky * KX + g * C::P)) & gmask;
         const uint32_t lo = spread_bits<CB>(rb & eqm[g]) * w, hi = spread_bits<CB>(rb & ~eqm[g]) * w;
         const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
         red_shared_if(lo, plane + col4[g * C::P], lo);
@@ -239,11 +244,12 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
 #pragma unroll
       for (int kx = 0; kx < KX; ++kx) {
         const uint32_t addr = rbase4[ky] + col4[kx] + (uint32_t)((ky * (KX / C::P) + kx / C::P) * txty * 4);
-        red_shared_if(m & (1u << (ky * KX + kx)), addr, w << (CB * (kx % C::P)));
+        red_shared_if((uint32_t)(m >> (ky * KX + kx)) & 1u, addr, w << (CB * (kx % C::P)));
       }
     }
   }
-  return (uint32_t)__popc(m);
+  if constexpr (sizeof(M) == 8) return (uint32_t)__popcll(m);
+  else return (uint32_t)__popc(m);
 }
 
 // Sum of the counters packed in one word.
@@ -273,7 +279,8 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
   uint32_t* s_seg_src = reinterpret_cast<uint32_t*>(smem + L.seg_src);
   Emit* s_emit = reinterpret_cast<Emit*>(smem + L.emit);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
-  // s_misc: [0..33) scan scratch, [42] active mask, [43] emission count,
+  // s_misc: [0..33) scan scratch, [42] active mask (points 0-31), [45] (points 32-63),
+  //         [43] emission count,
   //         [44] flush base
   const int tid = threadIdx.x;
   constexpr int P = C::P;
@@ -413,8 +420,9 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
     };
 
     // --- which lattice points of a velocity tile are searched ----------------
-    auto active_mask = [&](int kx0, int ky0) -> uint32_t {
-      if (tid < 32) {
+    auto active_mask = [&](int kx0, int ky0) -> Mask<KX, KY> {
+      constexpr int kWarpsM = (KX * KY + 31) / 32;
+      if (tid < 32 * kWarpsM) {
         bool act = false;
         if (tid < KX * KY) {
           const int kx = kx0 + tid % KX, ky = ky0 + tid / KX;
@@ -430,17 +438,19 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
           }
         }
         const uint32_t m = __ballot_sync(0xffffffffu, act);
-        if (tid == 0) s_misc[42] = m;
+        if ((tid & 31) == 0) s_misc[(tid >> 5) ? 45 : 42] = m;  // lattice points 0-31, 32-63
       }
       __syncthreads();
-      const uint32_t act = s_misc[42];
+      Mask<KX, KY> act = s_misc[42];
+      if constexpr (KX * KY > 32) act |= (Mask<KX, KY>)s_misc[45] << 32;
       __syncthreads();
       return act;
     };
 
     // --- run one velocity tile of the block against the staged records -------
-    auto compute = [&](int vtx, int vty, uint32_t act, uint32_t n_staged) {
-      const uint32_t full = (KX * KY == 32) ? 0xffffffffu : ((1u << (KX * KY)) - 1u);
+    auto compute = [&](int vtx, int vty, Mask<KX, KY> act, uint32_t n_staged) {
+      using M = Mask<KX, KY>;
+      const M full = (KX * KY == 8 * (int)sizeof(M)) ? ~(M)0 : (((M)1 << (KX * KY)) - 1);
       const int oxo = vtx * KX, oyo = vty * KY;
       uint32_t pairs = 0, added = 0;  // pairs, and the weight they added
       auto run = [&](auto masked, auto merge, auto weighted) {
@@ -534,7 +544,7 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       for (int vty = 0; vty < nvt_by; ++vty)
         for (int vtx = 0; vtx < nvt_bx; ++vtx) {
           const int kx0 = kxa + vtx * KX, ky0 = kya + vty * KY;
-          const uint32_t act = active_mask(kx0, ky0);
+          const auto act = active_mask(kx0, ky0);
           if (act == 0) continue;
           if (once) {
             compute(vtx, vty, act, ns_once);
@@ -551,7 +561,7 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       for (int vty = 0; vty < nvt_by; ++vty)
         for (int vtx = 0; vtx < nvt_bx; ++vtx) {
           const int kx0 = kxa + vtx * KX, ky0 = kya + vty * KY;
-          const uint32_t act = active_mask(kx0, ky0);
+          const auto act = active_mask(kx0, ky0);
           if (act == 0) continue;
           for (uint32_t e_base = 0; e_base < E; e_base += tc.ec) {
             const uint32_t D = prepare_chunk(e_base);
@@ -579,7 +589,7 @@ struct MultiArgs {
 template <int KX, int KY, int CB, bool MULTI>
 __global__ void __launch_bounds__(kNT, 1) k_stack(StackArgs a0, MultiArgs m) {
   static_assert(KX % (32 / CB) == 0, "kx must be a multiple of the counters per word");
-  static_assert(KX * KY <= 32, "at most 32 velocities per tile");
+  static_assert(KX * KY <= 64, "at most 64 velocities per tile");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ StackArgs s_args;
   __shared__ unsigned long long s_unit, s_local;
@@ -668,9 +678,9 @@ cudaError_t attr_t(size_t smem) {
 
 // Supported (KX, KY, CB) instantiations.
 #define SAS_STACK_CONFIGS(X) \
-  X(4, 1, 8) X(4, 2, 8) X(4, 4, 8) X(8, 2, 8) X(8, 4, 8) \
-  X(4, 1, 16) X(4, 2, 16) X(4, 4, 16) X(8, 2, 16) X(8, 4, 16) \
-  X(4, 1, 32) X(4, 2, 32) X(4, 4, 32) X(8, 2, 32) X(8, 4, 32)
+  X(4, 1, 8) X(4, 2, 8) X(4, 4, 8) X(8, 2, 8) X(8, 4, 8) X(8, 8, 8) \
+  X(4, 1, 16) X(4, 2, 16) X(4, 4, 16) X(8, 2, 16) X(8, 4, 16) X(8, 8, 16) \
+  X(4, 1, 32) X(4, 2, 32) X(4, 4, 32) X(8, 2, 32) X(8, 4, 32) X(8, 8, 32)
 
 }  // namespace
 

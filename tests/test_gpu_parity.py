@@ -86,6 +86,8 @@ def test_tiny_workload():
     dict(tile_bx=12, tile_by=8), dict(tile_bx=36, tile_by=20, coarse_bins=3),
     dict(coarse_bins=1), dict(coarse_bins=50), dict(tile_kx=8, tile_ky=4),
     dict(tile_kx=8, tile_ky=4, counter_bits=16, tile_bx=20, tile_by=28),
+    dict(tile_kx=8, tile_ky=8), dict(tile_kx=8, tile_ky=8, counter_bits=16),
+    dict(tile_kx=8, tile_ky=8, counter_bits=32, tile_bx=16, tile_by=12),
 ])
 def test_tile_configurations_agree(cfg):
     """Every tile shape, counter width and bucket size gives the same bytes."""
@@ -127,6 +129,22 @@ def test_speed_annulus_and_lattice_range():
     nv = w.grid.nvx * w.grid.nvy
     for a, b in [(0, 17), (5, nv // 2), (nv // 3, nv), (nv - 1, nv)]:
         res, ref = run_both(cat, w.grid, 9, v_begin=a, v_end=b)
+        assert_same(res, ref)
+
+
+def test_tall_tiles_with_annulus_ranges_and_ragged_edges():
+    """8 x 8 velocity tiles (64-bit lattice masks) on the masked paths: speed
+    annulus, index ranges that end mid-tile, a lattice that is not a multiple of 8."""
+    w = W.scaled(W.decam_tno(), frac_noise=0.03, width_px=500, height_px=600, n_movers=30,
+                 grid_half=10, seed=8)
+    cat = W.load(w)
+    o = sas.make_opts(tile_kx=8, tile_ky=8)
+    g = W.GridSpec(**{**w.grid.__dict__, "speed_min": 2000, "speed_max": 9000})
+    res, ref = run_both(cat, g, 9, opts=o)
+    assert_same(res, ref)
+    nv = w.grid.nvx * w.grid.nvy
+    for a, b in [(0, 17), (5, nv // 2), (nv // 3, nv), (nv - 1, nv)]:
+        res, ref = run_both(cat, w.grid, 9, opts=o, v_begin=a, v_end=b)
         assert_same(res, ref)
 
 
