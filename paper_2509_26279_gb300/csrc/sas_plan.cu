@@ -238,7 +238,8 @@ int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t,
   if (cb == 8 && n_min > 128) cb = 16;
   if (cb == 16 && n_min > 32768) cb = 32;
   const int kx = o.tile_kx ? (int)o.tile_kx : 8;
-  int ky = o.tile_ky ? (int)o.tile_ky : 8;
+  // 8 x 8 tiles for 8-bit counters; wider counters leave 8 x 8 tiles too little area
+  int ky = o.tile_ky ? (int)o.tile_ky : (cb == 8 ? 8 : 4);
   if (o.superbin > 4) return set_error(SAS_ERR_ARG, "superbin must be 0..4");
   const int sb = o.superbin ? (int)o.superbin : choose_superbin(d, n, n_min, v_end - v_begin);
   const int n_rows = (int)((v_end - 1) / d.nvx - v_begin / d.nvx + 1);
