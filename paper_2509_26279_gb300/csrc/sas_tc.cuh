@@ -26,6 +26,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kc) {
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
+// The same layout for 4-byte elements (TF32): a core-matrix row holds 4 of them.
+__host__ __device__ __forceinline__ uint32_t cm_offset4(int row, int k, int kc) {
+  return (uint32_t)(((row >> 3) * kc + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// Instruction descriptor of kind::tf32 (A and B read as TF32 from FP32, both
+// K-major) with an FP32 accumulator: formats 2 at bits 7 and 10.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major) and an
 // FP32 accumulator: N/8 at bit 17, M/16 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
@@ -52,6 +63,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+// D[tmem] (+)= A * B^T, M x N x 8 with TF32 operands, one thread.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 

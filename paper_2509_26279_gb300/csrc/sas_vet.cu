@@ -639,6 +639,172 @@ __global__ void __launch_bounds__(kBackThreads) k_conv_back(
   if (t < kCh) out[PARTS * kCh * C * 9 + t] = accb;
 }
 
+// ---- conv backward on the tensor cores (TF32) for the 32-channel layers ------
+//
+// Per block (a fixed set of stamps, so gradients stay bit-reproducible):
+//   dW[k = (c, tap)][o] += sum_p im2col(a)[k][p] * g[o][p]: M = 288 rows of k
+//     (three 128-row tiles, the last padded), N = 32, K = output pixels in
+//     chunks of 32; accumulated in TMEM across the block's stamps.
+//   dX[q][c] = sum_(o, tap) g[o][q - tap] * w[o][c][tap]: M = input pixels in
+//     128-row tiles, N = 32, K = 288 in chunks of 32; masked by the ReLU of the
+//     layer's input and written per stamp.
+// Operands are FP32 read as TF32 (activations and weights are BF16 values, so
+// exact; deltas round to TF32) in the no-swizzle K-major layout with 4-byte
+// elements; one thread issues the MMAs, completion through an mbarrier with a
+// bounded wait.  Bias gradients stay on the CUDA cores.
+constexpr int kBtThreads = 256;
+constexpr int kBtKCX = 9 * kCh / 4;                 // dX K (o, tap) = 288: 72 core matrices
+constexpr int kBtSmWb = 0;                           // [32 c][288] dX B operand (resident)
+constexpr int kBtSmA = kBtSmWb + kCh * 9 * kCh * 4;  // A chunk: 384 x 32 (dW) or up to 256 x 32 (dX)
+constexpr int kBtSmB = kBtSmA + 384 * 32 * 4;        // dW B chunk: 32 x 32
+constexpr int kBtSmG = kBtSmB + kCh * 32 * 4;        // g [32][P], then a [32][Q], then barrier
+
+template <int HI>
+constexpr size_t back_tc_smem() {
+  return (size_t)kBtSmG + (size_t)kCh * (HI - 2) * (HI - 2) * 4 + (size_t)kCh * HI * HI * 4 + 16;
+}
+
+template <int HI>
+__global__ void __launch_bounds__(kBtThreads, 1) k_conv_back_tc(
+    const float* __restrict__ gin, const __nv_bfloat16* __restrict__ ain, uint32_t n,
+    const __nv_bfloat16* __restrict__ w, float* __restrict__ gout, float* __restrict__ partial,
+    uint32_t* __restrict__ status) {
+  constexpr int C = kCh, HO = HI - 2, P = HO * HO, Q = HI * HI;
+  constexpr int NCW = (P + 31) / 32, MQ = (Q + 127) / 128, KC = 8;
+  static_assert(MQ * 128 <= 384, "dX tile fits the A buffer");
+  extern __shared__ __align__(1024) unsigned char smb[];
+  unsigned char* Wb = smb + kBtSmWb;
+  unsigned char* Ab = smb + kBtSmA;
+  unsigned char* Bb = smb + kBtSmB;
+  float* g_s = reinterpret_cast<float*>(smb + kBtSmG);
+  float* a_s = g_s + C * P;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(a_s + C * Q);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(tslot, 256);  // dW: columns [0, 96), dX: [128, 128 + 32 MQ)
+  if (tid == 0) tc::mbar_init(bar, 1);
+  for (int i = tid; i < C * 9 * C; i += kBtThreads) {  // Wb[c][(o, tap)] = w[o][c][tap]
+    const int c = i / (9 * C), K = i - c * 9 * C, o = K / 9, tap = K - o * 9;
+    *reinterpret_cast<float*>(Wb + tc::cm_offset4(c, K, kBtKCX)) = ld(w + (o * C + c) * 9 + tap);
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const uint32_t a0 = tc::smem_u32(Ab), b0 = tc::smem_u32(Bb), wb0 = tc::smem_u32(Wb);
+  constexpr uint32_t idesc = tc::idesc_tf32(128, 32);
+  uint32_t phase = 0;
+  float accb = 0.f;
+  bool any = false, ok = true;
+  // one chunk of MMAs issued by thread 0, then everyone waits for them
+  auto run = [&](auto issue) -> bool {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue();
+      tc::commit(bar);
+    }
+    const bool done = tc::mbar_wait(bar, phase, 1u << 22);
+    phase ^= 1u;
+    return !__syncthreads_or(!done);
+  };
+  for (uint32_t b = blockIdx.x; b < n && ok; b += gridDim.x) {
+    for (int i = tid; i < C * P; i += kBtThreads) g_s[i] = gin[(size_t)b * C * P + i];
+    for (int i = tid; i < C * Q; i += kBtThreads) a_s[i] = ld(ain + (size_t)b * C * Q + i);
+    __syncthreads();
+    if (tid < C)
+      for (int p = 0; p < P; ++p) accb += g_s[tid * P + p];
+    // dW: im2col(a)^T x g over chunks of 32 output pixels
+    for (int ch = 0; ch < NCW && ok; ++ch) {
+      const int p0 = ch * 32;
+      for (int i = tid; i < 384 * 32; i += kBtThreads) {
+        const int k = i >> 5, kk = i & 31, p = p0 + kk;
+        float v = 0.f;
+        if (k < 9 * C && p < P) {
+          const int c = k / 9, tap = k - c * 9, y = p / HO, x = p - y * HO;
+          v = a_s[c * Q + (y + tap / 3) * HI + x + tap % 3];
+        }
+        *reinterpret_cast<float*>(Ab + tc::cm_offset4(k, kk, KC)) = v;
+      }
+      for (int i = tid; i < C * 32; i += kBtThreads) {
+        const int o = i >> 5, kk = i & 31, p = p0 + kk;
+        *reinterpret_cast<float*>(Bb + tc::cm_offset4(o, kk, KC)) = p < P ? g_s[o * P + p] : 0.f;
+      }
+      const uint32_t acc0 = (any || ch > 0) ? 1u : 0u;
+      ok = run([&] {
+        for (int mt = 0; mt < 3; ++mt)
+          for (int ks = 0; ks < 4; ++ks)
+            tc::mma_tf32(tmem + (uint32_t)(mt * 32), tc::smem_desc(a0 + (uint32_t)(mt * 16 * KC * 128 + ks * 256), KC),
+                         tc::smem_desc(b0 + (uint32_t)(ks * 256), KC), idesc, (acc0 | (uint32_t)ks) ? 1u : 0u);
+      });
+    }
+    any = true;
+    // dX: im2col(g) x w over chunks of 32 of (o, tap)
+    for (int ch = 0; ch < 9 && ok; ++ch) {
+      for (int i = tid; i < MQ * 128 * 32; i += kBtThreads) {
+        const int q = i >> 5, kk = i & 31, K = ch * 32 + kk, o = K / 9, tap = K - o * 9;
+        float v = 0.f;
+        if (q < Q) {
+          const int yi = q / HI, xi = q - yi * HI, yo = yi - tap / 3, xo = xi - tap % 3;
+          if (yo >= 0 && yo < HO && xo >= 0 && xo < HO) v = g_s[o * P + yo * HO + xo];
+        }
+        *reinterpret_cast<float*>(Ab + tc::cm_offset4(q, kk, KC)) = v;
+      }
+      ok = run([&] {
+        for (int mt = 0; mt < MQ; ++mt)
+          for (int ks = 0; ks < 4; ++ks)
+            tc::mma_tf32(tmem + (uint32_t)(128 + mt * 32),
+                         tc::smem_desc(a0 + (uint32_t)(mt * 16 * KC * 128 + ks * 256), KC),
+                         tc::smem_desc(wb0 + (uint32_t)(ch * 8 * 128 + ks * 256), kBtKCX), idesc,
+                         (ch > 0 || ks > 0) ? 1u : 0u);
+      });
+    }
+    if (!ok) break;
+    tc::fence_after_sync();
+    {  // dX epilogue: warp w reads lane quadrant w % 4, columns 16 (w / 4) .. + 15
+      const int q4 = warp & 3, h = warp >> 2;
+      float* go = gout + (size_t)b * C * Q;
+      for (int mt = 0; mt < MQ; ++mt) {
+        float v[16];
+        tc::ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(128 + mt * 32 + h * 16), v);
+        const int q = mt * 128 + q4 * 32 + lane;
+        if (q < Q) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int c = h * 16 + j;
+            go[c * Q + q] = a_s[c * Q + q] > 0.f ? v[j] : 0.f;
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // g_s, a_s and the dX columns are free for the next stamp
+  }
+  if (!ok && tid == 0) atomicOr(status, 1u);
+  tc::fence_after_sync();
+  float* out = partial + (size_t)blockIdx.x * kPartialStride;  // [32 o][C][9], then [32] biases
+  if (ok) {
+    const int q4 = warp & 3, h = warp >> 2;
+    for (int mt = 0; mt < 3; ++mt) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(mt * 32 + h * 16), v);
+      const int k = mt * 128 + q4 * 32 + lane;
+      if (k < 9 * C) {
+        const int c = k / 9, tap = k - c * 9;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[((h * 16 + j) * C + c) * 9 + tap] = any ? v[j] : 0.f;
+      }
+    }
+  }
+  if (tid < C) out[C * C * 9 + tid] = accb;
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 256);
+}
+
 // grad[w_off + i] = sum over blocks and parts of the partial weight sums;
 // grad[b_off + o] likewise for the biases.  Fixed summation order.
 __global__ void k_reduce_partials(const float* __restrict__ partial, int n_blocks, int parts, int nw,
@@ -695,11 +861,11 @@ cudaError_t set_attrs() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fc_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFcTcSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_back<kCh, kH2, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)back_smem<kCh, kH2, true>());
+    e = cudaFuncSetAttribute(k_conv_back_tc<kH2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)back_tc_smem<kH2>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_back<kCh, kH1, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)back_smem<kCh, kH1, true>());
+    e = cudaFuncSetAttribute(k_conv_back_tc<kH1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)back_tc_smem<kH1>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_back<kQ, kS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)back_smem<kQ, kS, false>());
@@ -743,12 +909,12 @@ cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, 
   k_fc1_dw<<<(kF + 31) / 32, 256, 0, s>>>(vt->g4, vt->a3, n, grad);
   k_fc1_dx<<<dim3((kF + 63) / 64, (n + 31) / 32), 256, 0, s>>>(vt->g4, vt->wb, vt->a3, n, vt->g3);
   const int nb = (int)std::min<uint32_t>(n, kBackBlocks);
-  k_conv_back<kCh, kH2, true, false><<<nb, kBackThreads, back_smem<kCh, kH2, true>(), s>>>(
-      vt->g3, vt->a2, nullptr, nullptr, n, vt->wb + kW3, vt->g2, vt->partial);
+  k_conv_back_tc<kH2><<<nb, kBtThreads, back_tc_smem<kH2>(), s>>>(vt->g3, vt->a2, n, vt->wb + kW3, vt->g2,
+                                                                   vt->partial, vt->status);
   k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW3, kB3);
-  k_conv_back<kCh, kH1, true, false><<<nb, kBackThreads, back_smem<kCh, kH1, true>(), s>>>(
-      vt->g2, vt->a1, nullptr, nullptr, n, vt->wb + kW2, vt->g1, vt->partial);
+  k_conv_back_tc<kH1><<<nb, kBtThreads, back_tc_smem<kH1>(), s>>>(vt->g2, vt->a1, n, vt->wb + kW2, vt->g1,
+                                                                   vt->partial, vt->status);
   k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW2, kB2);
   k_conv_back<kQ, kS, false, true><<<nb, kBackThreads, back_smem<kQ, kS, false>(), s>>>(
