@@ -659,6 +659,12 @@ constexpr int kBtSmA = kBtSmWb + kCh * 9 * kCh * 4;  // A chunk: 384 x 32 (dW) o
 constexpr int kBtSmB = kBtSmA + 384 * 32 * 4;        // dW B chunk: 32 x 32
 constexpr int kBtSmG = kBtSmB + kCh * 32 * 4;        // g [32][P], then a [32][Q], then barrier
 
+// Position i of a 4-byte-element operand with 32 K per row (8 core matrices
+// per row group) in the no-swizzle K-major layout: its row and k, so that
+// cm_offset4(cm_row(i), cm_k(i), 8) == 4 i.
+__device__ __forceinline__ int cm_row(int i) { return (i >> 8) * 8 + ((i >> 2) & 7); }
+__device__ __forceinline__ int cm_k(int i) { return ((i >> 5) & 7) * 4 + (i & 3); }
+
 template <int HI>
 constexpr size_t back_tc_smem() {
   return (size_t)kBtSmG + (size_t)kCh * (HI - 2) * (HI - 2) * 4 + (size_t)kCh * HI * HI * 4 + 16;
@@ -720,18 +726,20 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_conv_back_tc(
     // dW: im2col(a)^T x g over chunks of 32 output pixels
     for (int ch = 0; ch < NCW && ok; ++ch) {
       const int p0 = ch * 32;
+      // buffers are filled in memory order (a warp writes one 128-byte core
+      // matrix): element i is (row, k) = cm_row(i), cm_k(i)
       for (int i = tid; i < 384 * 32; i += kBtThreads) {
-        const int k = i >> 5, kk = i & 31, p = p0 + kk;
+        const int k = cm_row(i), kk = cm_k(i), p = p0 + kk;
         float v = 0.f;
         if (k < 9 * C && p < P) {
           const int c = k / 9, tap = k - c * 9, y = p / HO, x = p - y * HO;
           v = a_s[c * Q + (y + tap / 3) * HI + x + tap % 3];
         }
-        *reinterpret_cast<float*>(Ab + tc::cm_offset4(k, kk, KC)) = v;
+        reinterpret_cast<float*>(Ab)[i] = v;
       }
       for (int i = tid; i < C * 32; i += kBtThreads) {
-        const int o = i >> 5, kk = i & 31, p = p0 + kk;
-        *reinterpret_cast<float*>(Bb + tc::cm_offset4(o, kk, KC)) = p < P ? g_s[o * P + p] : 0.f;
+        const int o = cm_row(i), p = p0 + cm_k(i);
+        reinterpret_cast<float*>(Bb)[i] = p < P ? g_s[o * P + p] : 0.f;
       }
       const uint32_t acc0 = (any || ch > 0) ? 1u : 0u;
       ok = run([&] {
@@ -745,13 +753,13 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_conv_back_tc(
     // dX: im2col(g) x w over chunks of 32 of (o, tap)
     for (int ch = 0; ch < 9 && ok; ++ch) {
       for (int i = tid; i < MQ * 128 * 32; i += kBtThreads) {
-        const int q = i >> 5, kk = i & 31, K = ch * 32 + kk, o = K / 9, tap = K - o * 9;
+        const int q = cm_row(i), K = ch * 32 + cm_k(i), o = K / 9, tap = K - o * 9;
         float v = 0.f;
         if (q < Q) {
           const int yi = q / HI, xi = q - yi * HI, yo = yi - tap / 3, xo = xi - tap % 3;
           if (yo >= 0 && yo < HO && xo >= 0 && xo < HO) v = g_s[o * P + yo * HO + xo];
         }
-        *reinterpret_cast<float*>(Ab + tc::cm_offset4(q, kk, KC)) = v;
+        reinterpret_cast<float*>(Ab)[i] = v;
       }
       ok = run([&] {
         for (int mt = 0; mt < MQ; ++mt)
