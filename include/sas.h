@@ -511,8 +511,11 @@ int sas_param_dx_scan(double nu, double nu_th, const double* a, uint32_t n_epoch
  *   fc2.w [64], fc2.b [1].
  * Arithmetic: the kernels use BF16 copies of the weights (round to nearest
  * even), round the input and every stored activation to BF16 and accumulate
- * in FP32 (the convolutions of the forward pass on the tensor cores, tcgen05); deltas and gradients are FP32; Adam updates the FP32 masters and
- * refreshes the BF16 copies.  Gradients are bit-reproducible for a batch.
+ * in FP32.  The forward convolutions and fc1 run on the tensor cores (tcgen05,
+ * BF16 operands); deltas and gradients are FP32, and the backward of conv2 and
+ * conv3 runs on the tensor cores with TF32 operands (the deltas round to TF32
+ * there).  Adam updates the FP32 masters and refreshes the BF16 copies.
+ * Gradients are bit-reproducible for a batch.
  * A vetter lives on the device that was current at sas_vet_create; every call
  * makes that device current for its duration. */
 #define SAS_VET_MAX_BATCH 8192u
