@@ -529,35 +529,26 @@ __global__ void __launch_bounds__(256) k_fc1_dx(const float* __restrict__ g4,
   }
 }
 
-// ---- conv backward: weight gradients and (masked) input deltas ---------------
+// ---- conv1 weight gradient (CUDA cores) -----------------------------------------
 
 constexpr int kBackThreads = 256;
 
-// Layer with C input channels of HI x HI (output 32 x HO x HO).  gin: the
-// masked delta of this layer's output [n][32][HO*HO]; ain: its input
-// activations [n][C][HI*HI] (BF16), or the stamps for the first layer.
-// With DX, gout[n][C][HI*HI] = (sum over o, taps of gin * w) * (ain > 0).
-// Block partial (at partial + blockIdx.x * kPartialStride):
-//   [parts][32][C][9] weight sums, then [32] bias sums.
-template <int C, int HI, bool DX, bool STAMP>
-__global__ void __launch_bounds__(kBackThreads) k_conv_back(
-    const float* __restrict__ gin, const __nv_bfloat16* __restrict__ ain,
-    const uint16_t* __restrict__ stamps, const uint32_t* __restrict__ idx, uint32_t n,
-    const __nv_bfloat16* __restrict__ w, float* __restrict__ gout, float* __restrict__ partial) {
+// The first layer (C = 9 input channels of HI x HI, output 32 x HO x HO): gin
+// is the masked delta of its output [n][32][HO*HO], its input the stamps (no
+// input delta is needed).  Block partial (at partial + blockIdx.x *
+// kPartialStride): [parts][32][C][9] weight sums, then [32] bias sums.
+template <int C, int HI>
+__global__ void __launch_bounds__(kBackThreads) k_conv1_dw(const float* __restrict__ gin,
+                                                           const uint16_t* __restrict__ stamps,
+                                                           const uint32_t* __restrict__ idx, uint32_t n,
+                                                           float* __restrict__ partial) {
   constexpr int HO = HI - 2, P = HO * HO, Q = HI * HI;
-  constexpr int PARTS = kBackThreads / (8 * C);  // 1 for C = 32, 3 for C = 9
+  constexpr int PARTS = kBackThreads / (8 * C);  // 3 for C = 9
   static_assert(PARTS >= 1, "too many channels");
   extern __shared__ __align__(16) float sm[];
   float* g_s = sm;             // [32][P]
   float* a_s = g_s + kCh * P;  // [C][Q]
-  float* w_s = a_s + C * Q;    // [32][9][C]  (DX only)
   const int t = threadIdx.x;
-  if (DX) {
-    for (int i = t; i < kCh * C * 9; i += blockDim.x) {
-      const int o = i / (C * 9), r = i - o * C * 9, c = r / 9, tap = r % 9;
-      w_s[(o * 9 + tap) * C + c] = ld(w + i);
-    }
-  }
   // weight-gradient ownership: (4 output channels, 1 input channel, 1 pixel part)
   const int c_own = t % C, oq = (t / C) % 8, part = t / (8 * C);
   const bool owner = part < PARTS;
@@ -570,12 +561,8 @@ __global__ void __launch_bounds__(kBackThreads) k_conv_back(
   for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
     __syncthreads();
     for (int i = t; i < kCh * P; i += blockDim.x) g_s[i] = gin[(size_t)b * kCh * P + i];
-    if (STAMP) {
-      for (int i = t; i < C * Q; i += blockDim.x)
-        a_s[i] = bf((float)stamps[(size_t)(idx ? idx[b] : b) * C * Q + i] * 0.0625f);
-    } else {
-      for (int i = t; i < C * Q; i += blockDim.x) a_s[i] = ld(ain + (size_t)b * C * Q + i);
-    }
+    for (int i = t; i < C * Q; i += blockDim.x)
+      a_s[i] = bf((float)stamps[(size_t)(idx ? idx[b] : b) * C * Q + i] * 0.0625f);
     __syncthreads();
     if (owner) {
       for (int p = part; p < P; p += PARTS) {
@@ -594,38 +581,6 @@ __global__ void __launch_bounds__(kBackThreads) k_conv_back(
     }
     if (t < kCh) {
       for (int p = 0; p < P; ++p) accb += g_s[t * P + p];
-    }
-    if (DX) {
-      const int warp = t >> 5, lane = t & 31;
-      constexpr int CQ = C / 4;  // channel quads
-      for (int cq = warp; cq < CQ; cq += kBackThreads / 32) {
-        for (int q = lane; q < Q; q += 32) {
-          const int yi = q / HI, xi = q - yi * HI;
-          float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-          for (int o = 0; o < kCh; ++o) {
-#pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-              const int yo = yi - dy;
-              if (yo < 0 || yo >= HO) continue;
-#pragma unroll
-              for (int dx = 0; dx < 3; ++dx) {
-                const int xo = xi - dx;
-                if (xo < 0 || xo >= HO) continue;
-                const float gg = g_s[o * P + yo * HO + xo];
-                const float4 ww = *reinterpret_cast<const float4*>(w_s + (o * 9 + dy * 3 + dx) * C + cq * 4);
-                d0 = fmaf(gg, ww.x, d0); d1 = fmaf(gg, ww.y, d1);
-                d2 = fmaf(gg, ww.z, d2); d3 = fmaf(gg, ww.w, d3);
-              }
-            }
-          }
-          float* go = gout + (size_t)b * C * Q;
-          const int c = cq * 4;
-          go[(c + 0) * Q + q] = a_s[(c + 0) * Q + q] > 0.f ? d0 : 0.f;
-          go[(c + 1) * Q + q] = a_s[(c + 1) * Q + q] > 0.f ? d1 : 0.f;
-          go[(c + 2) * Q + q] = a_s[(c + 2) * Q + q] > 0.f ? d2 : 0.f;
-          go[(c + 3) * Q + q] = a_s[(c + 3) * Q + q] > 0.f ? d3 : 0.f;
-        }
-      }
     }
   }
   float* out = partial + (size_t)blockIdx.x * kPartialStride;
@@ -815,12 +770,14 @@ __global__ void __launch_bounds__(kBtThreads, 1) k_conv_back_tc(
 
 // grad[w_off + i] = sum over blocks and parts of the partial weight sums;
 // grad[b_off + o] likewise for the biases.  Fixed summation order.
+// One warp per element: lane l adds blocks l, l + 32, ... in order, then the
+// lanes combine in a fixed xor pattern.
 __global__ void k_reduce_partials(const float* __restrict__ partial, int n_blocks, int parts, int nw,
                                   float* __restrict__ grad, int w_off, int b_off) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nw + kCh) return;
+  const int i = (int)((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= nw + kCh) return;  // whole warps leave together
   float s = 0.f;
-  for (int blk = 0; blk < n_blocks; ++blk) {
+  for (int blk = lane; blk < n_blocks; blk += 32) {
     const float* p = partial + (size_t)blk * kPartialStride;
     if (i < nw) {
       for (int q = 0; q < parts; ++q) s += p[(size_t)q * nw + i];
@@ -828,7 +785,9 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_block
       s += p[(size_t)parts * nw + (i - nw)];
     }
   }
-  grad[i < nw ? w_off + i : b_off + (i - nw)] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) grad[i < nw ? w_off + i : b_off + (i - nw)] = s;
 }
 
 // ---- parameters --------------------------------------------------------------
@@ -857,9 +816,9 @@ __global__ void k_adam(float* __restrict__ master, float* __restrict__ m, float*
 
 // ---- host side -----------------------------------------------------------------
 
-template <int C, int HI, bool DX>
-constexpr size_t back_smem() {
-  return sizeof(float) * ((size_t)kCh * (HI - 2) * (HI - 2) + (size_t)C * HI * HI + (DX ? (size_t)kCh * 9 * C : 0));
+template <int C, int HI>
+constexpr size_t conv1_dw_smem() {
+  return sizeof(float) * ((size_t)kCh * (HI - 2) * (HI - 2) + (size_t)C * HI * HI);
 }
 
 cudaError_t set_attrs() {
@@ -875,8 +834,8 @@ cudaError_t set_attrs() {
     e = cudaFuncSetAttribute(k_conv_back_tc<kH1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)back_tc_smem<kH1>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_conv_back<kQ, kS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)back_smem<kQ, kS, false>());
+    e = cudaFuncSetAttribute(k_conv1_dw<kQ, kS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)conv1_dw_smem<kQ, kS>());
   if (e == cudaSuccess) done = true;
   return e;
 }
@@ -919,15 +878,14 @@ cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, 
   const int nb = (int)std::min<uint32_t>(n, kBackBlocks);
   k_conv_back_tc<kH2><<<nb, kBtThreads, back_tc_smem<kH2>(), s>>>(vt->g3, vt->a2, n, vt->wb + kW3, vt->g2,
                                                                    vt->partial, vt->status);
-  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
+  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 7) / 8, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW3, kB3);
   k_conv_back_tc<kH1><<<nb, kBtThreads, back_tc_smem<kH1>(), s>>>(vt->g2, vt->a1, n, vt->wb + kW2, vt->g1,
                                                                    vt->partial, vt->status);
-  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 255) / 256, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
+  k_reduce_partials<<<(kCh * kCh * 9 + kCh + 7) / 8, 256, 0, s>>>(vt->partial, nb, 1, kCh * kCh * 9,
                                                                       grad, kW2, kB2);
-  k_conv_back<kQ, kS, false, true><<<nb, kBackThreads, back_smem<kQ, kS, false>(), s>>>(
-      vt->g1, nullptr, stamps, idx, n, vt->wb + kW1, nullptr, vt->partial);
-  k_reduce_partials<<<(kCh * kQ * 9 + kCh + 255) / 256, 256, 0, s>>>(
+  k_conv1_dw<kQ, kS><<<nb, kBackThreads, conv1_dw_smem<kQ, kS>(), s>>>(vt->g1, stamps, idx, n, vt->partial);
+  k_reduce_partials<<<(kCh * kQ * 9 + kCh + 7) / 8, 256, 0, s>>>(
       vt->partial, nb, kBackThreads / (8 * kQ), kCh * kQ * 9, grad, kW1, kB1);
   note_launch(10);
   return cudaGetLastError();
