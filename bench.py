@@ -70,7 +70,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples (the summary goes into the bench line): SAS_CLOCKS_DIR, else a temp dir
+        import tempfile
+        self.path = os.path.join(os.environ.get("SAS_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"sas_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
