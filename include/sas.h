@@ -200,7 +200,9 @@ int sas_result_get_info(const sas_result* result, sas_result_info* info);
  * and *n_ids_total (either may be NULL) receive the full sizes.  With
  * on_device = 1 the destinations are device pointers.  Returns
  * SAS_ERR_OVERFLOW (after the partial copy) when cap or ids_cap is too small;
- * out or ids may be NULL with cap or ids_cap 0 to query sizes. */
+ * out or ids may be NULL with cap or ids_cap 0 to query sizes.  Both copies
+ * are issued together and waited for once; page-locked host destinations
+ * (reused from call to call) copy fastest. */
 int sas_candidates(const sas_result* result, sas_candidate* out, uint64_t cap,
                    uint64_t* n_total, uint32_t* ids, uint64_t ids_cap,
                    uint64_t* n_ids_total, int on_device);

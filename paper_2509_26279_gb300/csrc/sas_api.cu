@@ -526,15 +526,21 @@ int sas_candidates(const sas_result* r, sas_candidate* out, uint64_t cap, uint64
   if (n_ids_total) *n_ids_total = ni;
   const uint64_t c1 = std::min(cap, nc), i1 = std::min(ids_cap, ni);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (c1 && !out) return fail(SAS_ERR_ARG, "null candidate buffer");
+  if (i1 && !ids) return fail(SAS_ERR_ARG, "null id buffer");
+  // both copies on the legacy default stream (the search completed before it
+  // returned), then one wait
   if (c1) {
-    if (!out) return fail(SAS_ERR_ARG, "null candidate buffer");
-    cudaError_t e = cudaMemcpy(out, r->d_cands, c1 * sizeof(sas_candidate), kind);
+    cudaError_t e = cudaMemcpyAsync(out, r->d_cands, c1 * sizeof(sas_candidate), kind, 0);
     if (e != cudaSuccess) return cuda_fail(e, "copy candidates");
   }
   if (i1) {
-    if (!ids) return fail(SAS_ERR_ARG, "null id buffer");
-    cudaError_t e = cudaMemcpy(ids, r->d_ids, i1 * sizeof(uint32_t), kind);
+    cudaError_t e = cudaMemcpyAsync(ids, r->d_ids, i1 * sizeof(uint32_t), kind, 0);
     if (e != cudaSuccess) return cuda_fail(e, "copy ids");
+  }
+  if (c1 || i1) {
+    cudaError_t e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy candidates");
   }
   if (cap < nc || ids_cap < ni)
     return fail(SAS_ERR_OVERFLOW, "buffers too small: need %llu candidates and %llu ids",

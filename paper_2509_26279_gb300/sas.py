@@ -169,17 +169,27 @@ class Result:
         _check(_lib.sas_result_get_info(self._h, ctypes.byref(inf)))
         return {k: getattr(inf, k) for k, _ in sas_result_info._fields_}
 
-    def candidates(self):
-        """(candidates: structured array of CANDIDATE_DTYPE, ids: uint32 array)."""
+    def candidates(self, out=None):
+        """(candidates: structured array of CANDIDATE_DTYPE, ids: uint32 array).
+        out = (cands, ids): caller-owned contiguous host arrays of those dtypes
+        (page-locked ones copy fastest) to fill instead of new arrays; the
+        returned arrays are their leading parts.  SasError when one is too
+        small."""
         nc, ni = ctypes.c_uint64(), ctypes.c_uint64()
         inf = self.info()
         nc_v, ni_v = inf["n_candidates"], inf["n_ids"]
-        cands = np.zeros(nc_v, CANDIDATE_DTYPE)
-        ids = np.zeros(ni_v, np.uint32)
-        _check(_lib.sas_candidates(self._h, cands.ctypes.data if nc_v else None, nc_v,
-                                   ctypes.byref(nc), ids.ctypes.data if ni_v else None, ni_v,
+        if out is None:
+            cands = np.zeros(nc_v, CANDIDATE_DTYPE)
+            ids = np.zeros(ni_v, np.uint32)
+        else:
+            cands, ids = out
+            if (cands.dtype != CANDIDATE_DTYPE or ids.dtype != np.uint32 or not cands.flags.c_contiguous
+                    or not ids.flags.c_contiguous):
+                raise SasError(SAS_ERR_ARG, "out: contiguous CANDIDATE_DTYPE and uint32 arrays")
+        _check(_lib.sas_candidates(self._h, cands.ctypes.data if nc_v else None, len(cands) if nc_v else 0,
+                                   ctypes.byref(nc), ids.ctypes.data if ni_v else None, len(ids) if ni_v else 0,
                                    ctypes.byref(ni), 0))
-        return cands, ids
+        return cands[:nc_v], ids[:ni_v]
 
     def candidates_into(self, cands_dev, ids_dev, cap: int, ids_cap: int):
         """Copy into caller-owned device buffers (sas_candidates with on_device=1)."""

@@ -232,6 +232,32 @@ def test_device_resident_inputs_match_host_inputs():
     assert gpu_tuples(res) == host
 
 
+def test_candidates_into_reused_pinned_host_buffers():
+    """candidates(out=...) fills caller-owned page-locked arrays with the same
+    bytes as fresh arrays, across results, and refuses buffers that are too
+    small or of the wrong type."""
+    w = W.tiny()
+    cat = W.load(w)
+    g = sas.Grid(w.grid)
+    res = sas.stack_catalog(g, cat, w.n_min)
+    want_c, want_i = res.candidates()
+    assert len(want_c) > 0
+    hc = torch.empty((len(want_c) + 5) * sas.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    hi = torch.empty(len(want_i) + 7, dtype=torch.int32).pin_memory()
+    out = (hc.numpy().view(sas.CANDIDATE_DTYPE), hi.numpy().view(np.uint32))
+    for _ in range(2):                     # reuse the same buffers for a second result
+        r = sas.stack_catalog(g, cat, w.n_min)
+        c, i = r.candidates(out=out)
+        assert c.tobytes() == want_c.tobytes() and np.array_equal(i, want_i)
+        r.free()
+    with pytest.raises(sas.SasError) as ei:
+        res.candidates(out=(out[0][:len(want_c) - 1], out[1]))
+    assert ei.value.status == sas.SAS_ERR_OVERFLOW
+    with pytest.raises(sas.SasError) as ei:
+        res.candidates(out=(out[0], out[1].view(np.int32)))
+    assert ei.value.status == sas.SAS_ERR_ARG
+
+
 def test_range_errors():
     g = sas.Grid(W.tiny().grid)
     bad_epoch = cases.catalog([1, 2], [1, 2], [0, 5], [0, 10], 3600)
