@@ -112,13 +112,18 @@ struct Counter {
   static constexpr uint32_t CMASK = CB == 32 ? 0xffffffffu : ((1u << CB) - 1u);
 };
 
-// One staged detection against every velocity of the tile (Sec. 2.1 steps 1-2).
-// ox/oy hold the tile origin plus the shift of each lattice column/row, relative
-// to the same window origin as the staged coordinates, so X = xr - ox[k] is the
-// projected position relative to the tile origin.  Returns the number of
-// (detection, velocity) pairs that landed in the tile.
+// Unconditional shared-memory reduction.  On the merged paths (the usual
+// ones) lanes with nothing to add give a zero increment at a harmless address
+// instead of a predicate: predicated reductions measured one divergent branch
+// each per warp.
+__device__ __forceinline__ void red_shared(uint32_t addr, uint32_t inc) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(inc));
+}
+
 // Predicated shared-memory reduction: adds inc to the word at shared address
-// addr when pred is nonzero, without a branch.
+// addr when pred is nonzero (the per-lattice-point path, taken only when the
+// planner cannot prove the merged reductions' two-run property; the zero-add
+// form spills registers there).
 __device__ __forceinline__ void red_shared_if(uint32_t pred, uint32_t addr, uint32_t inc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, 0;\n\t@p red.shared.add.u32 [%1], %2;\n\t}" ::"r"(pred),
@@ -134,6 +139,11 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t b) {
   else return b;
 }
 
+// One staged detection against every velocity of the tile (Sec. 2.1 steps 1-2).
+// ox/oy hold the tile origin plus the shift of each lattice column/row, relative
+// to the same window origin as the staged coordinates, so X = xr - ox[k] is the
+// projected position relative to the tile origin.  Returns the number of
+// (detection, velocity) pairs that landed in the tile.
 template <int KX, int KY, int CB, bool MASKED, bool MERGE, bool WT>
 __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 const int32_t* __restrict__ ox,
@@ -143,6 +153,9 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
                                                 int txty, Mask<KX, KY> act, uint32_t w_in) {
   using C = Counter<CB>;
   const uint32_t w = WT ? w_in : 1u;  // unweighted: a compile-time 1
+  // where a lane adds zero: one counter word per lane, in distinct banks (the
+  // tile holds at least 32 words); adding zero changes no counter
+  const uint32_t safe = cells_s + 4u * (threadIdx.x & 31u);
   int32_t oxv[KX], oyv[KY];
   if constexpr (KX % 4 == 0) {
 #pragma unroll
@@ -200,8 +213,8 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
       for (int g = 0; g < KX / C::P; ++g) {
         const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
         const uint32_t a = row ? lo[g] : 0u, b = row ? hi[g] : 0u;
-        red_shared_if(a, plane + col4[g * C::P], a);
-        red_shared_if(b, plane + col4[g * C::P + C::P - 1], b);
+        red_shared(a ? plane + col4[g * C::P] : safe, a);
+        red_shared(b ? plane + col4[g * C::P + C::P - 1] : safe, b);
       }
     }
     return (uint32_t)(__popc(okxb) * __popc(okyb));
@@ -234,8 +247,8 @@ __device__ __forceinline__ uint32_t process_rec(uint32_t xr, uint32_t yr,
         const uint32_t rb = (uint32_t)(m >> (ky * KX + g * C::P)) & gmask;
         const uint32_t lo = spread_bits<CB>(rb & eqm[g]) * w, hi = spread_bits<CB>(rb & ~eqm[g]) * w;
         const uint32_t plane = rbase4[ky] + (uint32_t)((ky * (KX / C::P) + g) * txty * 4);
-        red_shared_if(lo, plane + col4[g * C::P], lo);
-        red_shared_if(hi, plane + col4[g * C::P + C::P - 1], hi);
+        red_shared(lo ? plane + col4[g * C::P] : safe, lo);
+        red_shared(hi ? plane + col4[g * C::P + C::P - 1] : safe, hi);
       }
     }
   } else {
