@@ -12,7 +12,8 @@ N_min = 25.  The metric is detection-shifts per second: in-domain
             the library launches on, L2 flushed (256 MiB write) between steps
   e2e       the same search through the C ABI with pinned host buffers: the
             host->device copy of the catalog and the device->host copy of the
-            candidates and ids are inside the timed region (wall clock)
+            candidates and ids (into page-locked arrays allocated once and
+            reused) are inside the timed region (wall clock)
   roofline  the stack kernel against the shared-memory atomic peak measured in
             this run by the library's probe (one atomic per detection-shift)
 
