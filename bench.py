@@ -517,7 +517,8 @@ def main():
         r = dev_step()
         info0 = r.info()
         r.free()
-    peak_ops, probe_mhz = sas.sas_probe_shared_atomic_peak(2048, stream)
+    peak_ops, probe_mhz = sas.sas_probe_shared_reduction_peak(2048, stream)
+    atom_ops, atom_mhz = sas.sas_probe_shared_atomic_peak(2048, stream)
 
     def barrier():
         if dist is not None:
@@ -585,7 +586,12 @@ def main():
     roof = {"bound": "smem_atomic", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
             "unit": "Gop/s", "frac": achieved / peak_ops, "traffic": stack_traffic(args.workload),
             "kernel": "k_stack", "stack_ms": statistics.mean(stack_ms),
-            "peak_source": f"sas_probe_shared_atomic_peak, this run ({probe_mhz:.0f} MHz)"}
+            "peak_source": f"sas_probe_shared_reduction_peak (conflict-free red.shared.add.u32), this run "
+                           f"({probe_mhz:.0f} MHz)",
+            "peak_atomic_returning": atom_ops / 1e9,
+            "frac_vs_atomic_returning": achieved / atom_ops,
+            "peak_atomic_returning_source": f"sas_probe_shared_atomic_peak (conflict-free atomicAdd, old value "
+                                            f"used), this run ({atom_mhz:.0f} MHz)"}
     cfg = workload_desc(w, cat)
     cfg.update({"l2": "flushed between steps (256 MiB write)", "n_pairs_per_step": n_pairs,
                 "candidates": int(info0["n_candidates"]),

@@ -572,13 +572,25 @@ int sas_vet_train_step(sas_vet* vetter, const uint16_t* stamps, const float* lab
                        const uint32_t* index, uint32_t n, float lr, float* loss, void* stream);
 
 /* Measurement utility: throughput of conflict-free 32-bit shared-memory
- * atomicAdd on every SM of the current device, in operations per second,
- * measured with CUDA events over `iters` operations per thread; this is the
- * peak against which the stack kernel's detection-shifts/s are compared.
+ * atomicAdd whose old value is used (the returning form), on every SM of the
+ * current device, in operations per second, measured with CUDA events over
+ * `iters` operations per thread.  Reported beside the reduction peak below.
  * Also reports the SM clock (MHz) during the probe: clock64() cycles over the
- * global timer's nanoseconds on one SM, in the fastest repetition. */
+ * global timer's nanoseconds on one SM, in the fastest repetition.
+ * Not a paper operation (the roofline of Sec. 2.1 steps 1-2 on this GPU).
+ * Errors: SAS_ERR_ARG (null output or iters == 0), SAS_ERR_CUDA. */
 int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s,
                                  double* sm_mhz);
+
+/* Measurement utility: throughput of conflict-free 32-bit shared-memory
+ * reductions (`red.shared.add.u32`, no value returned: the instruction the
+ * stack kernel issues for Sec. 2.1 steps 1-2) on every SM of the current
+ * device, in operations per second, over `iters` x 8 reductions per thread,
+ * best of three timed repetitions after one warm-up.  This is the peak against
+ * which the stack kernel's detection-shifts/s are compared.  *sm_mhz as above.
+ * Errors: SAS_ERR_ARG (null output or iters == 0), SAS_ERR_CUDA. */
+int sas_probe_shared_reduction_peak(uint32_t iters, void* stream, double* ops_per_s,
+                                    double* sm_mhz);
 
 #ifdef __cplusplus
 }

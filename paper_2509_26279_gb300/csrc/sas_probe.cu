@@ -1,7 +1,9 @@
-// Shared-memory atomic throughput probe: the roofline peak of the stack kernel.
+// Shared-memory atomic throughput probes: the roofline peak of the stack kernel.
 //
-// Every thread of every resident CTA issues `iters` x 8 32-bit atomicAdd to
-// shared memory.  Lane l of warp w always touches word (w*32 + l) + k*blockDim,
+// Every thread of every resident CTA issues `iters` x 8 32-bit additions to
+// shared memory, either as `red.shared.add.u32` (no value returned: the
+// instruction the stack kernel's hot loop issues) or as atomicAdd whose old
+// value is used.  Lane l of warp w always touches word (w*32 + l) + k*blockDim,
 // so the 32 lanes of a warp hit 32 distinct banks (conflict-free) and the
 // addresses are compile-time offsets of one base register: the loop is bound by
 // the shared-memory atomic unit, not by address arithmetic.
@@ -22,6 +24,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // clk[0], clk[1]: SM cycles and nanoseconds (global timer) over block 0's loop,
 // from which the SM clock during the probe follows.
+template <bool RED>
 __global__ void __launch_bounds__(kProbeThreads, 2)
     k_atomic_probe(uint32_t iters, uint32_t* sink, unsigned long long* clk) {
   __shared__ uint32_t s[kProbeThreads * kProbeUnroll];
@@ -30,10 +33,16 @@ __global__ void __launch_bounds__(kProbeThreads, 2)
   const long long c0 = clock64();
   const unsigned long long t0 = global_ns();
   uint32_t* base = s + threadIdx.x;
+  const uint32_t base_s = (uint32_t)__cvta_generic_to_shared(base);
   uint32_t acc = 0;
   for (uint32_t it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int k = 0; k < kProbeUnroll; ++k) acc += atomicAdd(base + k * kProbeThreads, 1u);
+    for (int k = 0; k < kProbeUnroll; ++k) {
+      if constexpr (RED)
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base_s + 4u * (uint32_t)(k * kProbeThreads)), "r"(1u));
+      else
+        acc += atomicAdd(base + k * kProbeThreads, 1u);
+    }
   }
   __syncthreads();
   const long long c1 = clock64();
@@ -47,14 +56,13 @@ __global__ void __launch_bounds__(kProbeThreads, 2)
   }
 }
 
-}  // namespace
-
-cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s, double* sm_mhz) {
+template <bool RED>
+cudaError_t run_probe(uint32_t iters, cudaStream_t st, double* ops_per_s, double* sm_mhz) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_atomic_probe, kProbeThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_atomic_probe<RED>, kProbeThreads, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const int blocks = sms * per_sm;
@@ -70,7 +78,7 @@ cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s,
   for (int rep = 0; rep < 4; ++rep) {  // rep 0 warms up
     cudaMemsetAsync(cycles, 0, 2 * sizeof(unsigned long long), st);
     cudaEventRecord(a, st);
-    k_atomic_probe<<<blocks, kProbeThreads, 0, st>>>(iters, sink, cycles);
+    k_atomic_probe<RED><<<blocks, kProbeThreads, 0, st>>>(iters, sink, cycles);
     note_launch();
     cudaEventRecord(b, st);
     if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
@@ -92,6 +100,16 @@ cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t st, double* ops_per_s,
   *ops_per_s = ops / (best_ms * 1e-3);
   *sm_mhz = mhz;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz) {
+  return run_probe<false>(iters, s, ops_per_s, sm_mhz);
+}
+
+cudaError_t run_red_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz) {
+  return run_probe<true>(iters, s, ops_per_s, sm_mhz);
 }
 
 }  // namespace sas

@@ -48,6 +48,12 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// Shift-table rows per epoch in shared memory, padded by 4 words so that the
+// rows of consecutive epochs start in different banks (a warp's records span
+// one to three epochs; unpadded, their 16-byte loads hit the same banks).
+__host__ __device__ inline int ox_stride(const TileCfg& tc) { return tc.bvx * tc.kx + 4; }
+__host__ __device__ inline int oy_stride(const TileCfg& tc) { return tc.bvy * tc.ky + 4; }
+
 __host__ __device__ inline SmemLayout layout(const TileCfg& tc) {
   SmemLayout L;
   const int per_word = 32 / tc.cb;
@@ -57,9 +63,9 @@ __host__ __device__ inline SmemLayout layout(const TileCfg& tc) {
   L.staged = off;
   off += align16((size_t)tc.scap * 8);
   L.ox = off;
-  off += align16((size_t)tc.ec * tc.bvx * tc.kx * 4);
+  off += align16((size_t)tc.ec * ox_stride(tc) * 4);
   L.oy = off;
-  off += align16((size_t)tc.ec * tc.bvy * tc.ky * 4);
+  off += align16((size_t)tc.ec * oy_stride(tc) * 4);
   L.win = off;
   off += align16((size_t)tc.ec * 4 * 4);
   L.seg_pos = off;
@@ -304,6 +310,7 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
   const uint32_t E = g.E;
   const int n_st = a.nst_x * a.nst_y;
   const int bxk = tc.bvx * KX, byk = tc.bvy * KY;  // lattice columns / rows of a block
+  const int oxs = ox_stride(tc), oys = oy_stride(tc);  // their shift-table rows per epoch
   const int sbins = tc.s;                          // bins per super-bin side
   const int rows_per_epoch = tc.rows;
   const bool single_chunk = E <= (uint32_t)tc.ec;
@@ -362,13 +369,13 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
           // the edge keeps projections that differ by less than a super-bin,
           // which the merged reductions rely on.
           const int el = i / bxk, k = i % bxk, kx = min(kxa + k, g.nvx - 1);
-          s_ox[el * bxk + k] = s_win[el * 4 + 1] > 0
+          s_ox[el * oxs + k] = s_win[el * 4 + 1] > 0
                                    ? X0 + a.sxt[(size_t)kx * E + e_base + el] - s_win[el * 4]
                                    : kOutside;
         } else {
           const int j = i - ne * bxk;
           const int el = j / byk, k = j % byk, ky = kya + k;
-          s_oy[el * byk + k] = (ky < g.nvy && s_win[el * 4 + 3] > 0)
+          s_oy[el * oys + k] = (ky < g.nvy && s_win[el * 4 + 3] > 0)
                                    ? Y0 + a.syt[(size_t)ky * E + e_base + el] - s_win[el * 4 + 2]
                                    : kOutside;
         }
@@ -473,7 +480,7 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
           const int el = (int)(r.x >> 24);
           const uint32_t w = WT ? r.y >> 24 : 1u;
           const uint32_t p = process_rec<KX, KY, CB, decltype(masked)::value, decltype(merge)::value, WT>(
-              r.x & 0xffffffu, WT ? r.y & 0xffffffu : r.y, s_ox + el * bxk + oxo, s_oy + el * byk + oyo, cells_s,
+              r.x & 0xffffffu, WT ? r.y & 0xffffffu : r.y, s_ox + el * oxs + oxo, s_oy + el * oys + oyo, cells_s,
               tw_x, tw_y, a.magic, a.bin_is_one, tc.tx, txty, act, w);
           pairs += p;
           added += WT ? p * w : p;
