@@ -21,8 +21,13 @@ N_min = 25.  The metric is detection-shifts per second: in-domain
             batched + vetted form on 60 uneven fields, with recall per
             magnitude bin and purity (after training the vetter, untimed)
 
---impl reference times the CPU oracle (the plain definition, single thread) on
-a bounded lattice-row sample of the same workload.
+  configs   the other search workloads (tiny, fast_movers) measured the same
+            way, each with its stack kernel's roofline fraction and the oracle
+
+--impl reference times the CPU oracle (the plain definition; its OpenMP form
+over velocity chunks on all host cores) on a bounded lattice sample of the same
+workload.  --vetter-timing and --refine-timing print only the timing of the
+vetter's kernels or of refinement (the commands the profiles were taken with).
 Multi-GPU (torchrun): each rank searches its own field (weak scaling); the
 only collectives are the timing barrier and the max over ranks.
 """
@@ -140,23 +145,60 @@ def stack_traffic(workload: str):
     return int(fields["traffic_bytes_per_launch"])
 
 
+def host_info() -> dict:
+    """The host the CPU baseline ran on: CPU model, logical CPUs, the CPUs this
+    process may run on, and the oracle's default OpenMP team."""
+    import oracle
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Vendor ID") and v.strip() and v.strip() != "-":
+                model = v.strip() if model is None or k.strip() == "Model name" else model
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"cpu_model": model, "nproc": os.cpu_count(),
+            "affinity": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None,
+            "oracle_openmp_threads": oracle.threads()}
+
+
 def cpu_baseline(w: W.Workload, cat, budget_s: float = 15.0) -> dict:
-    """The oracle as it stands, single thread, on whole lattice rows of the same
-    workload, grown until about `budget_s` seconds of CPU work."""
+    """The oracle as it stands on the same workload: single thread on whole
+    lattice rows, grown until about budget_s / 2 seconds, and its OpenMP form
+    (velocity chunks over every core of the team) on a contiguous lattice range
+    sized to about the same time.  The main figure is the OpenMP one; both are
+    in det-shifts/s (in-domain pairs per second of wall time)."""
     import oracle
     g = w.grid
+    nv = g.nvx * g.nvy
     rows, pairs, secs = 0, 0, 0.0
     row = g.nvy // 2
-    while secs < budget_s and rows < g.nvy:
+    while secs < budget_s / 2 and rows < g.nvy:
         ky = (row + rows) % g.nvy
         t0 = time.perf_counter()
         r = oracle.stack(cat, g, w.n_min, ky * g.nvx, (ky + 1) * g.nvx)
         secs += time.perf_counter() - t0
         pairs += r.n_pairs
         rows += 1
-    return {"value": pairs / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{rows} lattice rows x {g.nvx} velocities of the same field "
-                      f"({pairs} detection-shifts in {secs:.1f} s)"}
+    single = {"value": pairs / secs, "cores": 1,
+              "sample": f"{rows} lattice rows x {g.nvx} velocities ({pairs} detection-shifts in {secs:.1f} s)"}
+    thr = oracle.threads()
+    per_v = secs / max(1, rows * g.nvx)                       # one velocity, one thread
+    n_v = int(min(nv, max(thr, budget_s / 2 / max(per_v, 1e-9) * thr * 0.8)))
+    a = max(0, nv // 2 - n_v // 2)
+    t0 = time.perf_counter()
+    r = oracle.stack(cat, g, w.n_min, a, a + n_v, threads=0)
+    secs_mt = time.perf_counter() - t0
+    return {"value": r.n_pairs / secs_mt, "unit": UNIT, "cores": thr, "kind": "oracle",
+            "sample": f"OpenMP over {thr} threads: lattice indices [{a}, {a + n_v}) of the same field "
+                      f"({r.n_pairs} detection-shifts in {secs_mt:.1f} s)",
+            "single_thread": single, "host": host_info()}
 
 
 def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epochs: int = 15,
@@ -433,6 +475,147 @@ def weighted_section(grid, dx, dy, de, cat, w, stream, dev, reps: int = 5) -> di
             "timing": f"CUDA events around sas_stack_weighted, median of {reps}, inputs on the device"}
 
 
+def config_entry(name: str, steps: int, warmup: int, dev, stream, flush, peak_ops: float,
+                 cpu_budget_s: float) -> dict:
+    """One more search workload measured like the main line (device-resident
+    inputs, L2 flushed between steps, CUDA events on the library's stream):
+    det-shifts/s of the whole search, the stack kernel's mean time and its
+    fraction of the in-run reduction peak, and the oracle beside it."""
+    import torch
+    from paper_2509_26279_gb300 import sas
+    w = getattr(W, name)()
+    cat = W.load(w)
+    grid = sas.Grid(w.grid)
+    dx = torch.from_numpy(cat.x).to(dev)
+    dy = torch.from_numpy(cat.y).to(dev)
+    de = torch.from_numpy(cat.epoch.view(np.int16)).to(dev)
+
+    def step():
+        return sas.sas_stack(grid, dx, dy, de, cat.t, cat.ticks_per_hour, w.n_min, on_device=True, stream=stream)
+
+    for _ in range(warmup):
+        r = step()
+        info0 = r.info()
+        r.free()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stack_ms = []
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        r = step()
+        ev[i][1].record(stream)
+        stack_ms.append(r.info()["ms_stack"])
+        r.free()
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in ev)
+    n_pairs = int(info0["n_pairs"])
+    achieved = n_pairs / (statistics.mean(stack_ms) * 1e-3)
+    out = {"value": n_pairs * steps / (total * 1e-3), "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": total / steps, "config": workload_desc(w, cat),
+           "n_pairs_per_step": n_pairs, "candidates": int(info0["n_candidates"]),
+           "tile": [info0["tile_kx"], info0["tile_ky"], info0["tile_bx"], info0["tile_by"]],
+           "superbin": int(info0["superbin"]), "velocity_block": [info0["vblock_x"], info0["vblock_y"]],
+           "roofline": {"bound": "smem_atomic", "kernel": "k_stack", "stack_ms": statistics.mean(stack_ms),
+                        "achieved": achieved / 1e9, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                        "frac": achieved / peak_ops}}
+    if cpu_budget_s > 0:
+        out["cpu_baseline"] = cpu_baseline(w, cat, cpu_budget_s)
+    return out
+
+
+def vetter_timing(dev, stream, n_forward: int = 32768, batch: int = 4096, reps: int = 5) -> dict:
+    """Throughput of the vetter's kernels on random count stamps shaped like
+    the search's (Poisson noise plus a central bump): the forward over
+    n_forward stamps (in chunks of the vetter's batch) and training steps of
+    `batch` stamps, CUDA events on the launching stream, best of reps."""
+    import torch
+    from paper_2509_26279_gb300 import sas, vetting
+    peaks = measured_peaks()
+    rng = np.random.default_rng(W.BASE_SEED + 80)
+    st = rng.poisson(1.2, size=(n_forward, 9, 15, 15))
+    st[:, 4, 6:9, 6:9] += rng.integers(0, 40, size=(n_forward, 3, 3))
+    dst = torch.from_numpy(st.astype(np.uint16).view(np.int16)).to(dev)
+    lab = torch.from_numpy((rng.random(n_forward) < 0.5).astype(np.float32)).to(dev)
+    vt = sas.Vetter(dev.index or 0, batch)
+    vt.set_state(vetting.init_params(1))
+    logits = torch.zeros(n_forward, device=dev)
+    loss = torch.zeros(1, device=dev)
+
+    def best_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None or ms < best else best
+        return best
+
+    fwd_ms = best_ms(lambda: vt.forward(dst, n_forward, logits, stream=stream))
+    trn_ms = best_ms(lambda: vt.train_step(dst, lab, batch, 1e-3, loss, stream=stream))
+    vt.check()
+    fwd_flop, trn_flop = 4.93e6, 14.8e6       # per stamp, see the header of csrc/sas_vet.cu
+    bf16 = peaks.get("bf16_tflops")
+    f_tf = n_forward * fwd_flop / (fwd_ms * 1e-3) / 1e12
+    t_tf = batch * trn_flop / (trn_ms * 1e-3) / 1e12
+    return {"forward": {"stamps": n_forward, "ms": fwd_ms, "stamps_per_s": n_forward / (fwd_ms * 1e-3),
+                        "tflops": f_tf, "frac_of_bf16_peak": f_tf / bf16 if bf16 else None},
+            "train_step": {"stamps": batch, "ms": trn_ms, "stamps_per_s": batch / (trn_ms * 1e-3),
+                           "tflops": t_tf, "frac_of_bf16_peak": t_tf / bf16 if bf16 else None},
+            "peak": {"bf16_tflops": bf16, "source": "MEASURED_PEAKS.json (cuBLAS bf16 burst)"},
+            "timing": f"CUDA events on the launching stream, best of {reps} after one warm-up"}
+
+
+def refine_timing(dev, stream, reps: int = 5) -> dict:
+    """Cluster finding and refinement on one search of the DECam TNO field:
+    sas_peel, then sas_refine with one fit round and with the default loop,
+    CUDA events on the launching stream, median of reps."""
+    import torch
+    from paper_2509_26279_gb300 import sas
+    w = W.decam_tno()
+    cat = W.load(w)
+    grid = sas.Grid(w.grid)
+    dx, dy = torch.from_numpy(cat.x).to(dev), torch.from_numpy(cat.y).to(dev)
+    de = torch.from_numpy(cat.epoch.view(np.int16)).to(dev)
+    res = sas.sas_stack(grid, dx, dy, de, cat.t, cat.ticks_per_hour, w.n_min, on_device=True, stream=stream)
+    pl = sas.sas_peel(res, w.n_min, 1000, stream=stream)
+    out = {"workload": workload_desc(w, cat)["workload"], "clusters": int(pl.info()["n_candidates"])}
+    for tag, kw in (("one_fit_round", {"max_iter": 1}), ("default", {})):
+        ms = []
+        for i in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tr = sas.sas_refine(res, pl, seed=1, stream=stream, **kw)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ms.append(a.elapsed_time(b))
+            tracks, _ = tr.tracks()
+            tr.free()
+        out[tag] = {"ms": statistics.median(ms), "tracks": int(len(tracks)),
+                    "converged": int((tracks["status"] == 0).sum()),
+                    "fits_max": int(tracks["iterations"].max()) if len(tracks) else 0}
+    pl.free()
+    res.free()
+    out["timing"] = f"CUDA events around sas_refine on the launching stream, median of {reps} after one warm-up"
+    return out
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -441,12 +624,13 @@ def run_reference(args):
     cat = W.load(w)
     import oracle
     g = w.grid
-    per_step = 12                      # lattice points per step (about a second of CPU)
+    thr = oracle.threads()
+    per_step = 12 * thr                # lattice points per step: about a second on the OpenMP team
     nv = g.nvx * g.nvy
     def step(i):
         a = (nv // 2 + i * per_step) % (nv - per_step)
         t0 = time.perf_counter()
-        pairs = oracle.stack(cat, g, w.n_min, a, a + per_step).n_pairs
+        pairs = oracle.stack(cat, g, w.n_min, a, a + per_step, threads=0).n_pairs
         return pairs, time.perf_counter() - t0
     for i in range(args.warmup):
         step(i)
@@ -457,13 +641,13 @@ def run_reference(args):
         tot_s += s
     v = tot_p / tot_s
     cfg = workload_desc(w, cat)
-    cfg["sample"] = f"{per_step} consecutive lattice points of the field per step"
+    cfg["sample"] = f"{per_step} consecutive lattice points of the field per step (OpenMP, {thr} threads)"
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64",
            "data": "synthetic", "config": cfg,
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": cfg["sample"]},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                            "sample": cfg["sample"], "host": host_info()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -479,6 +663,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-fields", action="store_true", help="skip the fields/s comparison")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other search workloads' entries")
+    ap.add_argument("--vetter-timing", action="store_true",
+                    help="only time the vetter's forward and training kernels and print that line")
+    ap.add_argument("--refine-timing", action="store_true",
+                    help="only time cluster finding's refinement on the TNO field and print that line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -497,6 +686,13 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.vetter_timing or args.refine_timing:
+        stream = torch.cuda.current_stream(dev)
+        if rank == 0:
+            fn = vetter_timing if args.vetter_timing else refine_timing
+            print(json.dumps({"mode": "vetter_timing" if args.vetter_timing else "refine_timing",
+                              **fn(dev, stream)}), flush=True)
+        return 0
 
     w = getattr(W, args.workload)()
     w = W.Workload(w.name, w.recipe, w.grid, w.n_min, w.seed + 1000 * rank)  # own field per rank
@@ -612,6 +808,12 @@ def main():
     if world == 1:
         out["peel"] = peel_section(grid, dx, dy, de, cat, w, stream)
         out["weighted"] = weighted_section(grid, dx, dy, de, cat, w, stream, dev)
+    if world == 1 and not args.no_configs:
+        steps_of = {"tiny": 20, "decam_tno": 10, "fast_movers": 3}
+        out["configs"] = {
+            name: config_entry(name, steps_of[name], args.warmup, dev, stream, flush, peak_ops,
+                               0.0 if args.no_cpu_baseline else min(args.cpu_budget_s, 10.0))
+            for name in ("tiny", "decam_tno", "fast_movers") if name != args.workload}
     if world == 1 and not args.no_fields:
         out["fields"] = fields_section(dev, stream)
     if world == 1 and not args.no_cpu_baseline:

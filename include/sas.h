@@ -283,8 +283,8 @@ int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
  * from a loop that must never wait on the CUDA allocator.  For each cell
  * (v_idx, bx, by) it returns the same numbers as the exact-count step of
  * sas_stack: distinct[i] = number of distinct epochs and raw[i] = number of
- * detections of the catalog that project into the cell (Sec. 2.1 steps 1-2,
- * reference epoch t0 = earliest detection time).
+ * detections of the catalog that project into the cell when shifted to the
+ * earliest detection time.
  *
  * cells: device array of n_cells triples (v_idx, bx, by) as uint32.
  * distinct, raw: device arrays of n_cells uint32, owned by the caller.
@@ -293,12 +293,13 @@ int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
  * cudaFree or allocating library call).  Its working state (epoch times and
  * flags) lives in one fixed 16 KiB array inside the library, which every GPU
  * that loads the library holds until the process exits; so n_epochs may not
- * exceed 1024 (SAS_ERR_RANGE otherwise).  The first call on a device looks up
- * that array's device address, so make it before capturing a stream into a
- * graph.  All calls on a device share the array: calls whose GPU work overlaps
- * (other streams, other host threads) race, and must be serialized by the
- * caller.  Each call resets the parts that must start at zero.  The call
- * synchronizes the stream.  Counting is exact in 64-bit arithmetic; the cost is
+ * exceed 1024 (SAS_ERR_RANGE otherwise).  The first call on a device does a
+ * set-up (it looks up that array's device address and the device's SM count),
+ * so make that first call before any stream capture.  All calls on a device
+ * share the array: calls whose GPU work overlaps (other streams, other host
+ * threads) race, and must be serialized by the caller.  Each call resets the
+ * parts that must start at zero.  Before returning, the call synchronizes the
+ * stream to read its status back.  Counting is exact in 64-bit arithmetic; the cost is
  * O(n_cells * n) (it scans the whole catalog per cell), meant for modest
  * numbers of cells.
  * Errors: SAS_ERR_ARG (nulls, host catalog, a cell outside the lattice or the
@@ -545,6 +546,18 @@ int sas_vet_set_state(sas_vet* vetter, const float* params, const float* m, cons
 int sas_vet_get_state(const sas_vet* vetter, float* params, float* m, float* v, uint64_t* step);
 /* The BF16 working copy of the parameters (flat order, raw bits), to host. */
 int sas_vet_get_bf16(const sas_vet* vetter, uint16_t* out);
+
+/* The activations the last batch stored (BF16 raw bits, to host): layer 1, 2, 3
+ * = the outputs of conv1, conv2, conv3 after ReLU, [n][32][h][h] with h = 13,
+ * 11, 9 (channel-major, as the stored layout of conv3 is fc1's input); layer 4
+ * = the fc1 output after ReLU, [n][64].  "The last batch" is the last forward
+ * chunk or gradient batch of this vetter (sas_vet_forward runs in chunks of the
+ * vetter's max_batch: its last chunk's activations are what remains).  n <=
+ * max_batch samples are copied from the start of that batch.  Waits for the
+ * device.  For inspection and tests (the backward of the network, Sec. 4's
+ * learned filter, runs from exactly these values).
+ * Errors: SAS_ERR_ARG (NULL, layer outside 1..4, n > max_batch), SAS_ERR_CUDA. */
+int sas_vet_get_activations(const sas_vet* vetter, uint32_t layer, uint64_t n, uint16_t* out);
 
 /* logits[i] of n stamps (device arrays: stamps [.][9][15][15] uint16,
  * logits [n] float); stamp i is stamps[index[i]] when index (device uint32

@@ -38,10 +38,16 @@ assert CAND_DTYPE.itemsize == 40
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (plain C11, -O2)."""
+    """Compile the oracle with the host C compiler (plain C11, -O2, OpenMP for
+    oracle_stack_mt's loop over velocity chunks; without OpenMP that loop runs
+    on one thread)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -66,6 +72,10 @@ def bind(path: str):
                                      i32, i32, i32, i32, i32, p, p]
     lib.oracle_t0.restype = ctypes.c_int64
     lib.oracle_t0.argtypes = [i64, p, p]
+    lib.oracle_stack_mt.restype = ctypes.c_int
+    lib.oracle_stack_mt.argtypes = lib.oracle_stack.argtypes + [i32]
+    lib.oracle_threads.restype = ctypes.c_int32
+    lib.oracle_threads.argtypes = []
     return lib
 
 
@@ -99,9 +109,17 @@ class OracleResult:
         return [self.ids[c["id_off"]: c["id_off"] + c["id_len"]] for c in self.cands]
 
 
+def threads() -> int:
+    """Threads the OpenMP form uses by default (1 when built without OpenMP)."""
+    return int(_load().oracle_threads())
+
+
 def stack(cat, grid, n_min: int, v_begin: int = 0, v_end: int | None = None,
-          max_candidates: int = 0, lib=None) -> OracleResult:
-    """Run the oracle search over lattice indices [v_begin, v_end)."""
+          max_candidates: int = 0, lib=None, threads: int = 1) -> OracleResult:
+    """Run the oracle search over lattice indices [v_begin, v_end).  threads == 1:
+    the single loop over velocities (oracle_stack); otherwise oracle_stack_mt,
+    the same search over velocity chunks in an OpenMP loop (threads <= 0: all
+    of OpenMP's default team), merged in the same total order."""
     lib = lib or _load()
     x, y, e, t = _cat_arrays(cat)
     if v_end is None:
@@ -111,14 +129,18 @@ def stack(cat, grid, n_min: int, v_begin: int = 0, v_end: int | None = None,
         cands = np.zeros(cap, CAND_DTYPE)
         ids = np.zeros(ids_cap, np.int32)
         nc, ni, npairs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-        rc = lib.oracle_stack(x.shape[0], _ptr(x), _ptr(y), _ptr(e), t.shape[0], _ptr(t),
-                              int(cat.ticks_per_hour),
-                              grid.vx0, grid.vy0, grid.dvx, grid.dvy, grid.nvx, grid.nvy,
-                              grid.speed_min, grid.speed_max,
-                              grid.x_min, grid.y_min, grid.nbx, grid.nby, grid.bin,
-                              int(n_min), int(v_begin), int(v_end), int(max_candidates),
-                              _ptr(cands), cap, ctypes.byref(nc), _ptr(ids), ids_cap,
-                              ctypes.byref(ni), ctypes.byref(npairs))
+        args = (x.shape[0], _ptr(x), _ptr(y), _ptr(e), t.shape[0], _ptr(t),
+                int(cat.ticks_per_hour),
+                grid.vx0, grid.vy0, grid.dvx, grid.dvy, grid.nvx, grid.nvy,
+                grid.speed_min, grid.speed_max,
+                grid.x_min, grid.y_min, grid.nbx, grid.nby, grid.bin,
+                int(n_min), int(v_begin), int(v_end), int(max_candidates),
+                _ptr(cands), cap, ctypes.byref(nc), _ptr(ids), ids_cap,
+                ctypes.byref(ni), ctypes.byref(npairs))
+        if threads == 1:
+            rc = lib.oracle_stack(*args)
+        else:
+            rc = lib.oracle_stack_mt(*args, int(threads))
         if rc == 3:
             cap, ids_cap = max(cap, nc.value), max(ids_cap, ni.value)
             continue

@@ -34,6 +34,12 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+static int omp_default_threads(void) { return omp_get_max_threads(); }
+#else
+static int omp_default_threads(void) { return 1; }
+#endif
 
 typedef struct {
   int64_t v_idx;
@@ -296,3 +302,115 @@ int oracle_histogram(int64_t n, const int32_t* x, const int32_t* y, const uint16
   free(mask);
   return ORACLE_OK;
 }
+
+/*
+ * The same search with the lattice range split into chunks that run in an
+ * OpenMP loop over velocities (each chunk is one oracle_stack call, with its
+ * own private histograms), then merged: every chunk's candidates concatenated
+ * and sorted by the same total order, the optional top-K cut applied, ids
+ * copied in that order.  The velocities' histograms are independent (Sec. 2.1
+ * step 2), so the output equals oracle_stack's byte for byte.  n_threads <= 0:
+ * OpenMP's default team.  Same outputs and statuses as oracle_stack.
+ */
+typedef struct {
+  oracle_candidate* cands;
+  int32_t* ids;
+  int64_t n_cands, n_ids, n_pairs;
+  int status;
+} oracle_chunk;
+
+int oracle_stack_mt(int64_t n, const int32_t* x, const int32_t* y, const uint16_t* epoch,
+                    int32_t n_epochs, const int64_t* t, int64_t tph,
+                    int32_t vx0, int32_t vy0, int32_t dvx, int32_t dvy, int32_t nvx, int32_t nvy,
+                    int32_t speed_min, int32_t speed_max,
+                    int32_t x_min, int32_t y_min, int32_t nbx, int32_t nby, int32_t w,
+                    int32_t n_min, int64_t v_begin, int64_t v_end, int64_t max_candidates,
+                    oracle_candidate* cands, int64_t cap, int64_t* n_cands,
+                    int32_t* ids, int64_t ids_cap, int64_t* n_ids, int64_t* n_pairs,
+                    int32_t n_threads) {
+  if (v_begin < 0 || v_end > (int64_t)nvx * nvy || v_begin > v_end) return ORACLE_ERR_ARG;
+  const int64_t nv = v_end - v_begin;
+  const int team = n_threads > 0 ? n_threads : omp_default_threads();
+  /* chunks of at least 8 velocities (each chunk allocates its own histograms),
+     at most 256, and at least two per thread where the range allows it */
+  int64_t n_chunks = nv / 8;
+  if (n_chunks > 256) n_chunks = 256;
+  if (n_chunks < 2 * (int64_t)team) n_chunks = 2 * (int64_t)team;
+  if (n_chunks > nv) n_chunks = nv;
+  if (n_chunks < 1) n_chunks = 1;
+  oracle_chunk* ch = (oracle_chunk*)calloc((size_t)n_chunks, sizeof(oracle_chunk));
+  if (!ch) return ORACLE_ERR_OOM;
+  (void)team;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(team)
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    const int64_t a = v_begin + nv * k / n_chunks, b = v_begin + nv * (k + 1) / n_chunks;
+    int64_t ccap = 256, icap = 4096;
+    for (;;) {
+      ch[k].cands = (oracle_candidate*)malloc((size_t)ccap * sizeof(oracle_candidate));
+      ch[k].ids = (int32_t*)malloc((size_t)icap * sizeof(int32_t));
+      if (!ch[k].cands || !ch[k].ids) { ch[k].status = ORACLE_ERR_OOM; break; }
+      ch[k].status = oracle_stack(n, x, y, epoch, n_epochs, t, tph, vx0, vy0, dvx, dvy, nvx, nvy,
+                                  speed_min, speed_max, x_min, y_min, nbx, nby, w, n_min, a, b, 0,
+                                  ch[k].cands, ccap, &ch[k].n_cands, ch[k].ids, icap, &ch[k].n_ids,
+                                  &ch[k].n_pairs);
+      if (ch[k].status != ORACLE_ERR_CAP) break;
+      free(ch[k].cands); free(ch[k].ids);
+      ch[k].cands = NULL; ch[k].ids = NULL;
+      if (ch[k].n_cands > ccap) ccap = ch[k].n_cands;
+      if (ch[k].n_ids > icap) icap = ch[k].n_ids;
+    }
+  }
+  int status = ORACLE_OK;
+  int64_t total_c = 0, total_i = 0, pairs = 0;
+  for (int64_t k = 0; k < n_chunks; ++k) {
+    if (ch[k].status != ORACLE_OK && status == ORACLE_OK) status = ch[k].status;
+    total_c += ch[k].n_cands;
+    total_i += ch[k].n_ids;
+    pairs += ch[k].n_pairs;
+  }
+  oracle_candidate* all = NULL;
+  int32_t* all_ids = NULL;
+  if (status == ORACLE_OK) {
+    all = (oracle_candidate*)malloc((size_t)(total_c > 0 ? total_c : 1) * sizeof(oracle_candidate));
+    all_ids = (int32_t*)malloc((size_t)(total_i > 0 ? total_i : 1) * sizeof(int32_t));
+    if (!all || !all_ids) status = ORACLE_ERR_OOM;
+  }
+  if (status == ORACLE_OK) {
+    /* concatenate, with id_off pointing into the concatenated id array */
+    int64_t pc = 0, pi = 0;
+    for (int64_t k = 0; k < n_chunks; ++k) {
+      for (int64_t c = 0; c < ch[k].n_cands; ++c) {
+        all[pc] = ch[k].cands[c];
+        all[pc].id_off += pi;
+        ++pc;
+      }
+      memcpy(all_ids + pi, ch[k].ids, (size_t)ch[k].n_ids * sizeof(int32_t));
+      pi += ch[k].n_ids;
+    }
+    qsort(all, (size_t)total_c, sizeof(oracle_candidate), cand_cmp);
+    int64_t cn = total_c;
+    if (max_candidates > 0 && cn > max_candidates) cn = max_candidates;
+    int64_t kept_ids = 0;
+    for (int64_t c = 0; c < cn; ++c) kept_ids += all[c].id_len;
+    *n_cands = cn;
+    *n_ids = kept_ids;
+    *n_pairs = pairs;
+    if (cn > cap || kept_ids > ids_cap) status = ORACLE_ERR_CAP;
+    int64_t off = 0;
+    for (int64_t c = 0; c < cn && c < cap; ++c) {
+      oracle_candidate o = all[c];
+      const int64_t src = o.id_off;
+      o.id_off = off;
+      if (off + o.id_len <= ids_cap)
+        memcpy(&ids[off], &all_ids[src], (size_t)o.id_len * sizeof(int32_t));
+      off += o.id_len;
+      cands[c] = o;
+    }
+  }
+  for (int64_t k = 0; k < n_chunks; ++k) { free(ch[k].cands); free(ch[k].ids); }
+  free(ch); free(all); free(all_ids);
+  return status;
+}
+
+/* Number of threads the OpenMP loop above uses by default (1 without OpenMP). */
+int32_t oracle_threads(void) { return omp_default_threads(); }

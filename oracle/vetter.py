@@ -151,28 +151,38 @@ def bce_with_logits(logit, y):
     return float(np.mean(np.maximum(logit, 0) - logit * y + np.log1p(np.exp(-np.abs(logit)))))
 
 
+def backward(flat, act, g_logit):
+    """Flat gradient of the loss given dL/dlogit per sample and the activations
+    the forward stored (act: x0, a1, a2, a3, a4 as forward returns them):
+    back-propagation through those values and their ReLU masks (a > 0)."""
+    p = unflatten(np.asarray(flat, np.float64))
+    a1, a2, a3, a4 = (np.asarray(act[k], np.float64) for k in ("a1", "a2", "a3", "a4"))
+    x0 = np.asarray(act["x0"], np.float64)
+    g_logit = np.asarray(g_logit, np.float64)
+    g = {}
+    g["fc2.w"] = a4.T @ g_logit
+    g["fc2.b"] = np.array([g_logit.sum()])
+    g4 = np.outer(g_logit, p["fc2.w"]) * (a4 > 0)
+    g["fc1.w"] = g4.T @ a3.reshape(len(a3), -1)
+    g["fc1.b"] = g4.sum(axis=0)
+    g3 = (g4 @ p["fc1.w"]).reshape(a3.shape) * (a3 > 0)
+    d2, g["conv3.w"], g["conv3.b"] = _conv_back(a2, p["conv3.w"], g3)
+    g2 = d2 * (a2 > 0)
+    d1, g["conv2.w"], g["conv2.b"] = _conv_back(a1, p["conv2.w"], g2)
+    g1 = d1 * (a1 > 0)
+    _, g["conv1.w"], g["conv1.b"] = _conv_back(x0, p["conv1.w"], g1)
+    return flatten(g)
+
+
 def gradients(flat, stamp_counts, y, store=None):
     """(loss, flat gradient of the mean BCE loss).  With store (see forward),
     back-propagation runs through the stored activations: their ReLU masks
     and their values in the weight gradients."""
     logit, a = forward(flat, stamp_counts, store)
-    p = a["p"]
     B = len(logit)
     y = np.asarray(y, np.float64)
     g_logit = (1.0 / (1.0 + np.exp(-logit)) - y) / B              # d loss / d logit
-    g = {}
-    g["fc2.w"] = a["a4"].T @ g_logit
-    g["fc2.b"] = np.array([g_logit.sum()])
-    g4 = np.outer(g_logit, p["fc2.w"]) * (a["a4"] > 0)
-    g["fc1.w"] = g4.T @ a["f"]
-    g["fc1.b"] = g4.sum(axis=0)
-    g3 = (g4 @ p["fc1.w"]).reshape(a["a3"].shape) * (a["a3"] > 0)
-    d2, g["conv3.w"], g["conv3.b"] = _conv_back(a["a2"], p["conv3.w"], g3)
-    g2 = d2 * (a["a2"] > 0)
-    d1, g["conv2.w"], g["conv2.b"] = _conv_back(a["a1"], p["conv2.w"], g2)
-    g1 = d1 * (a["a1"] > 0)
-    _, g["conv1.w"], g["conv1.b"] = _conv_back(a["x0"], p["conv1.w"], g1)
-    return bce_with_logits(logit, y), flatten(g)
+    return bce_with_logits(logit, y), backward(flat, a, g_logit)
 
 
 def adam_step(flat, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

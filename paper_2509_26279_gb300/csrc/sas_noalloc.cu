@@ -34,6 +34,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 std::mutex g_mu;
 void* g_scratch_ptr[64] = {};
+int g_sms[64] = {};  // multiprocessors of each device (grid sizes)
 
 constexpr int kCountThreads = 256;
 
@@ -138,17 +139,23 @@ __global__ void __launch_bounds__(kCountThreads) k_count_cells(
 
 // The device address of the fixed array, looked up once per device with that
 // device current.  In host code the array's name is only a host-side stand-in,
-// so kernels are given this address instead.
-int scratch_for_device(int dev, unsigned char** out) {
+// so kernels are given this address instead.  The same set-up reads the
+// device's multiprocessor count, which sizes the grids.
+int scratch_for_device(int dev, unsigned char** out, int* sms) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (dev < 0 || dev >= 64) return SAS_ERR_ARG;
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) return SAS_ERR_CUDA;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n < 1) return SAS_ERR_CUDA;
+    g_sms[dev] = n;
     g_scratch_ptr[dev] = p;
   }
   *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *sms = g_sms[dev];
   return SAS_OK;
 }
 
@@ -198,8 +205,9 @@ int noalloc_cell_counts(const sas_grid_desc& d, const sas_catalog* cat, const ui
     return SAS_ERR_CUDA;
   }
   unsigned char* scratch = nullptr;
-  if (scratch_for_device(dev, &scratch) != SAS_OK) {
-    *err = "cudaGetSymbolAddress of the fixed working array failed";
+  int sms = 0;
+  if (scratch_for_device(dev, &scratch, &sms) != SAS_OK) {
+    *err = "set-up failed (cudaGetSymbolAddress of the fixed working array, or the device's SM count)";
     return SAS_ERR_CUDA;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -218,12 +226,12 @@ int noalloc_cell_counts(const sas_grid_desc& d, const sas_catalog* cat, const ui
   g.nbx = (int32_t)d.nbx; g.nby = (int32_t)d.nby; g.bin = d.bin;
   g.E = E; g.tph = cat->ticks_per_hour;
   if (cat->n > 0) {
-    const unsigned blocks = (unsigned)std::min<uint64_t>((cat->n + 255) / 256, 152ull * 16);
+    const unsigned blocks = (unsigned)std::min<uint64_t>((cat->n + 255) / 256, (uint64_t)sms * 16);
     k_mark_epochs<<<blocks, 256, 0, s>>>(cat->epoch, cat->x, cat->y, cat->n, E, scratch);
     note_launch();
   }
   if (n_cells > 0) {
-    const unsigned blocks = (unsigned)std::min<uint64_t>(n_cells, 152ull * 8);
+    const unsigned blocks = (unsigned)std::min<uint64_t>(n_cells, (uint64_t)sms * 8);
     k_count_cells<<<blocks, kCountThreads, 0, s>>>(cat->x, cat->y, cat->epoch, cat->n, E,
                                                    cat->ticks_per_hour, g, cells, n_cells,
                                                    distinct, raw, scratch);

@@ -1069,6 +1069,20 @@ int sas_vet_get_bf16(const sas_vet* vt, uint16_t* out) {
   return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_get_bf16");
 }
 
+int sas_vet_get_activations(const sas_vet* vt, uint32_t layer, uint64_t n, uint16_t* out) {
+  if (!vt || (n && !out)) return set_error(SAS_ERR_ARG, "sas_vet_get_activations: NULL argument");
+  if (layer < 1 || layer > 4) return set_error(SAS_ERR_ARG, "sas_vet_get_activations: layer must be 1..4");
+  if (n > vt->max_batch) return set_error(SAS_ERR_ARG, "sas_vet_get_activations: n exceeds the vetter's batch");
+  const size_t per = layer == 1 ? (size_t)vet::kCh * vet::kH1 * vet::kH1
+                   : layer == 2 ? (size_t)vet::kCh * vet::kH2 * vet::kH2
+                   : layer == 3 ? (size_t)vet::kF : (size_t)vet::kHid;
+  const __nv_bfloat16* src = layer == 1 ? vt->a1 : layer == 2 ? vt->a2 : layer == 3 ? vt->a3 : vt->a4;
+  DeviceGuard guard(vt->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && n) e = cudaMemcpy(out, src, n * per * 2, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SAS_OK : cuda_fail(e, "sas_vet_get_activations");
+}
+
 int sas_vet_forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* index, uint64_t n, float* logits,
                     void* stream) {
   if (!vt) return set_error(SAS_ERR_ARG, "sas_vet_forward: NULL vetter");

@@ -463,6 +463,7 @@ _lib.sas_vet_check.argtypes = [_p]
 _lib.sas_vet_set_state.argtypes = [_p, _p, _p, _p, ctypes.c_uint64]
 _lib.sas_vet_get_state.argtypes = [_p, _p, _p, _p, ctypes.POINTER(ctypes.c_uint64)]
 _lib.sas_vet_get_bf16.argtypes = [_p, _p]
+_lib.sas_vet_get_activations.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint64, _p]
 _lib.sas_vet_forward.argtypes = [_p, _p, _p, ctypes.c_uint64, _p, _p]
 _lib.sas_vet_gradients.argtypes = [_p, _p, _p, _p, ctypes.c_uint32, _p, _p, _p]
 _lib.sas_vet_apply_gradients.argtypes = [_p, _p, ctypes.c_float, _p]
@@ -476,7 +477,7 @@ _lib.sas_batch_owned.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, _p, ctype
 _lib.sas_peel.argtypes = [_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _p, ctypes.POINTER(_p)]
 _lib.sas_batch_vet.argtypes = [_p, _p, _p, _p, _p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _p]
 EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_destroy",
-             "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16",
+             "sas_vet_set_adam", "sas_vet_set_state", "sas_vet_get_state", "sas_vet_get_bf16", "sas_vet_get_activations",
              "sas_vet_forward", "sas_vet_gradients", "sas_vet_apply_gradients",
              "sas_vet_train_step", "sas_vet_check", "sas_stamps_indexed", "sas_peaks", "sas_batch_peaks",
              "sas_batch_stamps", "sas_owned", "sas_batch_owned", "sas_batch_vet", "sas_peel"]
@@ -725,6 +726,14 @@ class Vetter:
         """The BF16 working copy as float32 values."""
         raw = np.zeros(self.n_params, np.uint16)
         _check(_lib.sas_vet_get_bf16(self._h, raw.ctypes.data))
+        return (raw.astype(np.uint32) << 16).view(np.float32)
+
+    def activations(self, layer: int, n: int) -> np.ndarray:
+        """The BF16 activations of layer 1..4 that the last batch stored (first n
+        samples), as float32: [n, 32, h, h] for the convolutions, [n, 64] for fc1."""
+        shape = {1: (32, 13, 13), 2: (32, 11, 11), 3: (32, 9, 9), 4: (64,)}[int(layer)]
+        raw = np.zeros((int(n),) + shape, np.uint16)
+        _check(_lib.sas_vet_get_activations(self._h, int(layer), int(n), raw.ctypes.data))
         return (raw.astype(np.uint32) << 16).view(np.float32)
 
     def forward(self, stamps_dev, n: int, logits_dev, index=None, stream=None):

@@ -34,6 +34,16 @@ def _fields(n, seed):
     return out
 
 
+def _assert_oracle(c, ids, n_pairs, ref):
+    """Element-by-element equality of a field's candidates and ids with the oracle's."""
+    assert len(c) == len(ref.cands), (len(c), len(ref.cands))
+    for fg, fo in [("v_idx", "v_idx"), ("bx", "bx"), ("by", "by"), ("count", "distinct"), ("raw", "raw"),
+                   ("id_off", "id_off"), ("id_len", "id_len")]:
+        assert np.array_equal(c[fg].astype(np.int64), ref.cands[fo].astype(np.int64)), fg
+    assert np.array_equal(ids.astype(np.int64), ref.ids.astype(np.int64))
+    assert n_pairs == ref.n_pairs
+
+
 def _single(grid, cat, n_min):
     r = sas.stack_catalog(grid, cat, n_min)
     c, ids = r.candidates()
@@ -42,18 +52,20 @@ def _single(grid, cat, n_min):
 
 def test_batch_equals_single_field_search():
     specs = _fields(7, 3)
-    fields, refs = [], []
+    fields, refs, orefs = [], [], []
     for w, n_min in specs:
         cat = W.load(w)
         g = sas.Grid(w.grid)
         x, y, e = _dev(cat)
         fields.append((g, x, y, e, cat.t, cat.ticks_per_hour, n_min))
         refs.append(_single(g, cat, n_min))
+        orefs.append(oracle.stack(cat, w.grid, n_min))
     b = sas.Batch(fields)
     for rep in range(2):  # two replays of the same graph
         b.run()
         for f, (c_ref, ids_ref, pairs_ref) in enumerate(refs):
             c, ids = b.candidates(f)
+            _assert_oracle(c, ids, b.field_info(f)["n_pairs"], orefs[f])
             assert np.array_equal(c, c_ref), (rep, f)
             assert np.array_equal(ids, ids_ref), (rep, f)
             assert b.field_info(f)["n_pairs"] == pairs_ref
@@ -151,3 +163,32 @@ def test_batch_with_per_field_tuned_options():
     for f, (c_ref, ids_ref) in enumerate(refs):
         c, ids = b.candidates(f)
         assert np.array_equal(c, c_ref) and np.array_equal(ids, ids_ref), f
+
+
+def test_full_size_uneven_fields_with_tuned_options_match_oracle():
+    """Four of the 60 full-size uneven fields (2048x4096 px, 111x111 lattice):
+    the fewest epochs, the most epochs, the most detections and the median
+    detection count, each with the autotuner's options for its size class, in
+    one batch; every field's candidates, ids and pair count byte for byte
+    against the oracle (OpenMP form over all host cores)."""
+    from paper_2509_26279_gb300 import tuning, vetting
+    ws = W.batched_fields(60)
+    load = [w.recipe.n_epochs * w.recipe.noise_per_epoch for w in ws]
+    pick = {int(np.argmin([w.recipe.n_epochs for w in ws])), int(np.argmax([w.recipe.n_epochs for w in ws])),
+            int(np.argmax(load)), int(np.argsort(load)[len(load) // 2])}
+    dev = torch.device("cuda")
+    fields = [vetting.Field(ws[i], dev) for i in sorted(pick)]
+    cache = tuning.TuneCache()
+    opts = []
+    for f in fields:
+        cache.tune(f)
+        opts.append(cache.opts_for(f))
+    b = sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, f.w.n_min) for f in fields], opts=opts)
+    b.run()
+    assert b.stats()[1] == 0  # no field left the batch
+    for k, f in enumerate(fields):
+        ref = oracle.stack(f.cat, f.w.grid, f.w.n_min, threads=0)
+        c, ids = b.candidates(k)
+        assert len(ref.cands) > 100
+        _assert_oracle(c, ids, b.field_info(k)["n_pairs"], ref)
+    b.destroy()

@@ -315,6 +315,18 @@ def test_full_decam_tno():
     assert info["n_pairs"] > 3e9
 
 
+def test_full_decam_tno_whole_list():
+    """The whole candidate list and id array of the full TNO field (2048x4096 px,
+    100 epochs, 111x111 lattice), byte for byte against the oracle run over all
+    host cores (its OpenMP form, equal to the single loop by its own pin)."""
+    w = W.decam_tno()
+    cat = W.load(w)
+    res = sas.stack_catalog(sas.Grid(w.grid), cat, w.n_min)
+    ref = oracle.stack(cat, w.grid, w.n_min, threads=0)
+    assert len(ref.cands) > 1000 and ref.n_pairs > 3e9
+    assert_same(res, ref)
+
+
 def test_full_fast_movers():
     info = _full_size_check(W.fast_movers(), n_ranges=2, n_cells_sample=30, seed=2)
     assert info["n_pairs"] > 1e11

@@ -173,6 +173,56 @@ def gpu_grad(vt, st, y):
     return g.cpu().numpy().astype(np.float64), float(loss.item())
 
 
+@pytest.mark.parametrize("n", [5, 40, 300, 512, 4096])
+def test_gradients_elementwise_within_bound(n):
+    """Every element, at the training batch (512) and the timing batch (4096)
+    as well as small ones, in two parts that together cover the whole path.
+
+    (1) The activations the kernels stored (sas_vet_get_activations), element
+    by element against the float64 oracle with BF16 storage: both are within
+    (l+1) u A_l of the exact network (the forward bound, A_l = the network run
+    with |w|, |b|), so they differ by at most 2 (l+1) u A_l.
+    (2) The gradient against the float64 oracle's backward run through those
+    same stored activations (so the ReLU masks are identical):
+    |g_gpu - g_ref| <= 4 * 2^-9 * A, A = the same backward with |w| and
+    |dL/dlogit| (every element is a sum of products; the kernels round the
+    deltas to TF32 (2^-11) in two layers and accumulate in FP32 (K 2^-24 <=
+    1.6e-4), so their error is a small multiple of 2^-11 of that sum).  A
+    mis-indexed element or a lost block partial anywhere fails."""
+    rng = np.random.default_rng(100 + n)
+    vt, params = make_vetter(13, max_batch=max(512, n), bias=0.05)
+    st = rand_stamps(rng, n)
+    y = (rng.random(n) < 0.5).astype(np.float64)
+    g, loss = gpu_grad(vt, st, y)
+    acts = {"x0": st.astype(np.float64) / 16.0}
+    for layer, key in enumerate(("a1", "a2", "a3", "a4"), start=1):
+        acts[key] = vt.activations(layer, n).astype(np.float64)
+    wb = V.bf16_round(params).astype(np.float64)
+    # (1) stored activations
+    _, a_s = V.forward(wb, st, V.bf16_store)
+    _, a_abs = V.forward(np.abs(wb), st)
+    for layer, key in enumerate(("a1", "a2", "a3", "a4"), start=1):
+        err = np.abs(acts[key] - a_s[key])
+        bound = 2 * (layer + 1) * U * a_abs[key]
+        assert np.all(err <= bound), (key, float(err.max()))
+    # (2) the backward through them
+    p = V.unflatten(wb)
+    logit = acts["a4"] @ p["fc2.w"] + p["fc2.b"][0]
+    assert abs(loss - V.bce_with_logits(logit, y)) <= 2.0 ** -16 * (1 + abs(loss))
+    g_logit = (1.0 / (1.0 + np.exp(-logit)) - y) / n
+    g_ref = V.backward(wb, acts, g_logit)
+    A = V.backward(np.abs(wb), acts, np.abs(g_logit))
+    err = np.abs(g - g_ref)
+    o = 0
+    for name, shape in V.SHAPES:
+        k = int(np.prod(shape))
+        sl = slice(o, o + k)
+        bound = 4 * 2.0 ** -9 * A[sl]
+        bad = np.nonzero(err[sl] > bound)[0]
+        assert bad.size == 0, (name, int(bad[0]), float(err[sl][bad[0]]), float(bound[bad[0]]))
+        o += k
+
+
 @pytest.mark.parametrize("n", [5, 40, 300])
 def test_gradients_match_float64(n):
     """Against the oracle with BF16 activation storage (the network's stated
