@@ -170,7 +170,7 @@ void sas_destroy_grid(sas_grid* grid);
 int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc);
 
 /* Weighted stacking -- the likelihood accumulation the paper proposes for
- * future work (Sec. 4): detection i carries an integer weight w[i] in
+ * future work (Sec. 5): detection i carries an integer weight w[i] in
  * [0, 255] (a fixed-point likelihood or S/N; uint8, in host or device memory
  * like the catalog arrays, indexed like them).  A cell's score is the sum over
  * epochs of the largest weight among that epoch's detections in the cell
@@ -311,7 +311,7 @@ int sas_cell_counts_noalloc(const sas_grid* grid, const sas_catalog* cat, const 
 /* ---- Candidate vetter ---------------------------------------------------------
  *
  * Filtering the search results better is the paper's suggested route to fainter
- * objects (Sec. 4).  The vetter scores each candidate with a small CNN from
+ * objects (Sec. 5).  The vetter scores each candidate with a small CNN from
  * its count stamp, so the search can run at a lower n_min.
  *
  * Stamp of candidate (v_idx, bx, by), kx = v_idx % nvx, ky = v_idx / nvx: a
@@ -554,7 +554,7 @@ int sas_vet_get_bf16(const sas_vet* vetter, uint16_t* out);
  * chunk or gradient batch of this vetter (sas_vet_forward runs in chunks of the
  * vetter's max_batch: its last chunk's activations are what remains).  n <=
  * max_batch samples are copied from the start of that batch.  Waits for the
- * device.  For inspection and tests (the backward of the network, Sec. 4's
+ * device.  For inspection and tests (the backward of the network, Sec. 5's
  * learned filter, runs from exactly these values).
  * Errors: SAS_ERR_ARG (NULL, layer outside 1..4, n > max_batch), SAS_ERR_CUDA. */
 int sas_vet_get_activations(const sas_vet* vetter, uint32_t layer, uint64_t n, uint16_t* out);

@@ -1,6 +1,6 @@
 """CPU oracle of the candidate vetter -- TEST INFRASTRUCTURE (float64 NumPy).
 
-The paper's conclusion (Sec. 4) names better filtering of the search results as
+The paper's conclusion (Sec. 5) names better filtering of the search results as
 the way to reach fainter objects without drowning in candidates.  The vetter is
 that filter: a small convolutional network that scores a candidate from its
 count stamp.  This module is the plain definition the GPU kernels are checked

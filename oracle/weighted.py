@@ -1,7 +1,7 @@
 """CPU oracle of likelihood-weighted stacking -- TEST INFRASTRUCTURE.
 
 The paper's discussion proposes accumulating each detection's likelihood instead
-of the 0/1 indicator of "detected in this epoch" (Sec. 4, future work).  The
+of the 0/1 indicator of "detected in this epoch" (Sec. 5, future work).  The
 weighted score of a cell (velocity, bin) generalises the distinct-epoch count:
 
     score = sum over epochs e of  max { w_i : detection i of epoch e in the cell }

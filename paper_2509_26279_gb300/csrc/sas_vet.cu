@@ -2,7 +2,7 @@
 // trained and run on the GPU (BF16 weights and activations, FP32 accumulation).
 //
 // Filtering the search results better is the paper's own suggestion for going
-// fainter (Sec. 4); this network is that filter.  Network (input = count / 16):
+// fainter (Sec. 5); this network is that filter.  Network (input = count / 16):
 //   conv1 9->32 3x3 valid + ReLU (15 -> 13), conv2 32->32 (13 -> 11) + ReLU,
 //   conv3 32->32 (11 -> 9) + ReLU, flatten (channel, row, column),
 //   fc1 2592 -> 64 + ReLU, fc2 64 -> 1 = logit;  loss: mean BCE with logits.

@@ -1,5 +1,5 @@
 """Training and judging the candidate vetter (the learned filter the paper's
-Sec. 4 calls for) on seeded synthetic fields.
+Sec. 5 calls for) on seeded synthetic fields.
 
 Forms compared on the same fields, each reporting its candidate list:
   plain   -- the paper's threshold at the field's N_min (every cell >= N_min);
