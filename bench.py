@@ -301,8 +301,10 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
               "plain": {"form": "one sas_stack per field, N_min = ceil(E/4)", "ms": round(ms_plain, 3),
                         "fields_per_s": round(n_fields / (ms_plain * 1e-3), 2), **score(plain_out)},
               "autotune": {"classes": len(cache.entries), "seconds": round(tune_s, 1),
-                           "choices": {k: [v["superbin"], v["velocity_block"]] for k, v in cache.entries.items()},
-                           "rule": "sas_autotune per size class (superbin x velocity_block sweep, median of 3)"},
+                           "choices": {k: tuning.shape_of(v) for k, v in cache.entries.items()},
+                           "ms": {k: v["ms"] for k, v in cache.entries.items()},
+                           "rule": "sas_autotune per size class: velocity tile {8x8, 8x4} x super-bin {1..4} x "
+                                   "tile_bx {planner, 32, 64} x velocity block {planner, 2, 4}, median of 3"},
               "vetter_training": {"fields": train_fields, "stamps": n_train, "epochs": epochs,
                                   "final_loss": round(hist[-1], 4), "seconds": round(train_s, 1),
                                   "threshold": round(tau, 4),

@@ -265,12 +265,16 @@ typedef struct sas_vet sas_vet;
 int sas_batch_vet(const sas_batch* batch, sas_vet* vetter, uint32_t* field_out, uint32_t* cand_out,
                   float* logit_out, uint64_t cap, uint64_t* n_out, void* stream);
 
-/* Autotuner: times sas_stack on (grid, cat, n_min) for each candidate pair of
- * superbin in {1, 2, 3} and velocity_block in {1, 2, 4, 8} (other fields of
- * *base kept; tile sizes chosen by the planner), `reps` timed runs each after
- * one warm-up, and returns in *best the options with the lowest median device
- * time of the whole search (*best_ms).  Every candidate gives the same
- * candidates; only the speed differs. */
+/* Autotuner: times sas_stack on (grid, cat, n_min) for every combination of
+ * the velocity tile (tile_kx x tile_ky in {8 x 8, 8 x 4}), the bin tile
+ * (superbin in {1, 2, 3, 4} bins per super-bin side, tile_bx in {planner, 32,
+ * 64} super-bins per spatial tile row, tile_by from the planner) and the
+ * velocity block (velocity_block in {planner, 2, 4}); a field of *base that is
+ * set (nonzero) is kept instead of swept, and combinations the planner
+ * rejects for this field are skipped.  `reps` timed runs each after one
+ * warm-up; *best gets the options with the lowest median device time of the
+ * whole search (*best_ms).  Every combination gives the same candidates
+ * (Sec. 2.1 steps 1-3 are independent of the tiling); only the speed differs. */
 int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
                  const sas_opts* base, uint32_t reps, void* stream, sas_opts* best,
                  float* best_ms);

@@ -9,6 +9,7 @@
 // enough, or whose counters wrapped, is recomputed exactly on the single-field
 // path, so the results always equal sas_stack's.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -34,14 +35,21 @@ struct sas_batch {
   unsigned long long* h_c64 = nullptr;     // pinned [n_fields][kC64N]
   uint32_t* d_ctr = nullptr;
   unsigned long long* d_c64 = nullptr;
-  unsigned long long* d_work = nullptr;
-  StackArgs* d_args = nullptr;
-  unsigned long long* d_unit_base = nullptr;
   uint32_t* d_ecount_all = nullptr;
   size_t ecount_words = 0;
-  int kx = 0, ky = 0, cb = 0;
-  size_t stack_smem = 0;
-  int stack_grid = 0;
+  // Fields grouped by stack kernel configuration (velocity tile and counter
+  // width): one persistent stack launch per group, each over its own work
+  // counter and its fields' units.
+  struct Group {
+    int kx = 0, ky = 0, cb = 0;
+    std::vector<uint32_t> fields;
+    size_t smem = 0;
+    int grid = 0;
+    StackArgs* d_args = nullptr;
+    unsigned long long* d_unit_base = nullptr;
+    unsigned long long* d_work = nullptr;
+  };
+  std::vector<Group> groups;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -64,13 +72,15 @@ cudaError_t record_pass(sas_batch* b, cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(b->d_ctr, 0, (size_t)b->n_fields * kCtrN * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b->d_c64, 0, (size_t)b->n_fields * kC64N * 8, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(b->d_work, 0, 8, s)) != cudaSuccess) return e;
+  for (const sas_batch::Group& g : b->groups)
+    if ((e = cudaMemsetAsync(g.d_work, 0, 8, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b->d_ecount_all, 0, b->ecount_words * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(b->dev.bucket_count, 0, b->dev.total_buckets * 4, s)) != cudaSuccess) return e;
   if ((e = batch_launch_prep(b->dev, s)) != cudaSuccess) return e;
-  if ((e = launch_stack_multi(b->kx, b->ky, b->cb, b->d_args, b->d_unit_base, (int)b->n_fields,
-                              b->d_work, b->stack_smem, b->stack_grid, s)) != cudaSuccess)
-    return e;
+  for (const sas_batch::Group& g : b->groups)
+    if ((e = launch_stack_multi(g.kx, g.ky, g.cb, g.d_args, g.d_unit_base, (int)g.fields.size(), g.d_work,
+                                g.smem, g.grid, s)) != cudaSuccess)
+      return e;
   if ((e = batch_launch_post(b->dev, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b->h_ctr, b->d_ctr, (size_t)b->n_fields * kCtrN * 4,
                            cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -138,7 +148,15 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     b->n_min.push_back(n_min[f]);
     sas_opts o{};
     if (opts) o = opts[f];
-    o.counter_bits = 8;  // every field in one launch shares one counter width
+    // 8-bit counters (start 128 - n_min) wrap past 128 + n_min detections in
+    // one super-bin: a field whose brightest mover (one detection per epoch)
+    // plus a generous noise allowance could get there counts in 16 bits.  A
+    // wrap is still detected and recomputed exactly; this keeps it rare.
+    if (o.counter_bits == 0) {
+      const double lam = (double)c.n * 9.0 / ((double)desc.nbx * desc.nby);  // per 3 x 3-bin super-bin
+      const double reach = (double)c.n_epochs + lam + 6.0 * std::sqrt(lam) + 2.0;
+      o.counter_bits = reach >= 128.0 + n_min[f] ? 16 : 8;
+    }
     o.v_begin = o.v_end = 0;
     b->opts.push_back(o);
     FieldPlan fp;
@@ -148,32 +166,21 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     b->plans.push_back(fp);
   }
   if (rc != SAS_OK) { free_batch(b); return rc; }
-  // one launch needs one tile shape: where the default 8 x 8 tile fell back to
-  // 8 x 4 for some fields, plan every field with 8 x 4
-  bool mixed = false;
-  for (const FieldPlan& fp : b->plans) mixed |= fp.tc.ky != b->plans[0].tc.ky;
-  if (mixed) {
-    for (uint32_t f = 0; f < n_fields && rc == SAS_OK; ++f) {
-      if (b->opts[f].tile_ky) continue;  // chosen by the caller: left as is (checked below)
-      b->opts[f].tile_ky = 4;
-      sas_grid_desc desc;
-      rc = sas_grid_get_desc(b->grids[f], &desc);
-      const sas_catalog& c = b->cats[f];
-      if (rc == SAS_OK)
-        rc = plan_field(desc, c.n, c.n_epochs, c.t, c.ticks_per_hour, b->n_min[f], 0,
-                        (uint64_t)desc.nvx * desc.nvy, b->opts[f], di, &b->plans[f]);
+  // group the fields by stack kernel configuration
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const TileCfg& tc = b->plans[f].tc;
+    sas_batch::Group* g = nullptr;
+    for (sas_batch::Group& h : b->groups)
+      if (h.kx == tc.kx && h.ky == tc.ky && h.cb == tc.cb) g = &h;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->kx = tc.kx;
+      g->ky = tc.ky;
+      g->cb = tc.cb;
     }
-    if (rc != SAS_OK) { free_batch(b); return rc; }
-  }
-  b->kx = b->plans[0].tc.kx;
-  b->ky = b->plans[0].tc.ky;
-  b->cb = 8;
-  for (const FieldPlan& fp : b->plans) {
-    if (fp.tc.kx != b->kx || fp.tc.ky != b->ky) {
-      free_batch(b);
-      return set_error(SAS_ERR_ARG, "all fields of a batch need the same tile_kx and tile_ky");
-    }
-    b->stack_smem = std::max(b->stack_smem, fp.tc.smem);
+    g->fields.push_back(f);
+    g->smem = std::max(g->smem, tc.smem);
   }
   // --- sizes and arena layout --------------------------------------------------
   std::vector<unsigned long long> det_off(n_fields + 1, 0), tab_off(n_fields + 1, 0),
@@ -215,15 +222,17 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
   std::vector<int32_t*> f_sxt(n_fields), f_syt(n_fields);
   std::vector<int64_t*> f_t(n_fields), f_dt(n_fields);
   regs.push_back({(void**)&B.fields, n_fields * sizeof(BatchField)});
-  regs.push_back({(void**)&b->d_args, n_fields * sizeof(StackArgs)});
-  regs.push_back({(void**)&b->d_unit_base, (n_fields + 1) * 8});
+  for (sas_batch::Group& g : b->groups) {
+    regs.push_back({(void**)&g.d_args, g.fields.size() * sizeof(StackArgs)});
+    regs.push_back({(void**)&g.d_unit_base, (g.fields.size() + 1) * 8});
+    regs.push_back({(void**)&g.d_work, 8});
+  }
   regs.push_back({(void**)&B.det_off, (n_fields + 1) * 8});
   regs.push_back({(void**)&B.tab_off, (n_fields + 1) * 8});
   regs.push_back({(void**)&B.emit_off, (n_fields + 1) * 8});
   regs.push_back({(void**)&B.cand_off, (n_fields + 1) * 8});
   regs.push_back({(void**)&b->d_ctr, (size_t)n_fields * kCtrN * 4});
   regs.push_back({(void**)&b->d_c64, (size_t)n_fields * kC64N * 8});
-  regs.push_back({(void**)&b->d_work, 8});
   regs.push_back({(void**)&b->d_ecount_all, b->ecount_words * 4});
   regs.push_back({(void**)&B.bucket_count, B.total_buckets * 4});
   regs.push_back({(void**)&B.boff, (B.total_buckets + 1) * 4});
@@ -280,7 +289,7 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     sa.n_pairs = c64 + kC64Pairs;
     sa.balance = c64 + kC64Balance;
     sa.flags = ctr + kCtrFlags;
-    sa.tile_counter = b->d_work;
+    sa.tile_counter = nullptr;  // the group's work counter drives the multi-field launch
     BatchField& bf = b->hf[f];
     memset(&bf, 0, sizeof(bf));
     bf.args = sa;
@@ -308,17 +317,31 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     if ((ce = cudaMemcpyAsync(f_t[f], c.t, fp.g.E * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
   }
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.fields, b->hf.data(), n_fields * sizeof(BatchField), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_args, hargs.data(), n_fields * sizeof(StackArgs), cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_unit_base, unit_base.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  // per group: its fields' stack arguments and a unit base over its own units
+  std::vector<std::vector<StackArgs>> gargs(b->groups.size());
+  std::vector<std::vector<unsigned long long>> gbase(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    sas_batch::Group& g = b->groups[k];
+    gbase[k].assign(1, 0ull);
+    for (uint32_t f : g.fields) {
+      gargs[k].push_back(hargs[f]);
+      gbase[k].push_back(gbase[k].back() + hargs[f].n_tiles);
+    }
+    g.grid = (int)std::min<unsigned long long>((unsigned long long)di.sms, std::max<unsigned long long>(gbase[k].back(), 1));
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(g.d_args, gargs[k].data(), g.fields.size() * sizeof(StackArgs), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(g.d_unit_base, gbase[k].data(), (g.fields.size() + 1) * 8, cudaMemcpyHostToDevice, s);
+  }
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.det_off, det_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.tab_off, tab_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.emit_off, emit_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.cand_off, cand_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  if (ce == cudaSuccess) ce = stack_set_smem_attr(b->kx, b->ky, b->cb, b->stack_smem);
+  for (const sas_batch::Group& g : b->groups)
+    if (ce == cudaSuccess) ce = stack_set_smem_attr(g.kx, g.ky, g.cb, g.smem);
   if (ce == cudaSuccess) ce = batch_set_attrs();
   if (ce != cudaSuccess) { rc = cuda_err(ce, "batch setup"); free_batch(b); return rc; }
-  b->stack_grid = (int)std::min<unsigned long long>((unsigned long long)di.sms, std::max<unsigned long long>(unit_base[n_fields], 1));
   // --- record the pass as a graph ---------------------------------------------
   cudaStream_t cs;
   if ((ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_err(ce, "stream"); free_batch(b); return rc; }
@@ -602,10 +625,24 @@ int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, c
   float best_t = 1e30f;
   sas_opts best_o = o0;
   bool any = false;
-  for (uint32_t sb : {1u, 2u, 3u}) {
-    for (uint32_t vb : {1u, 2u, 4u, 8u}) {
+  // the velocity tile (lattice points per tile) x the bin tile (super-bin side
+  // and spatial tile width) x the velocity block, each where the caller left
+  // it open; 0 leaves the choice to the planner
+  std::vector<std::pair<uint32_t, uint32_t>> vtiles = {{8u, 8u}, {8u, 4u}};
+  if (o0.tile_kx || o0.tile_ky) vtiles = {{o0.tile_kx, o0.tile_ky}};
+  std::vector<uint32_t> sbs = {1u, 2u, 3u, 4u}, vbs = {0u, 2u, 4u}, bxs = {0u, 32u, 64u};
+  if (o0.superbin) sbs = {o0.superbin};
+  if (o0.velocity_block) vbs = {o0.velocity_block};
+  if (o0.tile_bx || o0.tile_by) bxs = {o0.tile_bx};
+  for (const auto& vt : vtiles)
+  for (uint32_t sb : sbs)
+  for (uint32_t bx : bxs)
+    for (uint32_t vb : vbs) {
       sas_opts o = o0;
+      o.tile_kx = vt.first;
+      o.tile_ky = vt.second;
       o.superbin = sb;
+      o.tile_bx = bx;
       o.velocity_block = vb;
       std::vector<float> ts;
       int rc = SAS_OK;
@@ -627,7 +664,6 @@ int sas_autotune(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min, c
         any = true;
       }
     }
-  }
   if (!any) return set_error(SAS_ERR_ARG, "no tile configuration fits this field");
   *best = best_o;
   if (best_ms) *best_ms = best_t;

@@ -1,11 +1,14 @@
 """Per-size-class tile choices from the autotuner, cached as JSON.
 
-sas_autotune times the whole search for each (super-bin size, velocity block)
-pair on one field and returns the fastest.  Fields of similar shape -- the same
+sas_autotune times the whole search for each velocity tile (lattice points
+per tile) x bin tile (super-bin side, spatial tile width) x velocity block on
+one field and returns the fastest.  Fields of similar shape -- the same
 lattice and bin, similar epoch count, detection density and threshold -- share
 the answer, so a batch of many uneven fields is tuned once per size class and
 each field takes its class's options.  The cache is a JSON object
-{class key: {"superbin": s, "velocity_block": b, "ms": t, "device": name}}
+{class key: {"tile_kx": kx, "tile_ky": ky, "superbin": s, "tile_bx": bx,
+"tile_by": by, "velocity_block": b, "ms": t, "device": name}} (0: the planner's
+choice for that field)
 that can be written to disk and reused across runs on the same GPU model.
 
 Host logic only: the timing runs in the library (sas_autotune).
@@ -18,6 +21,15 @@ import os
 from typing import Dict, Optional
 
 import numpy as np
+
+
+OPTION_KEYS = ("tile_kx", "tile_ky", "superbin", "tile_bx", "tile_by", "velocity_block")
+
+
+def shape_of(entry: dict) -> str:
+    """A cache entry's choice as text: velocity tile x bin tile, velocity block."""
+    return (f"{entry.get('tile_kx', 0)}x{entry.get('tile_ky', 0)} lattice points, super-bin {entry['superbin']}, "
+            f"tile_bx {entry.get('tile_bx', 0) or 'planner'}, velocity block {entry['velocity_block'] or 'planner'}")
 
 
 def size_class(n_epochs: int, n_detections: int, grid, n_min: int) -> str:
@@ -62,7 +74,9 @@ class TuneCache:
         if key not in self.entries:
             best, ms = sas.sas_autotune(field.grid, field.dx, field.dy, field.de, field.cat.t,
                                         field.cat.ticks_per_hour, field.w.n_min, reps=reps)
-            self.entries[key] = {"superbin": int(best.superbin), "velocity_block": int(best.velocity_block),
+            self.entries[key] = {"tile_kx": int(best.tile_kx), "tile_ky": int(best.tile_ky),
+                                 "superbin": int(best.superbin), "tile_bx": int(best.tile_bx),
+                                 "tile_by": int(best.tile_by), "velocity_block": int(best.velocity_block),
                                  "ms": round(float(ms), 4), "device": device_name}
         return self.entries[key]
 
@@ -72,4 +86,4 @@ class TuneCache:
         e = self.lookup(size_class(field.E, field.cat.n, field.w.grid, field.w.n_min))
         if e is None:
             return sas.make_opts()
-        return sas.make_opts(superbin=e["superbin"], velocity_block=e["velocity_block"])
+        return sas.make_opts(**{k: e.get(k, 0) for k in OPTION_KEYS})

@@ -136,7 +136,8 @@ def test_autotune_returns_a_valid_faster_config():
     g = sas.Grid(w.grid)
     x, y, e = _dev(cat)
     best, ms = sas.sas_autotune(g, x, y, e, cat.t, cat.ticks_per_hour, 10, reps=2)
-    assert best.superbin in (1, 2, 3) and best.velocity_block in (1, 2, 4, 8) and ms > 0
+    assert best.superbin in (1, 2, 3, 4) and best.velocity_block in (0, 2, 4) and ms > 0
+    assert (best.tile_kx, best.tile_ky) in ((8, 8), (8, 4)) and best.tile_bx in (0, 32, 64)
     r = sas.stack_catalog(g, cat, 10, opts=best)
     c, ids = r.candidates()
     c0, ids0, _ = _single(g, cat, 10)
@@ -191,4 +192,36 @@ def test_full_size_uneven_fields_with_tuned_options_match_oracle():
         c, ids = b.candidates(k)
         assert len(ref.cands) > 100
         _assert_oracle(c, ids, b.field_info(k)["n_pairs"], ref)
+    b.destroy()
+
+
+def test_batch_mixes_tile_shapes_and_counter_widths():
+    """One batch whose fields need different stack kernels -- 8 x 8 and 8 x 4
+    velocity tiles, and 16-bit counters for fields whose brightest mover could
+    wrap an 8-bit counter (many epochs, low threshold) -- runs one persistent
+    launch per kernel and still equals the oracle field by field, with no
+    field recomputed on the single-field path."""
+    # (epochs, N_min, movers, noise fraction, tile_ky): 150 and 140 epochs at
+    # N_min 20 and 12 could pass 128 + N_min detections in a super-bin
+    specs = [(150, 20, 3, 0.03, 8), (60, 15, 20, 0.05, 8), (140, 12, 3, 0.02, 4), (90, 23, 20, 0.05, 4)]
+    fields, orefs, opts = [], [], []
+    for i, (E, n_min, movers, frac, ky) in enumerate(specs):
+        w = W.scaled(W.decam_tno(), frac_noise=frac, width_px=600, height_px=500, n_epochs=E, n_movers=movers,
+                     grid_half=10, seed=1700 + i)
+        cat = W.load(w)
+        g = sas.Grid(w.grid)
+        x, y, e = _dev(cat)
+        fields.append((g, x, y, e, cat.t, cat.ticks_per_hour, n_min))
+        opts.append(sas.make_opts(tile_kx=8, tile_ky=ky))
+        orefs.append(oracle.stack(cat, w.grid, n_min))
+    b = sas.Batch(fields, opts=opts)
+    b.run()
+    widths = set()
+    for f, ref in enumerate(orefs):
+        c, ids = b.candidates(f)
+        info = b.field_info(f)
+        widths.add((info["tile_ky"], info["counter_bits"]))
+        _assert_oracle(c, ids, info["n_pairs"], ref)
+    assert widths == {(8, 16), (8, 8), (4, 16), (4, 8)}, widths
+    assert b.stats()[1] == 0
     b.destroy()
