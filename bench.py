@@ -303,6 +303,7 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
               "autotune": {"classes": len(cache.entries), "seconds": round(tune_s, 1),
                            "choices": {k: tuning.shape_of(v) for k, v in cache.entries.items()},
                            "ms": {k: v["ms"] for k, v in cache.entries.items()},
+                           "planner_ms": {k: v.get("planner_ms") for k, v in cache.entries.items()},
                            "rule": "sas_autotune per size class: velocity tile {8x8, 8x4} x super-bin {1..4} x "
                                    "tile_bx {planner, 32, 64} x velocity block {planner, 2, 4}, median of 3"},
               "vetter_training": {"fields": train_fields, "stamps": n_train, "epochs": epochs,
@@ -310,6 +311,8 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                                   "threshold": round(tau, 4),
                                   "threshold_rule": "purity 0.95 on 10 separate calibration fields"}}
     for name, thr, desc in (("batched_vetted", lambda f: f.w.n_min, "batch at N_min = ceil(E/4)"),
+                            ("batched_vetted_e6", lambda f: -(-f.E // 6), "batch at N_min = ceil(E/6)"),
+                            ("batched_vetted_e8", lambda f: -(-f.E // 8), "batch at N_min = ceil(E/8)"),
                             ("batched_vetted_low", lambda f: vetting.n_low(f.E),
                              "batch at N_min = max(5, ceil(E/14))")):
         batch = make_batch(thr)
@@ -332,6 +335,9 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                                        "calibrated threshold",
                         "ms": round(ms, 3),
                         "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
+                        "rebuilds": int(batch.rebuilds),
+                        "candidates_searched": int(sum(batch.field_info(k)["n_candidates"]
+                                                       for k in range(len(fields)))),
                         **score(per_field),
                         "dedup": {"form": "the same decision on the ownership-selected candidates only",
                                   **score(per_field_dedup)}}

@@ -236,9 +236,13 @@ int sas_batch_field_info(const sas_batch* batch, uint32_t field, sas_result_info
 int sas_batch_candidates(const sas_batch* batch, uint32_t field, sas_candidate* out,
                          uint64_t cap, uint64_t* n_total, uint32_t* ids, uint64_t ids_cap,
                          uint64_t* n_ids_total, int on_device);
-/* Device time (ms, CUDA events) of the last replayed pass and the number of
- * field fallbacks so far. */
-int sas_batch_stats(const sas_batch* batch, float* ms_last, uint64_t* fallbacks);
+/* Device time (ms, CUDA events) of the last replayed pass, the number of field
+ * fallbacks (fields recomputed on the single-field path: a counter wrapped, or
+ * the grown capacities would not fit in device memory) and the number of
+ * rebuilds so far (a replay that found a field over its key, emission or id
+ * capacity grows those capacities to what the field reported, rebuilds the
+ * arena and the graph, and replays).  Any output may be NULL. */
+int sas_batch_stats(const sas_batch* batch, float* ms_last, uint64_t* fallbacks, uint64_t* rebuilds);
 void sas_batch_destroy(sas_batch* batch);
 /* sas_peaks, sas_stamps and sas_owned for field `field` of the last run (idx NULL in
  * sas_batch_stamps: candidates 0..count). */

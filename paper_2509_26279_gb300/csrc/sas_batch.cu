@@ -5,9 +5,11 @@
 // sas_batch_create plans every field (tile shape from its own opts, e.g. the
 // autotuner's pick for its size class), lays out one device arena for all of
 // them with fixed capacities, and captures the whole device pipeline into a
-// graph.  sas_batch_run replays the graph; a field whose capacities were not
-// enough, or whose counters wrapped, is recomputed exactly on the single-field
-// path, so the results always equal sas_stack's.
+// graph.  sas_batch_run replays the graph; when a field needed more candidate,
+// emission or id slots than the arena has, the run grows them to what the
+// field reported, rebuilds the arena and the graph, and replays; a field whose
+// counters wrapped (or whose grown capacities would not fit) is recomputed
+// exactly on the single-field path, so the results always equal sas_stack's.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,8 +29,14 @@ struct sas_batch {
   std::vector<sas_opts> opts;
   std::vector<FieldPlan> plans;
   std::vector<BatchField> hf;              // host copy of the field descriptors
-  std::vector<uint32_t> key_cap;
+  // Capacities of the arena: candidate-key slots per field (one power of two for
+  // all fields: the segment of the segmented sort), emission slots and id slots
+  // per field.  A replay that finds a field over one of them rebuilds the arena
+  // and the graph at the sizes it reported, and replays.
+  uint32_t key_seg = kBatchKeyCap;
+  std::vector<uint32_t> emit_cap;
   std::vector<uint64_t> ids_cap;
+  uint64_t rebuilds = 0;
   BatchDev dev{};
   void* arena = nullptr;
   uint32_t* h_ctr = nullptr;               // pinned [n_fields][kCtrN]
@@ -89,18 +97,208 @@ cudaError_t record_pass(sas_batch* b, cudaStream_t s) {
                          cudaMemcpyDeviceToHost, s);
 }
 
-void free_batch(sas_batch* b) {
-  if (!b) return;
+// Releases the device arena and the recorded pass (capacities and plans stay).
+void free_pass(sas_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->ev0) cudaEventDestroy(b->ev0);
-  if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->arena) cudaFree(b->arena);
   if (b->h_ctr) cudaFreeHost(b->h_ctr);
   if (b->h_c64) cudaFreeHost(b->h_c64);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->arena = nullptr;
+  b->h_ctr = nullptr;
+  b->h_c64 = nullptr;
+}
+
+void free_batch(sas_batch* b) {
+  if (!b) return;
+  free_pass(b);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
   for (sas_result* r : b->fallback) sas_result_free(r);
   for (sas_grid* g : b->grids) sas_destroy_grid(g);
   delete b;
+}
+
+}  // namespace
+
+namespace {
+
+// Lays out the device arena for the current capacities, writes the field
+// descriptors and records one pass of the whole pipeline as a graph.
+int build_pass(sas_batch* b, const DevInfo& di, cudaStream_t s) {
+  const uint32_t n_fields = b->n_fields;
+  int rc = SAS_OK;
+  cudaError_t ce = cudaSuccess;
+  // --- sizes and arena layout --------------------------------------------------
+  std::vector<unsigned long long> det_off(n_fields + 1, 0), tab_off(n_fields + 1, 0),
+      emit_off(n_fields + 1, 0), cand_off(n_fields + 1, 0), unit_base(n_fields + 1, 0);
+  std::vector<uint64_t> bucket_base(n_fields + 1, 0), ecount_base(n_fields + 1, 0);
+  std::vector<StackArgs> hargs(n_fields);
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    const sas_catalog& c = b->cats[f];
+    det_off[f + 1] = det_off[f] + c.n;
+    tab_off[f + 1] = tab_off[f] + (unsigned long long)(fp.g.nvx + fp.g.nvy) * fp.g.E;
+    emit_off[f + 1] = emit_off[f] + b->emit_cap[f];
+    cand_off[f + 1] = cand_off[f] + b->key_seg;
+    bucket_base[f + 1] = bucket_base[f] + fp.nb;
+    ecount_base[f + 1] = ecount_base[f] + fp.g.E;
+    fill_stack_args(fp, b->n_min[f], &hargs[f]);
+    unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
+  }
+  BatchDev& B = b->dev;
+  B.n_fields = (int)n_fields;
+  B.total_dets = det_off[n_fields];
+  B.total_buckets = bucket_base[n_fields];
+  B.total_tab = tab_off[n_fields];
+  B.total_emit = emit_off[n_fields];
+  B.total_cand = cand_off[n_fields];
+  B.key_seg = b->key_seg;
+  b->ecount_words = ecount_base[n_fields];
+  // one arena: [region sizes computed here]
+  struct Reg { void** p; size_t bytes; };
+  std::vector<Reg> regs;
+  std::vector<Emit*> f_emits(n_fields);
+  std::vector<Key*> f_keys(n_fields);
+  std::vector<unsigned long long*> f_idoff(n_fields);
+  std::vector<uint32_t*> f_ids(n_fields), f_idt(n_fields);
+  std::vector<sas_candidate*> f_cands(n_fields);
+  std::vector<int32_t*> f_sxt(n_fields), f_syt(n_fields);
+  std::vector<int64_t*> f_t(n_fields), f_dt(n_fields);
+  regs.push_back({(void**)&B.fields, n_fields * sizeof(BatchField)});
+  for (sas_batch::Group& g : b->groups) {
+    regs.push_back({(void**)&g.d_args, g.fields.size() * sizeof(StackArgs)});
+    regs.push_back({(void**)&g.d_unit_base, (g.fields.size() + 1) * 8});
+    regs.push_back({(void**)&g.d_work, 8});
+  }
+  regs.push_back({(void**)&B.det_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.tab_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.emit_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&B.cand_off, (n_fields + 1) * 8});
+  regs.push_back({(void**)&b->d_ctr, (size_t)n_fields * kCtrN * 4});
+  regs.push_back({(void**)&b->d_c64, (size_t)n_fields * kC64N * 8});
+  regs.push_back({(void**)&b->d_ecount_all, b->ecount_words * 4});
+  regs.push_back({(void**)&B.bucket_count, B.total_buckets * 4});
+  regs.push_back({(void**)&B.boff, (B.total_buckets + 1) * 4});
+  regs.push_back({(void**)&B.cursor, B.total_buckets * 4});
+  regs.push_back({(void**)&B.scan_scratch, scan_scratch_elems(B.total_buckets) * 4});
+  regs.push_back({(void**)&B.bucket_of, B.total_dets * 4});
+  regs.push_back({(void**)&B.dets, B.total_dets * sizeof(Det)});
+  regs.push_back({(void**)&B.keys_all, B.total_cand * sizeof(Key)});
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    regs.push_back({(void**)&f_t[f], fp.g.E * 8});
+    regs.push_back({(void**)&f_dt[f], fp.g.E * 8});
+    regs.push_back({(void**)&f_sxt[f], (size_t)fp.g.nvx * fp.g.E * 4});
+    regs.push_back({(void**)&f_syt[f], (size_t)fp.g.nvy * fp.g.E * 4});
+    regs.push_back({(void**)&f_emits[f], (emit_off[f + 1] - emit_off[f]) * sizeof(Emit)});
+    regs.push_back({(void**)&f_idoff[f], ((size_t)b->key_seg + 1) * 8});
+    regs.push_back({(void**)&f_ids[f], b->ids_cap[f] * 4});
+    regs.push_back({(void**)&f_idt[f], b->ids_cap[f] * 4});
+    regs.push_back({(void**)&f_cands[f], (size_t)b->key_seg * sizeof(sas_candidate)});
+  }
+  size_t total = 0;
+  for (const Reg& r : regs) total += align256(std::max<size_t>(r.bytes, 1));
+  if ((ce = cudaMalloc(&b->arena, total)) != cudaSuccess) { rc = cuda_err(ce, "batch arena"); return rc; }
+  {
+    size_t off = 0;
+    for (const Reg& r : regs) {
+      *r.p = static_cast<char*>(b->arena) + off;
+      off += align256(std::max<size_t>(r.bytes, 1));
+    }
+  }
+  for (uint32_t f = 0; f < n_fields; ++f) f_keys[f] = B.keys_all + cand_off[f];
+  if ((ce = cudaMallocHost((void**)&b->h_ctr, (size_t)n_fields * kCtrN * 4)) != cudaSuccess ||
+      (ce = cudaMallocHost((void**)&b->h_c64, (size_t)n_fields * kC64N * 8)) != cudaSuccess) {
+    return cuda_err(ce, "pinned counters");
+  }
+  // --- field descriptors ---------------------------------------------------------
+  b->hf.resize(n_fields);
+  for (uint32_t f = 0; f < n_fields; ++f) {
+    const FieldPlan& fp = b->plans[f];
+    const sas_catalog& c = b->cats[f];
+    StackArgs& sa = hargs[f];
+    uint32_t* ctr = b->d_ctr + (size_t)f * kCtrN;
+    unsigned long long* c64 = b->d_c64 + (size_t)f * kC64N;
+    sa.dets = B.dets;
+    sa.boff = B.boff + bucket_base[f];
+    sa.ecount = b->d_ecount_all + ecount_base[f];
+    sa.sxt = f_sxt[f];
+    sa.syt = f_syt[f];
+    sa.emits = f_emits[f];
+    sa.emit_cap = (uint32_t)(emit_off[f + 1] - emit_off[f]);
+    sa.n_emit = ctr + kCtrEmit;
+    sa.n_pairs = c64 + kC64Pairs;
+    sa.balance = c64 + kC64Balance;
+    sa.flags = ctr + kCtrFlags;
+    sa.tile_counter = nullptr;  // the group's work counter drives the multi-field launch
+    BatchField& bf = b->hf[f];
+    memset(&bf, 0, sizeof(bf));
+    bf.args = sa;
+    bf.x = c.x;
+    bf.y = c.y;
+    bf.epoch = c.epoch;
+    bf.t = f_t[f];
+    bf.E = fp.g.E;
+    bf.emit_cap = sa.emit_cap;
+    bf.ecount = const_cast<uint32_t*>(sa.ecount);
+    bf.dt = f_dt[f];
+    bf.t0 = reinterpret_cast<long long*>(c64 + kC64T0);
+    bf.sxt = f_sxt[f];
+    bf.syt = f_syt[f];
+    bf.bucket_base = bucket_base[f];
+    bf.counters = ctr;
+    bf.keys = f_keys[f];
+    bf.key_cap = b->key_seg;
+    bf.max_out = b->opts[f].max_candidates ? (uint32_t)std::min<uint64_t>(b->opts[f].max_candidates, b->key_seg) : b->key_seg;
+    bf.id_off = f_idoff[f];
+    bf.ids = f_ids[f];
+    bf.ids_tmp = f_idt[f];
+    bf.ids_cap = b->ids_cap[f];
+    bf.cands = f_cands[f];
+    if ((ce = cudaMemcpyAsync(f_t[f], c.t, fp.g.E * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.fields, b->hf.data(), n_fields * sizeof(BatchField), cudaMemcpyHostToDevice, s);
+  // per group: its fields' stack arguments and a unit base over its own units
+  std::vector<std::vector<StackArgs>> gargs(b->groups.size());
+  std::vector<std::vector<unsigned long long>> gbase(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    sas_batch::Group& g = b->groups[k];
+    gbase[k].assign(1, 0ull);
+    for (uint32_t f : g.fields) {
+      gargs[k].push_back(hargs[f]);
+      gbase[k].push_back(gbase[k].back() + hargs[f].n_tiles);
+    }
+    g.grid = (int)std::min<unsigned long long>((unsigned long long)di.sms, std::max<unsigned long long>(gbase[k].back(), 1));
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(g.d_args, gargs[k].data(), g.fields.size() * sizeof(StackArgs), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(g.d_unit_base, gbase[k].data(), (g.fields.size() + 1) * 8, cudaMemcpyHostToDevice, s);
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.det_off, det_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.tab_off, tab_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.emit_off, emit_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.cand_off, cand_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  for (const sas_batch::Group& g : b->groups)
+    if (ce == cudaSuccess) ce = stack_set_smem_attr(g.kx, g.ky, g.cb, g.smem);
+  if (ce == cudaSuccess) ce = batch_set_attrs();
+  if (ce != cudaSuccess) { rc = cuda_err(ce, "batch setup"); return rc; }
+  // --- record the pass as a graph ---------------------------------------------
+  cudaStream_t cs;
+  if ((ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_err(ce, "stream"); return rc; }
+  ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t ce2 = ce == cudaSuccess ? record_pass(b, cs) : ce;
+  cudaGraph_t g = nullptr;
+  if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &g);
+  if (ce == cudaSuccess) ce = ce2;
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, g, 0);
+  b->graph = g;
+  cudaStreamDestroy(cs);
+  if (ce != cudaSuccess) { rc = cuda_err(ce, "graph capture"); return rc; }
+  return SAS_OK;
 }
 
 }  // namespace
@@ -162,6 +360,13 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     FieldPlan fp;
     rc = plan_field(desc, c.n, c.n_epochs, c.t, c.ticks_per_hour, n_min[f], 0,
                     (uint64_t)desc.nvx * desc.nvy, o, di, &fp);
+    if (rc != SAS_OK && (o.tile_bx || o.tile_by) && (!opts || opts[f].counter_bits != o.counter_bits)) {
+      // a spatial tile chosen for other counters (e.g. tuned with 8-bit ones)
+      // may not fit the wider counters picked here: the planner sizes it
+      o.tile_bx = o.tile_by = 0;
+      rc = plan_field(desc, c.n, c.n_epochs, c.t, c.ticks_per_hour, n_min[f], 0,
+                      (uint64_t)desc.nvx * desc.nvy, o, di, &fp);
+    }
     if (rc != SAS_OK) break;
     b->plans.push_back(fp);
   }
@@ -182,178 +387,13 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     g->fields.push_back(f);
     g->smem = std::max(g->smem, tc.smem);
   }
-  // --- sizes and arena layout --------------------------------------------------
-  std::vector<unsigned long long> det_off(n_fields + 1, 0), tab_off(n_fields + 1, 0),
-      emit_off(n_fields + 1, 0), cand_off(n_fields + 1, 0), unit_base(n_fields + 1, 0);
-  std::vector<uint64_t> bucket_base(n_fields + 1, 0), ecount_base(n_fields + 1, 0);
-  std::vector<StackArgs> hargs(n_fields);
+  b->emit_cap.resize(n_fields);
+  b->ids_cap.resize(n_fields);
   for (uint32_t f = 0; f < n_fields; ++f) {
-    const FieldPlan& fp = b->plans[f];
-    const sas_catalog& c = b->cats[f];
-    det_off[f + 1] = det_off[f] + c.n;
-    tab_off[f + 1] = tab_off[f] + (unsigned long long)(fp.g.nvx + fp.g.nvy) * fp.g.E;
-    const uint32_t emit_cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * c.n, 1u << 18), 1u << 24);
-    const uint32_t key_cap = kBatchKeyCap;
-    emit_off[f + 1] = emit_off[f] + emit_cap;
-    cand_off[f + 1] = cand_off[f] + key_cap;
-    bucket_base[f + 1] = bucket_base[f] + fp.nb;
-    ecount_base[f + 1] = ecount_base[f] + fp.g.E;
-    fill_stack_args(fp, b->n_min[f], &hargs[f]);
-    unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
-    b->key_cap.push_back(key_cap);
-    b->ids_cap.push_back((uint64_t)key_cap * (fp.g.E / 2 + 8));
+    b->emit_cap[f] = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(2 * b->cats[f].n, 1u << 18), 1u << 24);
+    b->ids_cap[f] = (uint64_t)b->key_seg * (b->plans[f].g.E / 2 + 8);
   }
-  BatchDev& B = b->dev;
-  B.n_fields = (int)n_fields;
-  B.total_dets = det_off[n_fields];
-  B.total_buckets = bucket_base[n_fields];
-  B.total_tab = tab_off[n_fields];
-  B.total_emit = emit_off[n_fields];
-  B.total_cand = cand_off[n_fields];
-  b->ecount_words = ecount_base[n_fields];
-  // one arena: [region sizes computed here]
-  struct Reg { void** p; size_t bytes; };
-  std::vector<Reg> regs;
-  std::vector<Emit*> f_emits(n_fields);
-  std::vector<Key*> f_keys(n_fields);
-  std::vector<unsigned long long*> f_idoff(n_fields);
-  std::vector<uint32_t*> f_ids(n_fields), f_idt(n_fields);
-  std::vector<sas_candidate*> f_cands(n_fields);
-  std::vector<int32_t*> f_sxt(n_fields), f_syt(n_fields);
-  std::vector<int64_t*> f_t(n_fields), f_dt(n_fields);
-  regs.push_back({(void**)&B.fields, n_fields * sizeof(BatchField)});
-  for (sas_batch::Group& g : b->groups) {
-    regs.push_back({(void**)&g.d_args, g.fields.size() * sizeof(StackArgs)});
-    regs.push_back({(void**)&g.d_unit_base, (g.fields.size() + 1) * 8});
-    regs.push_back({(void**)&g.d_work, 8});
-  }
-  regs.push_back({(void**)&B.det_off, (n_fields + 1) * 8});
-  regs.push_back({(void**)&B.tab_off, (n_fields + 1) * 8});
-  regs.push_back({(void**)&B.emit_off, (n_fields + 1) * 8});
-  regs.push_back({(void**)&B.cand_off, (n_fields + 1) * 8});
-  regs.push_back({(void**)&b->d_ctr, (size_t)n_fields * kCtrN * 4});
-  regs.push_back({(void**)&b->d_c64, (size_t)n_fields * kC64N * 8});
-  regs.push_back({(void**)&b->d_ecount_all, b->ecount_words * 4});
-  regs.push_back({(void**)&B.bucket_count, B.total_buckets * 4});
-  regs.push_back({(void**)&B.boff, (B.total_buckets + 1) * 4});
-  regs.push_back({(void**)&B.cursor, B.total_buckets * 4});
-  regs.push_back({(void**)&B.scan_scratch, scan_scratch_elems(B.total_buckets) * 4});
-  regs.push_back({(void**)&B.bucket_of, B.total_dets * 4});
-  regs.push_back({(void**)&B.dets, B.total_dets * sizeof(Det)});
-  regs.push_back({(void**)&B.keys_all, B.total_cand * sizeof(Key)});
-  for (uint32_t f = 0; f < n_fields; ++f) {
-    const FieldPlan& fp = b->plans[f];
-    regs.push_back({(void**)&f_t[f], fp.g.E * 8});
-    regs.push_back({(void**)&f_dt[f], fp.g.E * 8});
-    regs.push_back({(void**)&f_sxt[f], (size_t)fp.g.nvx * fp.g.E * 4});
-    regs.push_back({(void**)&f_syt[f], (size_t)fp.g.nvy * fp.g.E * 4});
-    regs.push_back({(void**)&f_emits[f], (emit_off[f + 1] - emit_off[f]) * sizeof(Emit)});
-    regs.push_back({(void**)&f_idoff[f], ((size_t)b->key_cap[f] + 1) * 8});
-    regs.push_back({(void**)&f_ids[f], b->ids_cap[f] * 4});
-    regs.push_back({(void**)&f_idt[f], b->ids_cap[f] * 4});
-    regs.push_back({(void**)&f_cands[f], (size_t)b->key_cap[f] * sizeof(sas_candidate)});
-  }
-  size_t total = 0;
-  for (const Reg& r : regs) total += align256(std::max<size_t>(r.bytes, 1));
-  if ((ce = cudaMalloc(&b->arena, total)) != cudaSuccess) { rc = cuda_err(ce, "batch arena"); free_batch(b); return rc; }
-  {
-    size_t off = 0;
-    for (const Reg& r : regs) {
-      *r.p = static_cast<char*>(b->arena) + off;
-      off += align256(std::max<size_t>(r.bytes, 1));
-    }
-  }
-  for (uint32_t f = 0; f < n_fields; ++f) f_keys[f] = B.keys_all + cand_off[f];
-  if ((ce = cudaMallocHost((void**)&b->h_ctr, (size_t)n_fields * kCtrN * 4)) != cudaSuccess ||
-      (ce = cudaMallocHost((void**)&b->h_c64, (size_t)n_fields * kC64N * 8)) != cudaSuccess) {
-    rc = cuda_err(ce, "pinned counters");
-    free_batch(b);
-    return rc;
-  }
-  // --- field descriptors ---------------------------------------------------------
-  b->hf.resize(n_fields);
-  for (uint32_t f = 0; f < n_fields; ++f) {
-    const FieldPlan& fp = b->plans[f];
-    const sas_catalog& c = b->cats[f];
-    StackArgs& sa = hargs[f];
-    uint32_t* ctr = b->d_ctr + (size_t)f * kCtrN;
-    unsigned long long* c64 = b->d_c64 + (size_t)f * kC64N;
-    sa.dets = B.dets;
-    sa.boff = B.boff + bucket_base[f];
-    sa.ecount = b->d_ecount_all + ecount_base[f];
-    sa.sxt = f_sxt[f];
-    sa.syt = f_syt[f];
-    sa.emits = f_emits[f];
-    sa.emit_cap = (uint32_t)(emit_off[f + 1] - emit_off[f]);
-    sa.n_emit = ctr + kCtrEmit;
-    sa.n_pairs = c64 + kC64Pairs;
-    sa.balance = c64 + kC64Balance;
-    sa.flags = ctr + kCtrFlags;
-    sa.tile_counter = nullptr;  // the group's work counter drives the multi-field launch
-    BatchField& bf = b->hf[f];
-    memset(&bf, 0, sizeof(bf));
-    bf.args = sa;
-    bf.x = c.x;
-    bf.y = c.y;
-    bf.epoch = c.epoch;
-    bf.t = f_t[f];
-    bf.E = fp.g.E;
-    bf.emit_cap = sa.emit_cap;
-    bf.ecount = const_cast<uint32_t*>(sa.ecount);
-    bf.dt = f_dt[f];
-    bf.t0 = reinterpret_cast<long long*>(c64 + kC64T0);
-    bf.sxt = f_sxt[f];
-    bf.syt = f_syt[f];
-    bf.bucket_base = bucket_base[f];
-    bf.counters = ctr;
-    bf.keys = f_keys[f];
-    bf.key_cap = b->key_cap[f];
-    bf.max_out = b->opts[f].max_candidates ? (uint32_t)std::min<uint64_t>(b->opts[f].max_candidates, b->key_cap[f]) : b->key_cap[f];
-    bf.id_off = f_idoff[f];
-    bf.ids = f_ids[f];
-    bf.ids_tmp = f_idt[f];
-    bf.ids_cap = b->ids_cap[f];
-    bf.cands = f_cands[f];
-    if ((ce = cudaMemcpyAsync(f_t[f], c.t, fp.g.E * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
-  }
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.fields, b->hf.data(), n_fields * sizeof(BatchField), cudaMemcpyHostToDevice, s);
-  // per group: its fields' stack arguments and a unit base over its own units
-  std::vector<std::vector<StackArgs>> gargs(b->groups.size());
-  std::vector<std::vector<unsigned long long>> gbase(b->groups.size());
-  for (size_t k = 0; k < b->groups.size(); ++k) {
-    sas_batch::Group& g = b->groups[k];
-    gbase[k].assign(1, 0ull);
-    for (uint32_t f : g.fields) {
-      gargs[k].push_back(hargs[f]);
-      gbase[k].push_back(gbase[k].back() + hargs[f].n_tiles);
-    }
-    g.grid = (int)std::min<unsigned long long>((unsigned long long)di.sms, std::max<unsigned long long>(gbase[k].back(), 1));
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(g.d_args, gargs[k].data(), g.fields.size() * sizeof(StackArgs), cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(g.d_unit_base, gbase[k].data(), (g.fields.size() + 1) * 8, cudaMemcpyHostToDevice, s);
-  }
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.det_off, det_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.tab_off, tab_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.emit_off, emit_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(B.cand_off, cand_off.data(), (n_fields + 1) * 8, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  for (const sas_batch::Group& g : b->groups)
-    if (ce == cudaSuccess) ce = stack_set_smem_attr(g.kx, g.ky, g.cb, g.smem);
-  if (ce == cudaSuccess) ce = batch_set_attrs();
-  if (ce != cudaSuccess) { rc = cuda_err(ce, "batch setup"); free_batch(b); return rc; }
-  // --- record the pass as a graph ---------------------------------------------
-  cudaStream_t cs;
-  if ((ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_err(ce, "stream"); free_batch(b); return rc; }
-  ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  cudaError_t ce2 = ce == cudaSuccess ? record_pass(b, cs) : ce;
-  cudaGraph_t g = nullptr;
-  if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &g);
-  if (ce == cudaSuccess) ce = ce2;
-  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, g, 0);
-  b->graph = g;
-  cudaStreamDestroy(cs);
-  if (ce != cudaSuccess) { rc = cuda_err(ce, "graph capture"); free_batch(b); return rc; }
+  if ((rc = build_pass(b, di, s)) != SAS_OK) { free_batch(b); return rc; }
   cudaEventCreate(&b->ev0);
   cudaEventCreate(&b->ev1);
   b->fallback.assign(n_fields, nullptr);
@@ -374,7 +414,52 @@ int sas_batch_run(sas_batch* b, void* stream) {
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return cuda_err(ce, "batch graph");
   cudaEventElapsedTime(&b->ms_last, b->ev0, b->ev1);
-  // exact fallback for fields that did not fit their capacities
+  // A field over a capacity (keys, emissions, ids) reports what it needed: grow
+  // those capacities, rebuild the arena and the graph, and replay (a few times
+  // at most: a field cut short at one stage can need more at the next).
+  for (int round = 0; round < 4; ++round) {
+    bool grow = false;
+    uint32_t key_seg = b->key_seg;
+    std::vector<uint32_t> emit_cap = b->emit_cap;
+    std::vector<uint64_t> ids_cap = b->ids_cap;
+    for (uint32_t f = 0; f < b->n_fields; ++f) {
+      const uint32_t* ctr = b->h_ctr + (size_t)f * kCtrN;
+      const uint32_t fl = ctr[kCtrFlags];
+      if (fl & (kFlagEpoch | kFlagPos | kFlagShift | kFlagCounter | kFlagInternal)) continue;
+      if (!(fl & kFlagEmitCap) && ctr[kCtrEmit] <= b->emit_cap[f]) continue;
+      const uint64_t need_emit = ctr[kCtrEmit], need_keys = ctr[kCtrValid];
+      const uint64_t need_ids = (uint64_t)ctr[kCtrIdsLo] | ((uint64_t)ctr[kCtrIdsHi] << 32);
+      if (need_emit > emit_cap[f]) emit_cap[f] = (uint32_t)std::min<uint64_t>(need_emit + need_emit / 4 + 1024, 1u << 30);
+      while (need_keys > key_seg && key_seg < kBatchKeyCapMax) key_seg *= 2;
+      if (need_ids > ids_cap[f]) ids_cap[f] = need_ids + need_ids / 4 + 1024;
+      grow = true;
+    }
+    if (!grow) break;
+    // the new arena must fit in what the device has free now (plus the old arena)
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    uint64_t want = 0;
+    for (uint32_t f = 0; f < b->n_fields; ++f)
+      want += (uint64_t)key_seg * (sizeof(Key) + 8 + sizeof(sas_candidate)) + (uint64_t)emit_cap[f] * sizeof(Emit) +
+              ids_cap[f] * 8;
+    if (want > free_b / 2) break;  // leave it to the exact single-field fallback below
+    b->key_seg = key_seg;
+    b->emit_cap = emit_cap;
+    b->ids_cap = ids_cap;
+    free_pass(b);
+    DevInfo di;
+    int rc = device_info(b->device, &di);
+    if (rc == SAS_OK) rc = build_pass(b, di, s);
+    if (rc != SAS_OK) return rc;
+    ++b->rebuilds;
+    cudaEventRecord(b->ev0, s);
+    ce = cudaGraphLaunch(b->exec, s);
+    cudaEventRecord(b->ev1, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_err(ce, "batch graph");
+    cudaEventElapsedTime(&b->ms_last, b->ev0, b->ev1);
+  }
+  // exact fallback for fields that still do not fit, or whose counters wrapped
   for (uint32_t f = 0; f < b->n_fields; ++f) {
     const uint32_t* ctr = b->h_ctr + (size_t)f * kCtrN;
     const unsigned long long* c64 = b->h_c64 + (size_t)f * kC64N;
@@ -607,10 +692,11 @@ int sas_batch_vet(const sas_batch* b, sas_vet* vt, uint32_t* field_out, uint32_t
   return SAS_OK;
 }
 
-int sas_batch_stats(const sas_batch* b, float* ms_last, uint64_t* fallbacks) {
+int sas_batch_stats(const sas_batch* b, float* ms_last, uint64_t* fallbacks, uint64_t* rebuilds) {
   if (!b) return set_error(SAS_ERR_ARG, "null batch");
   if (ms_last) *ms_last = b->ms_last;
   if (fallbacks) *fallbacks = b->fallback_count;
+  if (rebuilds) *rebuilds = b->rebuilds;
   return SAS_OK;
 }
 

@@ -18,10 +18,11 @@ enum : int {
 // Per-field 64-bit counters.
 enum : int { kC64Pairs = 0, kC64Balance = 1, kC64T0 = 2, kC64N = 4 };
 
-// Candidate-key slots of one field (a power of two: every field's keys form one
-// segment of a segmented sort); a field with more falls back to the
-// single-field path.
+// Initial candidate-key slots of one field (a power of two: every field's keys
+// form one segment of a segmented sort); a batch whose fields need more grows
+// its segment to the next power of two and rebuilds its pass.
 constexpr uint32_t kBatchKeyCap = 32768;
+constexpr uint32_t kBatchKeyCapMax = 1u << 22;
 
 // Everything the batch kernels need to know about one field.
 struct BatchField {
@@ -68,6 +69,7 @@ struct BatchDev {
   unsigned long long total_emit;
   unsigned long long* cand_off;  // [n_fields + 1] candidate slots
   unsigned long long total_cand;
+  uint32_t key_seg;              // key slots per field (a power of two)
   Key* keys_all;                 // [total_cand]: field f's keys at cand_off[f]
 };
 

@@ -176,14 +176,15 @@ __global__ void k_batch_cell_count(const BatchField* __restrict__ F, const Det* 
 // Keys slots beyond a field's valid keys get the maximum key, so the segmented
 // sort leaves the valid keys first; a field with more valid keys than slots
 // gets its capacity flag (and is recomputed on the single-field path).
-__global__ void k_batch_pad(const BatchField* __restrict__ F, Key* __restrict__ keys_all, uint64_t total) {
+__global__ void k_batch_pad(const BatchField* __restrict__ F, Key* __restrict__ keys_all, uint64_t total,
+                            uint32_t key_seg) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  const BatchField& bf = F[i / kBatchKeyCap];
-  const uint32_t local = (uint32_t)(i % kBatchKeyCap);
+  const BatchField& bf = F[i / key_seg];
+  const uint32_t local = (uint32_t)(i % key_seg);
   const uint32_t n_valid = bf.counters[kCtrValid];
   if (local >= n_valid) keys_all[i] = max_key_b();
-  if (local == 0 && n_valid > kBatchKeyCap) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
+  if (local == 0 && n_valid > key_seg) atomicOr(bf.counters + kCtrFlags, kFlagEmitCap);
 }
 
 // One block per field, after the sort: the exclusive scan of the raw counts of
@@ -191,7 +192,7 @@ __global__ void k_batch_pad(const BatchField* __restrict__ F, Key* __restrict__ 
 __global__ void __launch_bounds__(1024) k_batch_offsets(const BatchField* __restrict__ F) {
   __shared__ unsigned long long s_warp[33];
   const BatchField& bf = F[blockIdx.x];
-  const uint32_t n_valid = min(bf.counters[kCtrValid], kBatchKeyCap);
+  const uint32_t n_valid = min(bf.counters[kCtrValid], bf.key_cap);
   const uint32_t n_out = min(n_valid, bf.max_out);
   unsigned long long carry = 0;
   for (uint32_t base = 0; base < n_out; base += blockDim.x) {
@@ -368,9 +369,9 @@ cudaError_t batch_launch_prep(const BatchDev& B, cudaStream_t s) {
 
 cudaError_t batch_launch_post(const BatchDev& B, cudaStream_t s) {
   k_batch_cell_count<<<dim3(64, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.dets, B.boff);
-  k_batch_pad<<<(unsigned)((B.total_cand + 255) / 256), 256, 0, s>>>(B.fields, B.keys_all, B.total_cand);
+  k_batch_pad<<<(unsigned)((B.total_cand + 255) / 256), 256, 0, s>>>(B.fields, B.keys_all, B.total_cand, B.key_seg);
   note_launch(2);
-  cudaError_t e = launch_sort_segments(B.keys_all, (uint32_t)B.total_cand, kBatchKeyCap, s);
+  cudaError_t e = launch_sort_segments(B.keys_all, (uint32_t)B.total_cand, B.key_seg, s);
   if (e != cudaSuccess) return e;
   k_batch_offsets<<<B.n_fields, 1024, 0, s>>>(B.fields);
   k_batch_ids<<<dim3(32, B.n_fields), kWarps * 32, 0, s>>>(B.fields, B.dets, B.boff);

@@ -332,7 +332,8 @@ _lib.sas_batch_field_info.argtypes = [_p, ctypes.c_uint32, ctypes.POINTER(sas_re
 _lib.sas_batch_candidates.argtypes = [_p, ctypes.c_uint32, _p, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_uint64), _p, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
-_lib.sas_batch_stats.argtypes = [_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64)]
+_lib.sas_batch_stats.argtypes = [_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)]
 _lib.sas_batch_destroy.argtypes = [_p]
 _lib.sas_batch_destroy.restype = None
 _lib.sas_autotune.argtypes = [_p, ctypes.POINTER(sas_catalog), ctypes.c_uint32,
@@ -425,7 +426,9 @@ class Batch:
 
     def stats(self):
         ms, fb = ctypes.c_float(), ctypes.c_uint64()
-        _check(_lib.sas_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(fb)))
+        rb = ctypes.c_uint64()
+        _check(_lib.sas_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(fb), ctypes.byref(rb)))
+        self.rebuilds = rb.value
         return ms.value, fb.value
 
     def destroy(self):

@@ -7,8 +7,9 @@ lattice and bin, similar epoch count, detection density and threshold -- share
 the answer, so a batch of many uneven fields is tuned once per size class and
 each field takes its class's options.  The cache is a JSON object
 {class key: {"tile_kx": kx, "tile_ky": ky, "superbin": s, "tile_bx": bx,
-"tile_by": by, "velocity_block": b, "ms": t, "device": name}} (0: the planner's
-choice for that field)
+"tile_by": by, "velocity_block": b, "ms": t, "planner_ms": t0, "device": name}}
+(0: the planner's choice for that field; planner_ms: the planner's own options
+timed the same way on the same field)
 that can be written to disk and reused across runs on the same GPU model.
 
 Host logic only: the timing runs in the library (sas_autotune).
@@ -74,10 +75,20 @@ class TuneCache:
         if key not in self.entries:
             best, ms = sas.sas_autotune(field.grid, field.dx, field.dy, field.de, field.cat.t,
                                         field.cat.ticks_per_hour, field.w.n_min, reps=reps)
+            # the planner's own choice on the same field, timed the same way (device
+            # time of the whole search, median of reps after one warm-up)
+            ts = []
+            for r in range(reps + 1):
+                res = sas.sas_stack(field.grid, field.dx, field.dy, field.de, field.cat.t,
+                                    field.cat.ticks_per_hour, field.w.n_min, on_device=True)
+                if r:
+                    ts.append(res.info()["ms_total"])
+                res.free()
             self.entries[key] = {"tile_kx": int(best.tile_kx), "tile_ky": int(best.tile_ky),
                                  "superbin": int(best.superbin), "tile_bx": int(best.tile_bx),
                                  "tile_by": int(best.tile_by), "velocity_block": int(best.velocity_block),
-                                 "ms": round(float(ms), 4), "device": device_name}
+                                 "ms": round(float(ms), 4), "planner_ms": round(float(sorted(ts)[len(ts) // 2]), 4),
+                                 "device": device_name}
         return self.entries[key]
 
     def opts_for(self, field):

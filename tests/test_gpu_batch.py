@@ -74,9 +74,10 @@ def test_batch_equals_single_field_search():
     b.destroy()
 
 
-def test_batch_field_fallback_is_exact():
-    """A field with far more candidates than the batch's per-field capacity
-    (32768) is recomputed on the single-field path; the others stay batched."""
+def test_batch_grows_past_its_capacity():
+    """A field with far more candidates than the batch's initial per-field
+    capacity (32768) makes the run grow its capacities, rebuild the pass and
+    replay: every field stays batched and exact."""
     w = W.tiny()
     cat = W.load(w)
     g = sas.Grid(w.grid)
@@ -96,7 +97,12 @@ def test_batch_field_fallback_is_exact():
     c2, ids2, _ = _single(g2, cat2, 12)
     cb, idsb = b.candidates(1)
     assert np.array_equal(cb, c2) and np.array_equal(idsb, ids2)
-    assert b.stats()[1] == 1
+    assert b.stats()[1] == 0 and b.rebuilds >= 1
+    # a second run replays the grown pass without rebuilding
+    b.run()
+    assert b.stats()[1] == 0 and b.rebuilds == 1
+    c, ids = b.candidates(0)
+    assert np.array_equal(ids.astype(np.int64), ref.ids.astype(np.int64))
     b.destroy()
 
 

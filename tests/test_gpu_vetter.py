@@ -450,10 +450,15 @@ def test_batch_vet_equals_per_field_pipeline():
         fields.append((sas.Grid(w.grid), torch.from_numpy(cat.x).cuda(), torch.from_numpy(cat.y).cuda(),
                        torch.from_numpy(cat.epoch.view(np.int16)).cuda(), cat.t, cat.ticks_per_hour,
                        max(8, w.n_min)))
-    tw = W.tiny()                         # n_min 2: far beyond the batch's candidate capacity
-    tc = W.load(tw)
+    # a field whose 8-bit counters wrap (300 same-spot detections, 15 per epoch,
+    # in a 20-epoch field): recomputed exactly on the single-field path
+    tw = W.tiny()
+    t0 = W.load(tw)
+    ex = np.full(300, 100_000, np.int32)
+    tc = cases.catalog(np.concatenate([t0.x, ex]), np.concatenate([t0.y, ex]),
+                       np.concatenate([t0.epoch, np.arange(300) % t0.t.shape[0]]), t0.t, t0.ticks_per_hour)
     fields.append((sas.Grid(tw.grid), torch.from_numpy(tc.x).cuda(), torch.from_numpy(tc.y).cuda(),
-                   torch.from_numpy(tc.epoch.view(np.int16)).cuda(), tc.t, tc.ticks_per_hour, 2))
+                   torch.from_numpy(tc.epoch.view(np.int16)).cuda(), tc.t, tc.ticks_per_hour, tw.n_min))
     b = sas.Batch(fields)
     b.run()
     # a field recomputed on the single-field path reports its own stack time
