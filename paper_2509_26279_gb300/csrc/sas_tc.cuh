@@ -26,6 +26,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int kc) {
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
+// Descriptor with explicit strides (no swizzle, K-major): lbo = bytes between
+// core matrices adjacent along K, sbo = bytes between core matrices adjacent
+// along M/N.  With sbo = 128 the rows of an operand sit at a uniform 16-byte
+// stride, so the operand may start at any row (a shifted window of a larger
+// matrix) as long as the address stays 16-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_strided(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
 // The same layout for 4-byte elements (TF32): a core-matrix row holds 4 of them.
 __host__ __device__ __forceinline__ uint32_t cm_offset4(int row, int k, int kc) {
   return (uint32_t)(((row >> 3) * kc + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);

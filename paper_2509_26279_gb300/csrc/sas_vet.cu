@@ -74,151 +74,152 @@ __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162
 
 // ---- forward on the tensor cores: the three convolutions as implicit GEMMs ---
 //
-// Per stamp and layer: D[pixel][out channel] = sum_k A[pixel][k] * W[out][k]
-// with k = in_channel * 9 + tap, A the im2col of the layer's input (M = output
-// pixels padded to 128-row tiles, N = 32, K = 9 * channels padded to 16s).  A is
-// built in shared memory in the no-swizzle K-major core-matrix layout, W stays
-// resident in the same layout, one thread issues tcgen05.mma (BF16 x BF16 ->
-// FP32 in TMEM), and every warp reads its TMEM lanes back for bias + ReLU + BF16
-// rounding.  Same numerics as the CUDA-core form: exact products, FP32 sums.
+// Per stamp and layer: D[pixel][out] = sum over taps (dy, dx) and input channels
+// c of A[pixel + dy * W + dx][c] * w[out][c][dy][dx], with A the layer's input
+// (W x W pixels, row r = y * W + x) and D computed over the padded output grid
+// (rows y * W + x for x < W; the columns x >= W - 2 are not outputs and are
+// dropped).  A sits in shared memory as [8-channel chunk][row][8 channels], so
+// its rows are 16 bytes apart and the operand of tap (dy, dx) is the same
+// buffer started dy * W + dx rows later: no im2col is built.  Each tap of each
+// 128-row tile is one tcgen05.mma per 16 input channels (BF16 x BF16 -> FP32 in
+// TMEM), all issued by one thread; every warp then reads its TMEM lanes back for
+// bias + ReLU + BF16 rounding straight into the next layer's input layout.
+// Products are exact in FP32 and the sums accumulate in FP32.
 
-constexpr int kTcThreads = 512;  // 16 warps: 4 TMEM lane quadrants x 4 column quarters
-constexpr int kTcKC1 = 12;  // conv1: K = 81 padded to 96 = 12 core matrices
-constexpr int kTcKC = 36;   // conv2, conv3: K = 288
-constexpr int kSmW1 = 0;
-constexpr int kSmW2 = kSmW1 + kCh * kTcKC1 * 8 * 2;
-constexpr int kSmW3 = kSmW2 + kCh * kTcKC * 8 * 2;
-constexpr int kSmA = kSmW3 + kCh * kTcKC * 8 * 2;
-constexpr int kSmX0 = kSmA + 128 * kTcKC * 8 * 2;             // 128 x 288 >= 256 x 96
-constexpr int kSmA1 = kSmX0 + 4096;                            // 9 x 225 bf16
-constexpr int kSmA2 = kSmA1 + 10880;                           // 32 x 169 bf16
-constexpr int kSmBias = kSmA2 + 7808;                          // 32 x 121 bf16
-constexpr int kSmTab = kSmBias + 3 * kCh * 4;
-constexpr int kSmBar = kSmTab + (kTcKC1 * 8 + 2 * kTcKC * 8) * 4;
+constexpr int kTcThreads = 512;   // 16 warps: 4 TMEM lane quadrants x 4 eight-channel slices
+constexpr int kTcRows0 = 288;     // x0: 15 x 15 pixels; tiles read up to row 2 * 128 - 1 + 2 * 15 + 2
+constexpr int kTcRows1 = 288;     // a1: 13 x 13 pixels; up to row 2 * 128 - 1 + 2 * 13 + 2
+constexpr int kTcRows2 = 160;     // a2: 11 x 11 pixels; up to row 127 + 2 * 11 + 2
+constexpr int kTcW1 = 9 * kCh * 16 * 2;   // per tap: 32 outputs x 16 input channels (9 real)
+constexpr int kTcW23 = 9 * kCh * kCh * 2; // per tap: 32 x 32
+constexpr int kSmX0 = 0;
+constexpr int kSmA1 = kSmX0 + 2 * kTcRows0 * 16;
+constexpr int kSmA2 = kSmA1 + 4 * kTcRows1 * 16;
+constexpr int kSmW1 = kSmA2 + 4 * kTcRows2 * 16;
+constexpr int kSmW2 = kSmW1 + kTcW1;
+constexpr int kSmW3 = kSmW2 + kTcW23;
+constexpr int kSmBias = kSmW3 + kTcW23;
+constexpr int kSmBar = kSmBias + 3 * kCh * 4;
 constexpr int kTcSmem = kSmBar + 16;
-static_assert(kSmA % 128 == 0 && kSmW2 % 128 == 0 && kSmW3 % 128 == 0, "operand alignment");
-static_assert(256 * kTcKC1 * 8 <= 128 * kTcKC * 8, "conv1 operand fits the A buffer");
-static_assert(kTcSmem <= 227 * 1024, "shared memory");
+constexpr int kTcTmemCols = 256;  // conv1 tiles at columns 0, 32; conv2 at 64, 96; conv3 at 128
+static_assert(2 * kTcRows0 >= 2 * 128 + 2 * kS + 2 && kTcRows1 >= 2 * 128 + 2 * kH1 + 2 &&
+                  kTcRows2 >= 128 + 2 * kH2 + 2, "shifted windows stay inside the buffers");
+static_assert(kTcRows0 >= 2 * 128 + 2 * kS + 2, "conv1 windows");
+static_assert(kSmW1 % 128 == 0 && kSmW2 % 128 == 0 && kSmW3 % 128 == 0 && kSmA1 % 16 == 0 &&
+                  kSmA2 % 16 == 0, "operand alignment");
+static_assert(2 * kTcSmem <= 227 * 1024, "two CTAs per SM");
 
-// Weights of a conv layer as the B operand: B[n][k] = w[n][k] (k < kreal), 0 after.
-__device__ void tc_load_w(const __nv_bfloat16* __restrict__ w, int kreal, int kc, unsigned char* dst) {
-  for (int i = threadIdx.x; i < kCh * kc * 8; i += blockDim.x) {
-    const int n = i / (kc * 8), k = i - n * kc * 8;
-    const __nv_bfloat16 v = k < kreal ? w[n * kreal + k] : __float2bfloat16_rn(0.f);
-    *reinterpret_cast<__nv_bfloat16*>(dst + tc::cm_offset(n, k, kc)) = v;
+// Per-tap weights of a layer as the B operand: B_t[o][c] = w[o][c][t] (c < cin),
+// zero for c >= cin; kc 16-byte chunks per row (K = 8 kc).
+__device__ void tc_load_w_taps(const __nv_bfloat16* __restrict__ w, int cin, int kc, unsigned char* dst) {
+  const int per_tap = kCh * kc * 8;
+  for (int i = threadIdx.x; i < 9 * per_tap; i += blockDim.x) {
+    const int t = i / per_tap, j = i - t * per_tap, o = j / (kc * 8), c = j - o * (kc * 8);
+    const __nv_bfloat16 v = c < cin ? w[(o * cin + c) * 9 + t] : __float2bfloat16_rn(0.f);
+    *reinterpret_cast<__nv_bfloat16*>(dst + t * per_tap * 2 + tc::cm_offset(o, c, kc)) = v;
   }
 }
 
-// im2col of one layer into A: chunk ci (16 bytes = 8 consecutive k of one row)
-// sits at byte ci * 16, so consecutive threads store consecutive chunks.
-template <int HI, int KC, int NTILE>
-__device__ __forceinline__ void tc_im2col(const __nv_bfloat16* act, const int* tab, unsigned char* A) {
-  constexpr int HO = HI - 2, P = HO * HO, CHUNKS = NTILE * 128 * KC;
-  const uint16_t* a16 = reinterpret_cast<const uint16_t*>(act);
-  for (int ci = threadIdx.x; ci < CHUNKS; ci += kTcThreads) {
-    const int mr = ci & 7, g = ci >> 3, kc = g % KC, m = (g / KC) * 8 + mr;
-    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-    if (m < P) {
-      const int y = m / HO, base = y * HI + (m - y * HO);
-      const int* t = tab + kc * 8;
-      uint32_t v[8];
+// The MMAs of one layer (thread 0): NT tiles of 128 output rows, 9 taps, KS
+// steps of 16 input channels; input rows R per chunk, input width W.
+template <int NT, int KS, int R, int W>
+__device__ __forceinline__ void tc_conv_mma(uint32_t a_base, uint32_t w_base, uint32_t tmem_col) {
+  constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+  constexpr uint32_t per_tap = kCh * KS * 2 * 16;  // bytes of one tap's B operand
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = t[j] >= 0 ? (uint32_t)a16[base + t[j]] : 0u;
-      w0 = v[0] | (v[1] << 16); w1 = v[2] | (v[3] << 16); w2 = v[4] | (v[5] << 16); w3 = v[6] | (v[7] << 16);
-    }
-    *reinterpret_cast<uint4*>(A + ci * 16) = make_uint4(w0, w1, w2, w3);
-  }
-}
-
-// Bias, ReLU and BF16 rounding of D (NTILE tiles of 128 pixels x 32 channels at
-// TMEM column 32 * tile) into out_s[ch][p] (shared) and out_g (global, optional).
-template <int P, int NTILE>
-__device__ __forceinline__ void tc_epilogue(uint32_t tmem, const float* bias, __nv_bfloat16* out_s,
-                                            __nv_bfloat16* out_g) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+  for (int t = 0; t < NT; ++t)
+    for (int tap = 0; tap < 9; ++tap) {
+      const uint32_t shift = (uint32_t)((tap / 3) * W + (tap % 3));
 #pragma unroll
-  for (int t = 0; t < NTILE; ++t) {
-    float v[8];
-    tc::ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32 + h * 8), v);
-    const int m = t * 128 + q * 32 + lane;
-    if (m < P) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int ch = h * 8 + j;
-        const __nv_bfloat16 r = __float2bfloat16_rn(fmaxf(v[j] + bias[ch], 0.f));
-        if (out_s) out_s[ch * P + m] = r;
-        if (out_g) out_g[ch * P + m] = r;
+      for (int ks = 0; ks < KS; ++ks) {
+        const uint64_t ad = tc::smem_desc_strided(a_base + (uint32_t)(2 * ks * R * 16) + (t * 128u + shift) * 16u,
+                                                  (uint32_t)(R * 16), 128u);
+        const uint64_t bd = tc::smem_desc(w_base + (uint32_t)tap * per_tap + (uint32_t)(2 * ks * 128), 2 * KS);
+        tc::mma_bf16(tmem_col + (uint32_t)(t * 32), ad, bd, idesc, (tap | ks) != 0);
       }
     }
+}
+
+// Bias, ReLU and BF16 rounding of a layer's D (NT tiles at TMEM column tmem_col)
+// over the padded grid of width W (outputs: W - 2 x W - 2) into the next layer's
+// input layout (rows (W - 2) * y + x, Rn rows per chunk) and, optionally, the
+// global activation [ch][W-2][W-2].
+template <int NT, int W, int Rn>
+__device__ __forceinline__ void tc_conv_epi(uint32_t tmem_col, const float* bias, unsigned char* next,
+                                            __nv_bfloat16* out_g) {
+  constexpr int HO = W - 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    float v[8];
+    tc::ld8(tmem_col + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * 32 + h * 8), v);
+    const int m = t * 128 + q * 32 + lane, y = m / W, x = m - y * W;
+    if (y < HO && x < HO) {
+      const int p = y * HO + x;
+      uint32_t pk[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const __nv_bfloat16 r0 = __float2bfloat16_rn(fmaxf(v[j] + bias[h * 8 + j], 0.f));
+        const __nv_bfloat16 r1 = __float2bfloat16_rn(fmaxf(v[j + 1] + bias[h * 8 + j + 1], 0.f));
+        pk[j / 2] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
+        if (out_g) {
+          out_g[(h * 8 + j) * HO * HO + p] = r0;
+          out_g[(h * 8 + j + 1) * HO * HO + p] = r1;
+        }
+      }
+      if (next)
+        *reinterpret_cast<uint4*>(next + (h * Rn + p) * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
   }
 }
 
-// One layer: im2col, MMAs by thread 0, bounded wait, epilogue.  Returns false
-// (block-uniform) when the wait gave up.
-template <int HI, int KC, int NTILE>
-__device__ __forceinline__ bool tc_layer(const __nv_bfloat16* act, const int* tab, unsigned char* A,
-                                         const unsigned char* W, uint32_t tmem, uint64_t* bar, uint32_t& phase,
-                                         const float* bias, __nv_bfloat16* out_s, __nv_bfloat16* out_g) {
-  constexpr int HO = HI - 2;
-  tc_im2col<HI, KC, NTILE>(act, tab, A);
+// One layer: operand visible to the tensor core, MMAs by thread 0, bounded
+// wait, epilogue.  Returns false (block-uniform) when the wait gave up.
+template <int NT, int KS, int R, int W, int Rn>
+__device__ __forceinline__ bool tc_conv_layer(unsigned char* smc, int a_off, int w_off, uint32_t tmem_col,
+                                              uint64_t* bar, uint32_t& phase, const float* bias, int next_off,
+                                              __nv_bfloat16* out_g) {
   tc::fence_smem_to_async();
   tc::fence_before_sync();
   __syncthreads();
   if (threadIdx.x == 0) {
     tc::fence_after_sync();
-    const uint32_t a0 = tc::smem_u32(A), w0 = tc::smem_u32(W);
-    constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
-#pragma unroll
-    for (int t = 0; t < NTILE; ++t)
-      for (int ks = 0; ks < KC / 2; ++ks)
-        tc::mma_bf16(tmem + (uint32_t)(t * 32), tc::smem_desc(a0 + (uint32_t)((t * 16 * KC + 2 * ks) * 128), KC),
-                     tc::smem_desc(w0 + (uint32_t)(2 * ks * 128), KC), idesc, ks > 0);
+    tc_conv_mma<NT, KS, R, W>(tc::smem_u32(smc + a_off), tc::smem_u32(smc + w_off), tmem_col);
     tc::commit(bar);
   }
   const bool ok = tc::mbar_wait(bar, phase, 1u << 22);
   phase ^= 1u;
   if (__syncthreads_or(!ok)) return false;
   tc::fence_after_sync();
-  tc_epilogue<HO * HO, NTILE>(tmem, bias, out_s, out_g);
+  tc_conv_epi<NT, W, Rn>(tmem_col, bias, next_off >= 0 ? smc + next_off : nullptr, out_g);
   tc::fence_before_sync();
-  __syncthreads();
   return true;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* __restrict__ stamps,
+__global__ void __launch_bounds__(kTcThreads, 2) k_conv_fwd_tc(const uint16_t* __restrict__ stamps,
                                                                const uint32_t* __restrict__ idx, uint32_t n,
                                                                const __nv_bfloat16* __restrict__ wb,
                                                                __nv_bfloat16* a1g, __nv_bfloat16* a2g,
                                                                __nv_bfloat16* __restrict__ a3g,
                                                                uint32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smc[];
-  __nv_bfloat16* x0 = reinterpret_cast<__nv_bfloat16*>(smc + kSmX0);
-  __nv_bfloat16* a1 = reinterpret_cast<__nv_bfloat16*>(smc + kSmA1);
-  __nv_bfloat16* a2 = reinterpret_cast<__nv_bfloat16*>(smc + kSmA2);
   float* bias = reinterpret_cast<float*>(smc + kSmBias);
-  int* tab1 = reinterpret_cast<int*>(smc + kSmTab);
-  int* tab2 = tab1 + kTcKC1 * 8;
-  int* tab3 = tab2 + kTcKC * 8;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smc + kSmBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smc + kSmBar + 8);
+  uint16_t* x0 = reinterpret_cast<uint16_t*>(smc + kSmX0);
   const int tid = threadIdx.x;
-  if (tid < 32) tc::tmem_alloc(tslot, 64);
+  if (tid < 32) tc::tmem_alloc(tslot, kTcTmemCols);
   if (tid == 0) tc::mbar_init(bar, 1);
-  tc_load_w(wb + kW1, kQ * 9, kTcKC1, smc + kSmW1);
-  tc_load_w(wb + kW2, kCh * 9, kTcKC, smc + kSmW2);
-  tc_load_w(wb + kW3, kCh * 9, kTcKC, smc + kSmW3);
+  // activation buffers: rows that are never written (input padding, channel
+  // padding of x0) stay zero
+  for (int i = tid; i < kSmW1 / 16; i += kTcThreads) reinterpret_cast<uint4*>(smc)[i] = make_uint4(0, 0, 0, 0);
+  tc_load_w_taps(wb + kW1, kQ, 2, smc + kSmW1);
+  tc_load_w_taps(wb + kW2, kCh, 4, smc + kSmW2);
+  tc_load_w_taps(wb + kW3, kCh, 4, smc + kSmW3);
   if (tid < 3 * kCh) {
     const int l = tid / kCh, o = tid % kCh;
     bias[tid] = ld(wb + (l == 0 ? kB1 : l == 1 ? kB2 : kB3) + o);
   }
-  // k -> offset of the input element in the layer's [C][HI][HI] activation
-  for (int k = tid; k < kTcKC1 * 8; k += kTcThreads)
-    tab1[k] = k < kQ * 9 ? (k / 9) * kS * kS + ((k % 9) / 3) * kS + (k % 3) : -1;
-  for (int k = tid; k < kTcKC * 8; k += kTcThreads) {
-    tab2[k] = (k / 9) * kH1 * kH1 + ((k % 9) / 3) * kH1 + (k % 3);
-    tab3[k] = (k / 9) * kH2 * kH2 + ((k % 9) / 3) * kH2 + (k % 3);
-  }
-  tc::fence_smem_to_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -238,26 +239,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_fwd_tc(const uint16_t* _
   };
   fetch(blockIdx.x);
   for (uint32_t b = blockIdx.x; b < n; b += gridDim.x) {
+    // x0[chunk c / 8][row][c % 8] = count / 16 in BF16 (exact for counts <= 256 * 16)
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
       const int i = tid + r * kTcThreads;
-      if (i < kQ * kS * kS) x0[i] = __float2bfloat16_rn((float)nxt[r] * 0.0625f);
+      if (i < kQ * kS * kS) {
+        const int c = i / (kS * kS), p = i - c * (kS * kS);
+        x0[((c >> 3) * kTcRows0 + p) * 8 + (c & 7)] =
+            __bfloat16_as_ushort(__float2bfloat16_rn((float)nxt[r] * 0.0625f));
+      }
     }
     fetch(b + gridDim.x);
-    __syncthreads();
-    if (!tc_layer<kS, kTcKC1, 2>(x0, tab1, smc + kSmA, smc + kSmW1, tmem, bar, phase, bias, a1,
-                                 a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr) ||
-        !tc_layer<kH1, kTcKC, 1>(a1, tab2, smc + kSmA, smc + kSmW2, tmem, bar, phase, bias + kCh, a2,
-                                 a2g ? a2g + (size_t)b * kCh * kH2 * kH2 : nullptr) ||
-        !tc_layer<kH2, kTcKC, 1>(a2, tab3, smc + kSmA, smc + kSmW3, tmem, bar, phase, bias + 2 * kCh, nullptr,
-                                 a3g + (size_t)b * kF)) {
+    if (!tc_conv_layer<2, 1, kTcRows0, kS, kTcRows1>(smc, kSmX0, kSmW1, tmem, bar, phase, bias, kSmA1,
+                                                     a1g ? a1g + (size_t)b * kCh * kH1 * kH1 : nullptr) ||
+        !tc_conv_layer<2, 2, kTcRows1, kH1, kTcRows2>(smc, kSmA1, kSmW2, tmem + 64, bar, phase, bias + kCh, kSmA2,
+                                                      a2g ? a2g + (size_t)b * kCh * kH2 * kH2 : nullptr) ||
+        !tc_conv_layer<1, 2, kTcRows2, kH2, 1>(smc, kSmA2, kSmW3, tmem + 128, bar, phase, bias + 2 * kCh, -1,
+                                               a3g + (size_t)b * kF)) {
       if (tid == 0) atomicOr(status, 1u);
       break;
     }
+    __syncthreads();  // the next stamp's input overwrites x0, which the MMAs above read
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid < 32) tc::tmem_free(tmem, 64);
+  if (tid < 32) tc::tmem_free(tmem, kTcTmemCols);
 }
 
 // ---- forward: fc1 on the tensor cores, fc2 in the epilogue --------------------
@@ -855,7 +861,7 @@ int fwd_blocks() {
 cudaError_t forward(sas_vet* vt, const uint16_t* stamps, const uint32_t* idx, uint32_t n, bool keep,
                     float* logits, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int blocks = (int)std::min<uint32_t>(n, (uint32_t)fwd_blocks());
+  const int blocks = (int)std::min<uint32_t>(n, 2u * (uint32_t)fwd_blocks());  // two CTAs per SM
   k_conv_fwd_tc<<<blocks, kTcThreads, kTcSmem, s>>>(stamps, idx, n, vt->wb, keep ? vt->a1 : nullptr,
                                                    keep ? vt->a2 : nullptr, vt->a3, vt->status);
   const uint32_t tiles = (n + kFcTcRows - 1) / kFcTcRows, ldp = tiles * kFcTcRows;
