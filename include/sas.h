@@ -529,7 +529,7 @@ int sas_param_dx_scan(double nu, double nu_th, const double* a, uint32_t n_epoch
  * Gradients are bit-reproducible for a batch.
  * A vetter lives on the device that was current at sas_vet_create; every call
  * makes that device current for its duration. */
-#define SAS_VET_MAX_BATCH 8192u
+#define SAS_VET_MAX_BATCH 32768u
 typedef struct sas_vet sas_vet;
 
 uint64_t sas_vet_num_params(void);

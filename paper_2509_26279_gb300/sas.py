@@ -486,7 +486,7 @@ EXPORTED += ["sas_stamps", "sas_vet_num_params", "sas_vet_create", "sas_vet_dest
              "sas_batch_stamps", "sas_owned", "sas_batch_owned", "sas_batch_vet", "sas_peel"]
 
 STAMP_SHAPE = (9, 15, 15)
-VET_MAX_BATCH = 8192
+VET_MAX_BATCH = 32768
 
 
 def sas_stamps(result: Result, out_dev, first: int = 0, count: int | None = None, stream=None) -> int:
