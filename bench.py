@@ -726,6 +726,7 @@ def main():
         r.free()
     peak_ops, probe_mhz = sas.sas_probe_shared_reduction_peak(2048, stream)
     atom_ops, atom_mhz = sas.sas_probe_shared_atomic_peak(2048, stream)
+    or64_ops, or64_mhz = sas.sas_probe_shared_or64_peak(2048, stream)
 
     def barrier():
         if dist is not None:
@@ -798,7 +799,11 @@ def main():
             "peak_atomic_returning": atom_ops / 1e9,
             "frac_vs_atomic_returning": achieved / atom_ops,
             "peak_atomic_returning_source": f"sas_probe_shared_atomic_peak (conflict-free atomicAdd, old value "
-                                            f"used), this run ({atom_mhz:.0f} MHz)"}
+                                            f"used), this run ({atom_mhz:.0f} MHz)",
+            "atomic_or_b64": or64_ops / 1e9,
+            "atomic_or_b64_source": f"sas_probe_shared_or64_peak (conflict-free 64-bit atomicOr, old value used: "
+                                    f"the epoch-bitmask update the kernel replaces by counters), this run "
+                                    f"({or64_mhz:.0f} MHz)"}
     cfg = workload_desc(w, cat)
     cfg.update({"l2": "flushed between steps (256 MiB write)", "n_pairs_per_step": n_pairs,
                 "candidates": int(info0["n_candidates"]),

@@ -613,6 +613,14 @@ int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s
 int sas_probe_shared_reduction_peak(uint32_t iters, void* stream, double* ops_per_s,
                                     double* sm_mhz);
 
+/* Measurement utility: throughput of conflict-free 64-bit shared-memory
+ * atomicOr whose old value is used -- the per-bin epoch-bitmask update that a
+ * literal form of Sec. 2.1 step 2 would issue per (detection, velocity) pair,
+ * which the stack kernel replaces by narrow counters -- in operations per
+ * second on every SM, as above.  *sm_mhz as above.
+ * Errors: SAS_ERR_ARG (null output or iters == 0), SAS_ERR_CUDA. */
+int sas_probe_shared_or64_peak(uint32_t iters, void* stream, double* ops_per_s, double* sm_mhz);
+
 #ifdef __cplusplus
 }
 #endif

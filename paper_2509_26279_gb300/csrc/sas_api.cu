@@ -720,6 +720,13 @@ int sas_probe_shared_atomic_peak(uint32_t iters, void* stream, double* ops_per_s
   return SAS_OK;
 }
 
+int sas_probe_shared_or64_peak(uint32_t iters, void* stream, double* ops_per_s, double* sm_mhz) {
+  if (!ops_per_s || !sm_mhz || iters == 0) return fail(SAS_ERR_ARG, "bad argument");
+  cudaError_t e = run_or64_probe(iters, (cudaStream_t)stream, ops_per_s, sm_mhz);
+  if (e != cudaSuccess) return cuda_fail(e, "64-bit atomicOr probe");
+  return SAS_OK;
+}
+
 int sas_probe_shared_reduction_peak(uint32_t iters, void* stream, double* ops_per_s, double* sm_mhz) {
   if (!ops_per_s || !sm_mhz || iters == 0) return fail(SAS_ERR_ARG, "bad argument");
   cudaError_t e = run_red_probe(iters, (cudaStream_t)stream, ops_per_s, sm_mhz);

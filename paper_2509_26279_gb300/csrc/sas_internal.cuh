@@ -284,6 +284,7 @@ CandView result_view(const sas_result* r);
 // sas_probe.cu
 cudaError_t run_atomic_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
 cudaError_t run_red_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
+cudaError_t run_or64_probe(uint32_t iters, cudaStream_t s, double* ops_per_s, double* sm_mhz);
 
 // sas_noalloc.cu (returns a sas_status; *err gets the message on failure)
 int noalloc_cell_counts(const sas_grid_desc& d, const sas_catalog* cat, const uint32_t* cells,

@@ -67,6 +67,9 @@ static_assert(kNParams == 187137, "parameter layout");
 
 constexpr int kBackBlocks = 256;      // blocks (and partial sums) of the conv backward kernels
 constexpr int kPartialStride = kCh * kCh * 9 + kCh;  // >= parts * weights + biases of any layer
+constexpr uint32_t kFc1Slices = 8;                   // stamp slices of the fc1 weight gradient
+static_assert((size_t)kFc1Slices * (kHid * kF + kHid) <= (size_t)kBackBlocks * kPartialStride,
+              "fc1 slices fit the partial buffer");
 static_assert(kPartialStride >= 3 * kCh * kQ * 9 + kCh, "partial stride");
 
 __device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -458,23 +461,30 @@ __global__ void k_g4(const float* __restrict__ glogit, const __nv_bfloat16* __re
 
 // fc1.w[j][k] = sum_b g4[b][j] * a3[b][k];  fc1.b[j] = sum_b g4[b][j].
 // Block: 32 columns k, all 64 rows j, whole batch.
+// Grid (columns / 32, slices): slice s adds the stamps [s n / S, (s + 1) n / S)
+// and writes its partial sums to part[s][j][k] (weights) and part[S * 64 * kF +
+// s * 64 + j] (biases); k_fc1_sum adds the slices in a fixed order.
 __global__ void __launch_bounds__(256) k_fc1_dw(const float* __restrict__ g4,
                                                 const __nv_bfloat16* __restrict__ a3g, uint32_t n,
-                                                float* __restrict__ grad) {
+                                                float* __restrict__ part) {
   __shared__ __align__(16) float Gs[32][kHid];
   __shared__ float Fs[32][33];
   const int t = threadIdx.x, jq = t & 15, kp = t >> 4;
   const int k0 = blockIdx.x * 32;
+  const uint32_t S = gridDim.y, s = blockIdx.y;
+  const uint32_t lo = (uint32_t)((uint64_t)n * s / S), hi = (uint32_t)((uint64_t)n * (s + 1) / S);
+  float* pw = part + (size_t)s * kHid * kF;                 // [j][k] of this slice
+  float* pb = part + (size_t)S * kHid * kF + (size_t)s * kHid;  // [j] of this slice
   float acc[4][2] = {}, accb[4] = {};
-  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+  for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
     for (int i = t; i < 32 * kHid; i += 256) {
       const uint32_t b = b0 + i / kHid;
-      Gs[i / kHid][i % kHid] = b < n ? g4[(size_t)b * kHid + i % kHid] : 0.f;
+      Gs[i / kHid][i % kHid] = b < hi ? g4[(size_t)b * kHid + i % kHid] : 0.f;
     }
     for (int i = t; i < 32 * 32; i += 256) {
       const uint32_t b = b0 + i / 32;
       const int k = k0 + i % 32;
-      Fs[i / 32][i % 32] = (b < n && k < kF) ? ld(a3g + (size_t)b * kF + k) : 0.f;
+      Fs[i / 32][i % 32] = (b < hi && k < kF) ? ld(a3g + (size_t)b * kF + k) : 0.f;
     }
     __syncthreads();
     for (int bb = 0; bb < 32; ++bb) {
@@ -494,9 +504,24 @@ __global__ void __launch_bounds__(256) k_fc1_dw(const float* __restrict__ g4,
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
       const int k = k0 + kp * 2 + kk;
-      if (k < kF) grad[kWf1 + (size_t)j * kF + k] = acc[jj][kk];
+      if (k < kF) pw[(size_t)j * kF + k] = acc[jj][kk];
     }
-    if (blockIdx.x == 0 && kp == 0) grad[kBf1 + j] = accb[jj];
+    if (blockIdx.x == 0 && kp == 0) pb[j] = accb[jj];
+  }
+}
+
+// grad[fc1.w] and grad[fc1.b]: the S slices of k_fc1_dw added in slice order.
+__global__ void k_fc1_sum(const float* __restrict__ part, uint32_t S, float* __restrict__ grad) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (uint32_t)(kHid * kF)) {
+    float v = 0.f;
+    for (uint32_t s = 0; s < S; ++s) v += part[(size_t)s * kHid * kF + i];
+    grad[kWf1 + i] = v;
+  } else if (i < (uint32_t)(kHid * kF + kHid)) {
+    const uint32_t j = i - kHid * kF;
+    float v = 0.f;
+    for (uint32_t s = 0; s < S; ++s) v += part[(size_t)S * kHid * kF + s * kHid + j];
+    grad[kBf1 + j] = v;
   }
 }
 
@@ -879,7 +904,13 @@ cudaError_t gradients(sas_vet* vt, const uint16_t* stamps, const float* labels, 
   if (e != cudaSuccess) return e;
   k_loss<<<1, kLossThreads, 0, s>>>(vt->logits, labels, idx, n, vt->a4, vt->glogit, grad, vt->loss);
   k_g4<<<(unsigned)(((uint64_t)n * kHid + 255) / 256), 256, 0, s>>>(vt->glogit, vt->a4, vt->wb, n, vt->g4);
-  k_fc1_dw<<<(kF + 31) / 32, 256, 0, s>>>(vt->g4, vt->a3, n, grad);
+  {
+    // stamp slices of about 512 (at most the partial buffer's room), summed in order
+    const uint32_t S = std::max<uint32_t>(1, std::min<uint32_t>(kFc1Slices, n / 512));
+    k_fc1_dw<<<dim3((kF + 31) / 32, S), 256, 0, s>>>(vt->g4, vt->a3, n, vt->partial);
+    k_fc1_sum<<<(kHid * kF + kHid + 255) / 256, 256, 0, s>>>(vt->partial, S, grad);
+    note_launch();
+  }
   k_fc1_dx<<<dim3((kF + 63) / 64, (n + 31) / 32), 256, 0, s>>>(vt->g4, vt->wb, vt->a3, n, vt->g3);
   const int nb = (int)std::min<uint32_t>(n, kBackBlocks);
   k_conv_back_tc<kH2><<<nb, kBtThreads, back_tc_smem<kH2>(), s>>>(vt->g3, vt->a2, n, vt->wb + kW3, vt->g2,

@@ -96,13 +96,15 @@ _lib.sas_probe_shared_atomic_peak.argtypes = [ctypes.c_uint32, _p, ctypes.POINTE
                                               ctypes.POINTER(ctypes.c_double)]
 _lib.sas_probe_shared_reduction_peak.argtypes = [ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_double)]
+_lib.sas_probe_shared_or64_peak.argtypes = [ctypes.c_uint32, _p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]
 _lib.sas_cell_counts_noalloc.argtypes = [_p, ctypes.POINTER(sas_catalog), _p, ctypes.c_uint64, _p, _p,
                                          _p]
 
 EXPORTED = ["sas_version", "sas_abi_version", "sas_kernel_launches", "sas_last_error", "sas_create_grid",
             "sas_destroy_grid", "sas_stack", "sas_result_get_info", "sas_candidates",
             "sas_result_free", "sas_probe_shared_atomic_peak", "sas_probe_shared_reduction_peak",
-            "sas_cell_counts_noalloc"]
+            "sas_probe_shared_or64_peak", "sas_cell_counts_noalloc"]
 
 
 def _check(status: int):
@@ -306,6 +308,14 @@ def sas_probe_shared_atomic_peak(iters: int = 4096, stream=None):
     ops, mhz = ctypes.c_double(), ctypes.c_double()
     _check(_lib.sas_probe_shared_atomic_peak(int(iters), _stream_handle(stream), ctypes.byref(ops),
                                              ctypes.byref(mhz)))
+    return ops.value, mhz.value
+
+
+def sas_probe_shared_or64_peak(iters: int = 4096, stream=None):
+    """(ops/s, SM MHz) of conflict-free 64-bit shared atomicOr (old value used) on all SMs."""
+    ops, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.sas_probe_shared_or64_peak(int(iters), _stream_handle(stream), ctypes.byref(ops),
+                                           ctypes.byref(mhz)))
     return ops.value, mhz.value
 
 
