@@ -165,9 +165,40 @@ __device__ __forceinline__ uint64_t order_key(double q) {
   return (b >> 63) ? ~b : (b | (1ull << 63));
 }
 
+// Membership bits of the h smallest (key, index) among n <= 32 NC points:
+// each lane counts its NC points' ranks against every key (no dependent
+// reductions).
+template <int NC>
+__device__ __forceinline__ uint32_t rank_select(const uint64_t* keys, uint32_t n, uint32_t h, int lane) {
+  uint64_t mine[NC];
+  uint32_t rank[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t i = c * 32 + lane;
+    mine[c] = i < n ? keys[i] : ~0ull;
+    rank[c] = 0;
+  }
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint64_t kj = keys[j];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const uint32_t i = c * 32 + lane;
+      rank[c] += (kj < mine[c] || (kj == mine[c] && j < i)) ? 1u : 0u;
+    }
+  }
+  uint32_t bits = 0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t i = c * 32 + lane;
+    if (i < n && rank[c] < h) bits |= 1u << c;
+  }
+  return bits;
+}
+
 // C-step: the h points of smallest (q, index) under the fit's (mean, adj).
 // Up to 256 points: each point's rank is counted against every key (no
-// dependent reductions); more: the h-th smallest key by binary descent.
+// dependent reductions), for the cluster's number of 32-point chunks; more:
+// the h-th smallest key by binary descent.
 __device__ __noinline__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h, uint64_t* keys, int lane) {
   const int64_t m = f.m;
   for (uint32_t c = 0; c < p.nc; ++c) {
@@ -184,26 +215,12 @@ __device__ __noinline__ uint32_t wselect(const Pts& p, const WFit& f, uint32_t h
   __syncwarp();
   uint32_t bits = 0;
   if (p.n <= 256) {
-    uint64_t mine[8];
-    uint32_t rank[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const uint32_t i = c * 32 + lane;
-      mine[c] = (c < (int)p.nc && i < p.n) ? keys[i] : ~0ull;
-      rank[c] = 0;
-    }
-    for (uint32_t j = 0; j < p.n; ++j) {
-      const uint64_t kj = keys[j];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const uint32_t i = c * 32 + lane;
-        rank[c] += (kj < mine[c] || (kj == mine[c] && j < i)) ? 1u : 0u;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const uint32_t i = c * 32 + lane;
-      if (c < (int)p.nc && i < p.n && rank[c] < h) bits |= 1u << c;
+    switch (p.nc) {
+      case 1: bits = rank_select<1>(keys, p.n, h, lane); break;
+      case 2: bits = rank_select<2>(keys, p.n, h, lane); break;
+      case 3: bits = rank_select<3>(keys, p.n, h, lane); break;
+      case 4: bits = rank_select<4>(keys, p.n, h, lane); break;
+      default: bits = rank_select<8>(keys, p.n, h, lane); break;
     }
     __syncwarp();
     return bits;
