@@ -281,9 +281,16 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     tune_s = time.perf_counter() - t1
     tuned_opts = [cache.opts_for(f) for f in fields]
 
-    def make_batch(thr):
+    def make_batch(thr, low=None):
+        opts = tuned_opts
+        if low is not None:
+            opts = []
+            for f, o in zip(fields, tuned_opts):
+                o2 = sas.make_opts(**{k: getattr(o, k) for k, _ in sas.sas_opts._fields_})
+                o2.n_low = low(f)
+                opts.append(o2)
         return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
-                         opts=tuned_opts, stream=stream)
+                         opts=opts, stream=stream)
 
     def vetted_pass(batch, cap):
         fo = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -310,12 +317,22 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                                   "final_loss": round(hist[-1], 4), "seconds": round(train_s, 1),
                                   "threshold": round(tau, 4),
                                   "threshold_rule": "purity 0.95 on 10 separate calibration fields"}}
-    for name, thr, desc in (("batched_vetted", lambda f: f.w.n_min, "batch at N_min = ceil(E/4)"),
-                            ("batched_vetted_e6", lambda f: -(-f.E // 6), "batch at N_min = ceil(E/6)"),
-                            ("batched_vetted_e8", lambda f: -(-f.E // 8), "batch at N_min = ceil(E/8)"),
-                            ("batched_vetted_low", lambda f: vetting.n_low(f.E),
-                             "batch at N_min = max(5, ceil(E/14))")):
-        batch = make_batch(thr)
+    e4 = lambda f: f.w.n_min
+    e6 = lambda f: -(-f.E // 6)
+    e8 = lambda f: -(-f.E // 8)
+    e14 = lambda f: vetting.n_low(f.E)
+    for name, thr, low, desc in (
+            ("batched_vetted", e4, None, "batch at N_min = ceil(E/4)"),
+            ("batched_vetted_e6", e6, None, "batch at N_min = ceil(E/6)"),
+            ("batched_vetted_e8", e8, None, "batch at N_min = ceil(E/8)"),
+            ("batched_vetted_low", e14, None, "batch at N_min = max(5, ceil(E/14))"),
+            ("batched_peaks_e6", e4, e6, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
+                                         "at n_low = ceil(E/6)"),
+            ("batched_peaks_e8", e4, e8, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
+                                         "at n_low = ceil(E/8)"),
+            ("batched_peaks_low", e4, e14, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
+                                           "at n_low = max(5, ceil(E/14))")):
+        batch = make_batch(thr, low)
         batch.run(stream)
         cap = sum(max(batch.field_info(k)["n_candidates"], 1) for k in range(len(fields))) + 1
         ms, (fo, co, lo) = timed(vetted_pass(batch, cap))
@@ -338,6 +355,8 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                         "rebuilds": int(batch.rebuilds),
                         "candidates_searched": int(sum(batch.field_info(k)["n_candidates"]
                                                        for k in range(len(fields)))),
+                        "superbins_emitted": int(sum(batch.field_info(k)["n_emitted"]
+                                                     for k in range(len(fields)))),
                         **score(per_field),
                         "dedup": {"form": "the same decision on the ownership-selected candidates only",
                                   **score(per_field_dedup)}}

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define SAS_ABI_VERSION 1
+#define SAS_ABI_VERSION 2
 #define SAS_MAX_EPOCHS 1024
 
 typedef enum sas_status {
@@ -112,6 +112,9 @@ typedef struct sas_opts {
   uint32_t superbin;         /* bins per counter side, 1..4; 0 = choose                 */
   uint32_t velocity_block;   /* velocity tiles per side sharing one staged detection
                                 set, 1..8; 0 = choose                                   */
+  uint32_t n_low;            /* 0: one threshold.  1 <= n_low <= n_min: also report the
+                                cells with >= n_low distinct epochs whose super-bin is
+                                a tile-local peak (see sas_stack); not with weights    */
 } sas_opts;
 
 /* One candidate trajectory: the cell (v_idx, bx, by) of the 3-D histogram with
@@ -139,7 +142,7 @@ typedef struct sas_result_info {
   uint32_t superbin;         /* bins per counter side                             */
   uint32_t vblock_x, vblock_y;  /* velocity tiles per staged detection set          */
   uint32_t staged_cap;       /* staged detection records per CTA                  */
-  uint32_t reserved;
+  uint32_t n_low;            /* lower threshold of the peak selection (n_min when off) */
   float ms_stack;            /* device time of the stack kernel (CUDA events)     */
   float ms_total;            /* device time of the whole call                     */
   float ms_prep;             /* ingest, buckets, reference epoch, shift tables    */
@@ -184,7 +187,20 @@ int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8
                        const sas_opts* opts, void* stream, sas_result** out);
 
 /* Run the search (Sec. 2.1 steps 1-3) on the current CUDA device.
- * grid, cat: see above.  n_min >= 1.  opts may be NULL.  stream: a
+ * grid, cat: see above.  n_min >= 1.  opts may be NULL.
+ * With opts->n_low in [1, n_min) the list holds every cell with >= n_min
+ * distinct epochs and, in addition, every cell with >= n_low distinct epochs
+ * whose S x S super-bin (S = info.superbin) is a tile-local peak of the raw
+ * counts: its raw count R(v, B) (detections whose projection at lattice point
+ * v lands in one of B's bins) is >= n_low and no super-bin B' at a lattice
+ * point v' of the same velocity tile (info.tile_kx x info.tile_ky lattice
+ * points; tiles start at kx = 0 and at ky = v_begin / nvx) and of the same
+ * spatial tile (info.tile_bx x info.tile_by super-bins from bin 0) with
+ * |kx'-kx|, |ky'-ky|, |B'x-Bx|, |B'y-By| all <= 1 has R(v', B') > R(v, B)
+ * (lattice points outside the searched set count 0).  This prunes the
+ * neighbouring cells a mover or a noise alignment raises before they are
+ * counted (an extension of the paper's threshold; the candidate list stays in
+ * the same order).  stream: a
  * cudaStream_t (NULL = legacy default).  On success *out holds a new result
  * that the caller releases with sas_result_free; the result owns its device
  * memory.  The call synchronizes the stream before returning.
@@ -212,15 +228,16 @@ void sas_result_free(sas_result* result);
 /* ---- Batched search: many fields in one graph-captured pass ---------------
  *
  * Many fields (CCDs) with uneven detection and epoch counts are searched by
- * one pass of every kernel -- one persistent stack launch over the work units
- * of all fields -- recorded once as a CUDA graph by sas_batch_create and
+ * one pass of every kernel -- one persistent stack launch per stack kernel
+ * configuration (velocity tile and counter width) over the work units of its
+ * fields -- recorded once as a CUDA graph by sas_batch_create and
  * replayed by sas_batch_run.  (The paper searches each CCD independently,
  * Sec. 3.3; batching is an implementation pattern with the same results.)
  *
  * grids[f], cats[f], n_min[f]: field f (catalogs in device memory, on_device
  * = 1, n >= 1; 1 <= n_min <= 128).  opts: NULL or an array of n_fields option
- * sets (tile_kx and tile_ky must agree across fields; v_begin/v_end and
- * counter_bits are ignored).  The batch keeps the catalogs' device pointers:
+ * sets (v_begin/v_end are ignored; n_low as in sas_stack, per field).  The
+ * batch keeps the catalogs' device pointers:
  * the caller may rewrite their contents between runs (same sizes, same
  * epoch times) and must keep them alive until sas_batch_destroy.
  * sas_batch_run replays the pass on `stream` and synchronizes; a field that

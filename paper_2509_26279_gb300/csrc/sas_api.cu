@@ -207,6 +207,9 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
   if (int rc = device_info(dev, &di)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if (n_min > (1u << 31)) return fail(SAS_ERR_ARG, "n_min must be <= 2^31");
+  if (o.n_low > n_min) return fail(SAS_ERR_ARG, "n_low %u is above n_min %u", o.n_low, n_min);
+  if (o.n_low && weights) return fail(SAS_ERR_ARG, "n_low is not supported by the weighted search");
+  const uint32_t n_low = o.n_low ? o.n_low : n_min;
 
   sas_result* res = new (std::nothrow) sas_result;
   if (!res) return fail(SAS_ERR_OOM, "host allocation");
@@ -214,6 +217,7 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
   res->device = dev;
   res->n_det = n;
   res->n_min = n_min;
+  res->info.n_low = n_low;
 
   if (n == 0 || v_begin == v_end) {
     res->info.t0 = 0;
@@ -363,7 +367,7 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
       const TileCfg& tc = plan.tc;
       CK(sc.alloc(&d_emits, emit_cap), "alloc emissions");
       CK(stack_set_smem_attr(tc.kx, tc.ky, tc.cb, tc.smem), "smem attribute");
-      fill_stack_args(plan, n_min, &sa);
+      fill_stack_args(plan, n_min, n_low, &sa);
       sa.w = d_w;
       sa.dets = d_dets;
       sa.boff = d_boff;
@@ -421,7 +425,7 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
       // a5/a7: exact distinct and raw counts of every bin of the emitted super-bins
       cudaEventRecord(evc0, s);
       CK(launch_cell_count(d_emits, n_emit, plan.tc.s, g, cg, d_dets, d_boff, d_ecount, d_sxt,
-                           d_syt, n_min, d_keys, &d_small[2], &d_small64[2], d_w, s), "cell count");
+                           d_syt, n_min, sa.n_low, d_keys, &d_small[2], &d_small64[2], d_w, s), "cell count");
       CK(cudaMemcpyAsync(&h_small[2], &d_small[2], 4, cudaMemcpyDeviceToHost, s), "read n_valid");
       CK(cudaMemcpyAsync(&h_small64[2], &d_small64[2], 8, cudaMemcpyDeviceToHost, s), "read raw");
       CK(cudaStreamSynchronize(s), "count sync");

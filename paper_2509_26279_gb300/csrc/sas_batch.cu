@@ -145,7 +145,7 @@ int build_pass(sas_batch* b, const DevInfo& di, cudaStream_t s) {
     cand_off[f + 1] = cand_off[f] + b->key_seg;
     bucket_base[f + 1] = bucket_base[f] + fp.nb;
     ecount_base[f + 1] = ecount_base[f] + fp.g.E;
-    fill_stack_args(fp, b->n_min[f], &hargs[f]);
+    fill_stack_args(fp, b->n_min[f], b->opts[f].n_low, &hargs[f]);
     unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
   }
   BatchDev& B = b->dev;
@@ -346,14 +346,16 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     b->n_min.push_back(n_min[f]);
     sas_opts o{};
     if (opts) o = opts[f];
-    // 8-bit counters (start 128 - n_min) wrap past 128 + n_min detections in
+    if (o.n_low > n_min[f]) { rc = set_errorf(SAS_ERR_ARG, "field %u: n_low is above n_min", f); break; }
+    if (o.n_low == 0) o.n_low = n_min[f];
+    // 8-bit counters (start 128 - n_low) wrap past 128 + n_low detections in
     // one super-bin: a field whose brightest mover (one detection per epoch)
     // plus a generous noise allowance could get there counts in 16 bits.  A
     // wrap is still detected and recomputed exactly; this keeps it rare.
     if (o.counter_bits == 0) {
       const double lam = (double)c.n * 9.0 / ((double)desc.nbx * desc.nby);  // per 3 x 3-bin super-bin
       const double reach = (double)c.n_epochs + lam + 6.0 * std::sqrt(lam) + 2.0;
-      o.counter_bits = reach >= 128.0 + n_min[f] ? 16 : 8;
+      o.counter_bits = reach >= 128.0 + o.n_low ? 16 : 8;
     }
     o.v_begin = o.v_end = 0;
     b->opts.push_back(o);
@@ -500,6 +502,7 @@ int sas_batch_field_info(const sas_batch* b, uint32_t field, sas_result_info* in
   info->vblock_x = (uint32_t)tc.bvx;
   info->vblock_y = (uint32_t)tc.bvy;
   info->staged_cap = (uint32_t)tc.scap;
+  info->n_low = b->opts[field].n_low;
   info->ms_total = b->ms_last;
   return SAS_OK;
 }
@@ -661,7 +664,7 @@ int sas_batch_vet(const sas_batch* b, sas_vet* vt, uint32_t* field_out, uint32_t
     uint32_t* idx = nullptr;
     if ((e = sc.alloc(&idx, v.n)) != cudaSuccess) break;
     uint64_t k = 0;
-    if (int rc = select_owned(v, b->n_min[f], idx, &k, s)) return rc;
+    if (int rc = select_owned(v, b->opts[f].n_low, idx, &k, s)) return rc;
     if (n + k > cap) return set_errorf(SAS_ERR_OVERFLOW, "room for %llu items, more needed", (unsigned long long)cap);
     if (k && (!field_out || !cand_out || !logit_out)) return set_error(SAS_ERR_ARG, "null output buffer");
     if (k) {

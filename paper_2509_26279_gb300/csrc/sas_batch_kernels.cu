@@ -160,7 +160,7 @@ __global__ void k_batch_cell_count(const BatchField* __restrict__ F, const Det* 
   for (uint32_t j = blockIdx.x * kWarps + (threadIdx.x >> 5); j < n_emit; j += gridDim.x * kWarps) {
     const Emit em = bf.args.emits[j];
     count_superbin(em, bf.args.tc.s, g, cg, cell_m, bin_m, dets, boff + bf.bucket_base, bf.ecount, bf.sxt,
-                   bf.syt, bf.args.n_min, lane,
+                   bf.syt, (em.flags & kEmitLowPeak) ? bf.args.n_low : bf.args.n_min, lane,
                    [&](int, uint32_t bx, uint32_t by, uint32_t distinct, uint32_t raw) {
                      Key k;
                      k.a = ((uint64_t)(~distinct) << 32) | (uint64_t)(~raw);
@@ -327,7 +327,7 @@ __global__ void k_batch_owned_flag(const BatchField* __restrict__ F, const unsig
     uint32_t mine = 0;
     for (uint32_t j = lane; j < cd.id_len; j += 32) mine += own[bf.ids[cd.id_off + j]] == c;
     mine = __reduce_add_sync(0xffffffffu, mine);
-    if (lane == 0) flag[cand_off[f] + c] = 2ull * mine >= cd.id_len || mine >= bf.args.n_min;
+    if (lane == 0) flag[cand_off[f] + c] = 2ull * mine >= cd.id_len || mine >= bf.args.n_low;
   }
 }
 

@@ -56,9 +56,13 @@ struct SearchGeom {
   uint64_t v_begin, v_end;
 };
 
-// Emitted cell (threshold crossing of the stack counters).
+// Emitted super-bin (threshold crossing of the stack counters); flags says why.
 struct __align__(16) Emit {
-  uint32_t v_idx, bx, by, pad;
+  uint32_t v_idx, bx, by, flags;
+};
+enum : uint32_t {
+  kEmitPlain = 1u,    // the super-bin's count reached n_min: its bins are counted against n_min
+  kEmitLowPeak = 2u,  // count >= n_low and no neighbour of the tile larger: counted against n_low
 };
 
 // Candidate sort key, compared lexicographically (a, b, c):
@@ -92,6 +96,7 @@ struct StackArgs {
   int32_t bin_is_one;  // s*bin == 1: the quotient is X itself
   int32_t merge;       // the P columns of a counter word span at most two super-bins
   uint32_t n_min;
+  uint32_t n_low;            // the counters' top bit means count >= n_low (n_low == n_min: one threshold)
   int32_t nvt_x, nvt_y;      // velocity blocks along kx, ky
   int32_t kx_lo, ky_lo;      // first lattice column/row covered by the blocks
   int32_t nst_x, nst_y;      // spatial tiles
@@ -148,9 +153,10 @@ int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t,
 // Same plan with counters twice as wide (after a counter wrapped).
 int replan_wider(const sas_grid_desc& d, uint64_t n, uint32_t n_min, const sas_opts& o,
                  const DevInfo& di, FieldPlan* fp);
-// Geometry, tiling and division parts of the stack kernel's arguments.
+// Geometry, tiling and division parts of the stack kernel's arguments
+// (n_low: the lower threshold of the tile-peak selection, n_min when off).
 struct StackArgs;
-void fill_stack_args(const FieldPlan& fp, uint32_t n_min, StackArgs* sa);
+void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, StackArgs* sa);
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 
@@ -190,7 +196,7 @@ cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
 cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, const SearchGeom& g,
                               const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
                               const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
-                              uint32_t n_min, Key* keys, uint32_t* n_valid,
+                              uint32_t n_min, uint32_t n_low, Key* keys, uint32_t* n_valid,
                               unsigned long long* raw_total, const uint8_t* wts, cudaStream_t s);
 cudaError_t launch_sort_keys(Key* keys, uint32_t n, uint32_t n_pad, cudaStream_t s);
 // Sorts every aligned segment of `seg` keys (a power of two) of keys[0..n_total)

@@ -312,7 +312,7 @@ int replan_wider(const sas_grid_desc& d, uint64_t n, uint32_t n_min, const sas_o
   return SAS_OK;
 }
 
-void fill_stack_args(const FieldPlan& fp, uint32_t n_min, StackArgs* sa) {
+void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, StackArgs* sa) {
   const TileCfg& tc = fp.tc;
   sa->g = fp.g;
   sa->cg = fp.cg;
@@ -328,6 +328,7 @@ void fill_stack_args(const FieldPlan& fp, uint32_t n_min, StackArgs* sa) {
   sa->merge = per_word >= 2 &&
               spread_bound((int64_t)(per_word - 1) * std::llabs((int64_t)fp.g.dvx), fp.dT, fp.g.tph) < sbin;
   sa->n_min = n_min;
+  sa->n_low = n_low && n_low < n_min ? n_low : n_min;
   sa->kx_lo = 0;
   sa->ky_lo = fp.ky_lo;
   sa->nvt_x = (int)div_ceil_u32((uint32_t)fp.g.nvx, tc.kx * tc.bvx);

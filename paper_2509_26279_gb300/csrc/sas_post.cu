@@ -44,7 +44,8 @@ __device__ __forceinline__ bool bin_window(const SearchGeom& g, const CoarseGeom
 }
 
 // One warp per emitted super-bin (count_superbin); every bin that reaches
-// n_min appends its key.
+// the super-bin's threshold (n_low for a tile-local peak, else n_min) appends
+// its key.
 constexpr int kMaxS = 4;
 
 template <bool W>
@@ -52,13 +53,15 @@ __global__ void k_cell_count(const Emit* __restrict__ emits, uint32_t n_emit, in
                              CoarseGeom cg, uint64_t cell_m, uint64_t bin_m, const Det* __restrict__ dets,
                              const uint32_t* __restrict__ boff, const uint32_t* __restrict__ ecount,
                              const int32_t* __restrict__ sxt, const int32_t* __restrict__ syt,
-                             uint32_t n_min, Key* __restrict__ keys, uint32_t* __restrict__ n_valid,
-                             unsigned long long* __restrict__ raw_total, const uint8_t* __restrict__ wts) {
+                             uint32_t n_min, uint32_t n_low, Key* __restrict__ keys,
+                             uint32_t* __restrict__ n_valid, unsigned long long* __restrict__ raw_total,
+                             const uint8_t* __restrict__ wts) {
   const uint32_t w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= n_emit) return;  // whole warps leave together
   const Emit em = emits[w];
-  count_superbin<W>(em, sb, g, cg, cell_m, bin_m, dets, boff, ecount, sxt, syt, n_min, lane,
+  const uint32_t thr = (em.flags & kEmitLowPeak) ? n_low : n_min;
+  count_superbin<W>(em, sb, g, cg, cell_m, bin_m, dets, boff, ecount, sxt, syt, thr, lane,
                  [&](int, uint32_t bx, uint32_t by, uint32_t distinct, uint32_t raw) {
                    Key k;
                    k.a = ((uint64_t)(~distinct) << 32) | (uint64_t)(~raw);
@@ -225,14 +228,14 @@ unsigned blocks_for(uint64_t n, unsigned per) { return (unsigned)((n + per - 1) 
 cudaError_t launch_cell_count(const Emit* emits, uint32_t n_emit, int s_bins, const SearchGeom& g,
                               const CoarseGeom& cg, const Det* dets, const uint32_t* boff,
                               const uint32_t* ecount, const int32_t* sxt, const int32_t* syt,
-                              uint32_t n_min, Key* keys, uint32_t* n_valid,
+                              uint32_t n_min, uint32_t n_low, Key* keys, uint32_t* n_valid,
                               unsigned long long* raw_total, const uint8_t* wts, cudaStream_t s) {
   if (n_emit == 0) return cudaSuccess;
   if (s_bins < 1 || s_bins > kMaxS) return cudaErrorInvalidValue;
   auto kern = wts ? k_cell_count<true> : k_cell_count<false>;
   kern<<<blocks_for(n_emit, kWarpsPerBlock), kWarpsPerBlock * 32, 0, s>>>(
       emits, n_emit, s_bins, g, cg, div_magic((uint32_t)cg.cell), div_magic((uint32_t)g.bin), dets, boff,
-      ecount, sxt, syt, n_min, keys, n_valid, raw_total, wts);
+      ecount, sxt, syt, n_min, n_low, keys, n_valid, raw_total, wts);
   note_launch();
   return cudaGetLastError();
 }

@@ -31,6 +31,17 @@
 // fall short of the number of pairs added, by 255 or 256 per wrap; the kernel
 // accumulates (sum - pairs) into a global balance and the host reruns with wider
 // counters when it is not zero, so the result is exact for any input.
+//
+// Two thresholds (n_low < N_min): the counters start at 2^(CB-1) - n_low and a
+// counter with the top bit set is emitted when its count reaches N_min (its
+// bins are counted against N_min, as above) or when no counter of the tile
+// adjacent to it -- lattice points and super-bins differing by at most one in
+// each of kx, ky, super-bin column and row -- holds a larger count (a
+// tile-local peak: its bins are counted against n_low).  A linear mover
+// raises a whole neighbourhood of velocities and super-bins, and a noise
+// alignment the velocities next to it; the peak test keeps the best of each
+// such group before any bin is counted.  Neighbours are read before any
+// counter of the tile is reset, so the reset runs as a second pass.
 #include <type_traits>
 
 #include "sas_internal.cuh"
@@ -314,8 +325,10 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
   const int sbins = tc.s;                          // bins per super-bin side
   const int rows_per_epoch = tc.rows;
   const bool single_chunk = E <= (uint32_t)tc.ec;
-  // counter start value: the top bit turns on when the count reaches n_min
-  const uint32_t start = (1u << (CB - 1)) - a.n_min;
+  // counter start value: the top bit turns on when the count reaches n_low
+  // (n_min with one threshold)
+  const uint32_t start = (1u << (CB - 1)) - a.n_low;
+  const bool two_thr = a.n_low < a.n_min;
   uint32_t start_word = 0;
 #pragma unroll
   for (int q = 0; q < P; ++q) start_word |= start << (CB * q);
@@ -501,7 +514,24 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       __syncthreads();  // the reductions above are asm: order them before any reader
     };
 
-    // --- read every counter of the tile: emit those at or over n_min, add up
+    // --- tile-local peak test of the counter (ky, kx, row, col) holding c:
+    //     no adjacent counter of the tile is larger -------------------------
+    auto is_peak = [&](int ky, int kx, int row, int col, uint32_t c) -> bool {
+      for (int ky2 = max(ky - 1, 0); ky2 <= min(ky + 1, KY - 1); ++ky2)
+        for (int kx2 = max(kx - 1, 0); kx2 <= min(kx + 1, KX - 1); ++kx2) {
+          const uint32_t* wb = cells + (uint32_t)(ky2 * (KX / P) + kx2 / P) * (uint32_t)txty;
+          const int sh = CB * (kx2 % P);
+          for (int r2 = max(row - 1, 0); r2 <= min(row + 1, tc.ty - 1); ++r2)
+            for (int c2 = max(col - 1, 0); c2 <= min(col + 1, tc.tx - 1); ++c2) {
+              const uint32_t v = (wb[r2 * tc.tx + c2] >> sh) & C::CMASK;
+              if (v > c) return false;  // the counter itself is not larger than itself
+            }
+        }
+      return true;
+    };
+
+    // --- read every counter of the tile: emit those at or over n_min (and,
+    //     with two thresholds, the tile-local peaks at or over n_low), add up
     //     the counts, and reset them to the start value -----------------------
     auto finish = [&](int kx0, int ky0) {
       __syncthreads();
@@ -523,11 +553,18 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
               const uint32_t r = widx / (uint32_t)txty, rem = widx % (uint32_t)txty;
               const uint32_t row = rem / (uint32_t)tc.tx, col = rem % (uint32_t)tc.tx;
               const uint32_t ky = r / (KX / P), kx = (r % (KX / P)) * P + lane;
+              uint32_t why = kEmitPlain;
+              if (two_thr) {
+                const uint32_t c = (wv[q] >> (CB * lane)) & C::CMASK;
+                why = c - start >= a.n_min ? kEmitPlain : 0u;
+                if (is_peak((int)ky, (int)kx, (int)row, (int)col, c)) why |= kEmitLowPeak;
+                if (!why) continue;
+              }
               Emit em;
               em.v_idx = (uint32_t)(ky0 + ky) * (uint32_t)g.nvx + (uint32_t)(kx0 + kx);
               em.bx = (uint32_t)bx0 + col * sbins;
               em.by = (uint32_t)by0 + row * sbins;
-              em.pad = 0;
+              em.flags = why;
               const uint32_t p = atomicAdd(&s_misc[43], 1u);
               if (p < (uint32_t)tc.emit_cap) {
                 s_emit[p] = em;
@@ -538,10 +575,13 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
             }
           }
         }
-        reinterpret_cast<uint4*>(cells)[i] = start4;
+        if (!two_thr) reinterpret_cast<uint4*>(cells)[i] = start4;
       }
       balance += (int64_t)acc - (int64_t)n_vec * 4 * P * start;
       __syncthreads();
+      if (two_thr) {  // every peak test has read its neighbours
+        for (uint32_t i = tid; i < n_words / 4; i += kNT) reinterpret_cast<uint4*>(cells)[i] = start4;
+      }
       const uint32_t ne_tile = min(s_misc[43], (uint32_t)tc.emit_cap);
       if (ne_tile) {
         if (tid == 0) s_misc[44] = atomicAdd(a.n_emit, ne_tile);

@@ -55,7 +55,7 @@ class sas_opts(ctypes.Structure):
                 ("tile_ky", ctypes.c_uint32), ("tile_bx", ctypes.c_uint32),
                 ("tile_by", ctypes.c_uint32), ("counter_bits", ctypes.c_uint32),
                 ("coarse_bins", ctypes.c_uint32), ("superbin", ctypes.c_uint32),
-                ("velocity_block", ctypes.c_uint32)]
+                ("velocity_block", ctypes.c_uint32), ("n_low", ctypes.c_uint32)]
 
 
 class sas_result_info(ctypes.Structure):
@@ -66,7 +66,7 @@ class sas_result_info(ctypes.Structure):
                 ("tile_bx", ctypes.c_uint32), ("tile_by", ctypes.c_uint32),
                 ("superbin", ctypes.c_uint32), ("vblock_x", ctypes.c_uint32),
                 ("vblock_y", ctypes.c_uint32), ("staged_cap", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("ms_stack", ctypes.c_float),
+                ("n_low", ctypes.c_uint32), ("ms_stack", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_prep", ctypes.c_float),
                 ("ms_count", ctypes.c_float), ("ms_ids", ctypes.c_float),
                 ("reserved_f", ctypes.c_float)]
@@ -80,6 +80,9 @@ assert CANDIDATE_DTYPE.itemsize == 32
 _p = ctypes.c_void_p
 _lib.sas_version.restype = ctypes.c_char_p
 _lib.sas_abi_version.restype = ctypes.c_int
+ABI_VERSION = 2  # the struct layouts below
+if _lib.sas_abi_version() != ABI_VERSION:
+    raise ImportError(f"{LIB_PATH} implements ABI {_lib.sas_abi_version()}, this binding ABI {ABI_VERSION}: rebuild")
 _lib.sas_kernel_launches.restype = ctypes.c_uint64
 _lib.sas_last_error.restype = ctypes.c_char_p
 _lib.sas_create_grid.argtypes = [ctypes.POINTER(sas_grid_desc), ctypes.POINTER(_p)]
