@@ -115,6 +115,8 @@ typedef struct sas_opts {
   uint32_t n_low;            /* 0: one threshold.  1 <= n_low <= n_min: also report the
                                 cells with >= n_low distinct epochs whose super-bin is
                                 a tile-local peak (see sas_stack); not with weights    */
+  uint32_t peaks_only;       /* 1: report only the cells of tile-local peaks (>= n_low,
+                                or >= n_min when n_low is 0); not with weights         */
 } sas_opts;
 
 /* One candidate trajectory: the cell (v_idx, bx, by) of the 3-D histogram with
@@ -148,7 +150,7 @@ typedef struct sas_result_info {
   float ms_prep;             /* ingest, buckets, reference epoch, shift tables    */
   float ms_count;            /* exact counts of emitted cells + ordering          */
   float ms_ids;              /* contributing ids + candidate records (+ host sync) */
-  float reserved_f;
+  uint32_t peaks_only;       /* the selection it ran with (sas_opts.peaks_only)    */
 } sas_result_info;
 
 typedef struct sas_grid sas_grid;      /* opaque, owned by the library */
@@ -200,7 +202,12 @@ int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8
  * (lattice points outside the searched set count 0).  This prunes the
  * neighbouring cells a mover or a noise alignment raises before they are
  * counted (an extension of the paper's threshold; the candidate list stays in
- * the same order).  stream: a
+ * the same order).  With opts->peaks_only = 1 the list holds only the cells
+ * with >= n_low distinct epochs (n_min when n_low is 0) whose super-bin is such
+ * a peak: the cells at or above n_min elsewhere -- the neighbourhood every
+ * mover raises around its best cell -- are pruned too, before counting, so
+ * the list is no longer complete at n_min (sas_peel then refuses it).
+ * stream: a
  * cudaStream_t (NULL = legacy default).  On success *out holds a new result
  * that the caller releases with sas_result_free; the result owns its device
  * memory.  The call synchronizes the stream before returning.

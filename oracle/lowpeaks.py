@@ -23,7 +23,10 @@ the raw counts within its tile.  Definitions, in the order they are used:
       R(v', B') > R(v, B);
   result: every cell (v, bx, by) with distinct >= N_min, and every cell with
       distinct >= n_low whose super-bin (bx // S, by // S) at v is a peak, in
-      the search's output order (distinct desc, raw desc, v_idx, by, bx).
+      the search's output order (distinct desc, raw desc, v_idx, by, bx);
+  peaks only: the cells with distinct >= n_low whose super-bin is a peak,
+      and no others (the cells at or above N_min elsewhere, the neighbourhood
+      a mover raises around its best cells, are left out as well).
 
 R is taken from the oracle's dense raw histograms (oracle.histogram), the
 cells and their ids from the oracle's search at n_low (oracle.stack); no code
@@ -119,21 +122,21 @@ def subset(res: OracleResult, keep: np.ndarray) -> OracleResult:
 
 
 def search(cat, grid, n_min: int, n_low: int, tiles: dict, v_begin: int = 0, v_end: int | None = None,
-           threads: int = 1) -> OracleResult:
+           threads: int = 1, peaks_only: bool = False) -> OracleResult:
     """The two-threshold search: oracle.stack at n_low, then each cell kept when
-    distinct >= n_min or its super-bin is a tile-local peak.  tiles = {"kx",
-    "ky", "bx", "by", "s"} (velocity tile, spatial tile in super-bins,
-    super-bin side in bins)."""
+    distinct >= n_min (unless peaks_only) or its super-bin is a tile-local
+    peak.  tiles = {"kx", "ky", "bx", "by", "s"} (velocity tile, spatial tile
+    in super-bins, super-bin side in bins)."""
     if v_end is None:
         v_end = grid.nvx * grid.nvy
     low = stack(cat, grid, n_low, v_begin, v_end, threads=threads)
-    if n_low >= n_min:
+    if n_low >= n_min and not peaks_only:
         return low
     R = SuperbinCounts(cat, grid, tiles["s"], v_begin, v_end)
     keep = np.zeros(len(low.cands), bool)
     peak_of = {}
     for i, c in enumerate(low.cands):
-        if int(c["distinct"]) >= n_min:
+        if int(c["distinct"]) >= n_min and not peaks_only:
             keep[i] = True
             continue
         v = int(c["v_idx"])

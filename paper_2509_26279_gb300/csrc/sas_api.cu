@@ -208,7 +208,9 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
   cudaStream_t s = (cudaStream_t)stream;
   if (n_min > (1u << 31)) return fail(SAS_ERR_ARG, "n_min must be <= 2^31");
   if (o.n_low > n_min) return fail(SAS_ERR_ARG, "n_low %u is above n_min %u", o.n_low, n_min);
-  if (o.n_low && weights) return fail(SAS_ERR_ARG, "n_low is not supported by the weighted search");
+  if ((o.n_low || o.peaks_only) && weights)
+    return fail(SAS_ERR_ARG, "n_low and peaks_only are not supported by the weighted search");
+  if (o.peaks_only > 1) return fail(SAS_ERR_ARG, "peaks_only must be 0 or 1");
   const uint32_t n_low = o.n_low ? o.n_low : n_min;
 
   sas_result* res = new (std::nothrow) sas_result;
@@ -218,6 +220,7 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
   res->n_det = n;
   res->n_min = n_min;
   res->info.n_low = n_low;
+  res->info.peaks_only = o.peaks_only;
 
   if (n == 0 || v_begin == v_end) {
     res->info.t0 = 0;
@@ -367,7 +370,7 @@ int stack_impl(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weig
       const TileCfg& tc = plan.tc;
       CK(sc.alloc(&d_emits, emit_cap), "alloc emissions");
       CK(stack_set_smem_attr(tc.kx, tc.ky, tc.cb, tc.smem), "smem attribute");
-      fill_stack_args(plan, n_min, n_low, &sa);
+      fill_stack_args(plan, n_min, n_low, o.peaks_only, &sa);
       sa.w = d_w;
       sa.dets = d_dets;
       sa.boff = d_boff;
@@ -586,6 +589,8 @@ int sas_peel(const sas_result* r, uint32_t n_min, uint32_t max_clusters, uint32_
     return fail(SAS_ERR_ARG, "n_min %u is below the search's threshold %u (cells under it are not in the list)",
                 n_min, r->n_min);
   if (!r->complete) return fail(SAS_ERR_ARG, "the search kept only its top candidates (max_candidates)");
+  if (r->info.peaks_only)
+    return fail(SAS_ERR_ARG, "the search kept only tile-local peaks (peaks_only): its list is not complete at n_min");
   if (r->weighted) return fail(SAS_ERR_ARG, "cluster finding counts distinct epochs; this search is weighted");
   if (flags & ~SAS_PEEL_SEQUENTIAL) return fail(SAS_ERR_ARG, "unknown flags 0x%x", flags);
   if (max_clusters == 0) max_clusters = 1000;

@@ -45,11 +45,12 @@ struct sas_batch {
   unsigned long long* d_c64 = nullptr;
   uint32_t* d_ecount_all = nullptr;
   size_t ecount_words = 0;
-  // Fields grouped by stack kernel configuration (velocity tile and counter
-  // width): one persistent stack launch per group, each over its own work
-  // counter and its fields' units.
+  // Fields grouped by stack kernel configuration (velocity tile, counter width,
+  // peak selection): one persistent stack launch per group, each over its own
+  // work counter and its fields' units.
   struct Group {
     int kx = 0, ky = 0, cb = 0;
+    bool peaks = false;
     std::vector<uint32_t> fields;
     size_t smem = 0;
     int grid = 0;
@@ -86,8 +87,8 @@ cudaError_t record_pass(sas_batch* b, cudaStream_t s) {
   if ((e = cudaMemsetAsync(b->dev.bucket_count, 0, b->dev.total_buckets * 4, s)) != cudaSuccess) return e;
   if ((e = batch_launch_prep(b->dev, s)) != cudaSuccess) return e;
   for (const sas_batch::Group& g : b->groups)
-    if ((e = launch_stack_multi(g.kx, g.ky, g.cb, g.d_args, g.d_unit_base, (int)g.fields.size(), g.d_work,
-                                g.smem, g.grid, s)) != cudaSuccess)
+    if ((e = launch_stack_multi(g.kx, g.ky, g.cb, g.peaks, g.d_args, g.d_unit_base, (int)g.fields.size(),
+                                g.d_work, g.smem, g.grid, s)) != cudaSuccess)
       return e;
   if ((e = batch_launch_post(b->dev, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b->h_ctr, b->d_ctr, (size_t)b->n_fields * kCtrN * 4,
@@ -145,7 +146,7 @@ int build_pass(sas_batch* b, const DevInfo& di, cudaStream_t s) {
     cand_off[f + 1] = cand_off[f] + b->key_seg;
     bucket_base[f + 1] = bucket_base[f] + fp.nb;
     ecount_base[f + 1] = ecount_base[f] + fp.g.E;
-    fill_stack_args(fp, b->n_min[f], b->opts[f].n_low, &hargs[f]);
+    fill_stack_args(fp, b->n_min[f], b->opts[f].n_low, b->opts[f].peaks_only, &hargs[f]);
     unit_base[f + 1] = unit_base[f] + hargs[f].n_tiles;
   }
   BatchDev& B = b->dev;
@@ -285,7 +286,22 @@ int build_pass(sas_batch* b, const DevInfo& di, cudaStream_t s) {
   for (const sas_batch::Group& g : b->groups)
     if (ce == cudaSuccess) ce = stack_set_smem_attr(g.kx, g.ky, g.cb, g.smem);
   if (ce == cudaSuccess) ce = batch_set_attrs();
+  // One launch of each group's stack kernel before the capture, with its work
+  // counter far past the end (0x7F7F...: every CTA leaves at once, and the
+  // counter cannot wrap): the kernel is loaded and its resources reserved
+  // outside the capture.
   if (ce != cudaSuccess) { rc = cuda_err(ce, "batch setup"); return rc; }
+  for (const sas_batch::Group& g : b->groups) {
+    ce = cudaMemsetAsync(g.d_work, 0x7F, 8, s);
+    if (ce == cudaSuccess)
+      ce = launch_stack_multi(g.kx, g.ky, g.cb, g.peaks, g.d_args, g.d_unit_base, (int)g.fields.size(), g.d_work,
+                              g.smem, g.grid, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess)
+      return set_errorf(SAS_ERR_CUDA, "batch setup: stack kernel (kx %d, ky %d, %d-bit counters%s, %zu B shared, "
+                                      "%d CTAs): %s", g.kx, g.ky, g.cb, g.peaks ? ", peaks" : "", g.smem, g.grid,
+                        cudaGetErrorString(ce));
+  }
   // --- record the pass as a graph ---------------------------------------------
   cudaStream_t cs;
   if ((ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_err(ce, "stream"); return rc; }
@@ -293,7 +309,7 @@ int build_pass(sas_batch* b, const DevInfo& di, cudaStream_t s) {
   cudaError_t ce2 = ce == cudaSuccess ? record_pass(b, cs) : ce;
   cudaGraph_t g = nullptr;
   if (ce == cudaSuccess) ce = cudaStreamEndCapture(cs, &g);
-  if (ce == cudaSuccess) ce = ce2;
+  if (ce2 != cudaSuccess) ce = ce2;  // the first failure inside the capture, not its consequence
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&b->exec, g, 0);
   b->graph = g;
   cudaStreamDestroy(cs);
@@ -348,6 +364,7 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
     if (opts) o = opts[f];
     if (o.n_low > n_min[f]) { rc = set_errorf(SAS_ERR_ARG, "field %u: n_low is above n_min", f); break; }
     if (o.n_low == 0) o.n_low = n_min[f];
+    if (o.peaks_only > 1) { rc = set_errorf(SAS_ERR_ARG, "field %u: peaks_only must be 0 or 1", f); break; }
     // 8-bit counters (start 128 - n_low) wrap past 128 + n_low detections in
     // one super-bin: a field whose brightest mover (one detection per epoch)
     // plus a generous noise allowance could get there counts in 16 bits.  A
@@ -377,14 +394,16 @@ int sas_batch_create(const sas_grid* const* grids, const sas_catalog* cats, cons
   for (uint32_t f = 0; f < n_fields; ++f) {
     const TileCfg& tc = b->plans[f].tc;
     sas_batch::Group* g = nullptr;
+    const bool peaks = b->opts[f].peaks_only || b->opts[f].n_low < b->n_min[f];
     for (sas_batch::Group& h : b->groups)
-      if (h.kx == tc.kx && h.ky == tc.ky && h.cb == tc.cb) g = &h;
+      if (h.kx == tc.kx && h.ky == tc.ky && h.cb == tc.cb && h.peaks == peaks) g = &h;
     if (!g) {
       b->groups.emplace_back();
       g = &b->groups.back();
       g->kx = tc.kx;
       g->ky = tc.ky;
       g->cb = tc.cb;
+      g->peaks = peaks;
     }
     g->fields.push_back(f);
     g->smem = std::max(g->smem, tc.smem);
@@ -503,6 +522,7 @@ int sas_batch_field_info(const sas_batch* b, uint32_t field, sas_result_info* in
   info->vblock_y = (uint32_t)tc.bvy;
   info->staged_cap = (uint32_t)tc.scap;
   info->n_low = b->opts[field].n_low;
+  info->peaks_only = b->opts[field].peaks_only;
   info->ms_total = b->ms_last;
   return SAS_OK;
 }

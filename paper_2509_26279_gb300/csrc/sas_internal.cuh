@@ -60,6 +60,10 @@ struct SearchGeom {
 struct __align__(16) Emit {
   uint32_t v_idx, bx, by, flags;
 };
+// Which counters the stack kernel emits: every one at or over n_min (one
+// threshold); those plus the tile-local peaks at or over n_low; or only the
+// tile-local peaks at or over n_low.
+enum : uint32_t { kSelectAll = 0u, kSelectPlainAndPeaks = 1u, kSelectPeaks = 2u };
 enum : uint32_t {
   kEmitPlain = 1u,    // the super-bin's count reached n_min: its bins are counted against n_min
   kEmitLowPeak = 2u,  // count >= n_low and no neighbour of the tile larger: counted against n_low
@@ -97,6 +101,7 @@ struct StackArgs {
   int32_t merge;       // the P columns of a counter word span at most two super-bins
   uint32_t n_min;
   uint32_t n_low;            // the counters' top bit means count >= n_low (n_low == n_min: one threshold)
+  uint32_t select;           // kSelectAll, kSelectPlainAndPeaks or kSelectPeaks
   int32_t nvt_x, nvt_y;      // velocity blocks along kx, ky
   int32_t kx_lo, ky_lo;      // first lattice column/row covered by the blocks
   int32_t nst_x, nst_y;      // spatial tiles
@@ -154,9 +159,10 @@ int plan_field(const sas_grid_desc& d, uint64_t n, uint32_t E, const int64_t* t,
 int replan_wider(const sas_grid_desc& d, uint64_t n, uint32_t n_min, const sas_opts& o,
                  const DevInfo& di, FieldPlan* fp);
 // Geometry, tiling and division parts of the stack kernel's arguments
-// (n_low: the lower threshold of the tile-peak selection, n_min when off).
+// (n_low: the lower threshold of the tile-peak selection, 0 or n_min when off;
+// peaks_only: emit the tile-local peaks alone).
 struct StackArgs;
-void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, StackArgs* sa);
+void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, uint32_t peaks_only, StackArgs* sa);
 
 // ---- launchers (defined in the .cu files) ----------------------------------
 
@@ -177,17 +183,26 @@ cudaError_t launch_scan_u32_to_u64(const uint32_t* in, unsigned long long* out, 
                                    unsigned long long* scratch, cudaStream_t s);
 size_t scan_scratch_elems(uint64_t n);
 
-// sas_stack.cu
+// sas_stack.cu (kernel: sas_stack_kernel.cuh)
 bool stack_config_supported(int kx, int ky, int cb);
 size_t stack_smem_bytes(const TileCfg& tc);
 size_t stack_counter_bytes(const TileCfg& tc);
+// Launches the instantiation with peak selection when a.select != kSelectAll.
 cudaError_t launch_stack(const StackArgs& a, int grid, cudaStream_t s);
 // One persistent launch over the units of several fields (per-field StackArgs in
-// device memory; field f owns units [unit_base[f], unit_base[f+1]) of counter).
-cudaError_t launch_stack_multi(int kx, int ky, int cb, const StackArgs* fargs,
+// device memory; field f owns units [unit_base[f], unit_base[f+1]) of counter);
+// peaks: the fields' select is not kSelectAll (all fields of a launch agree).
+cudaError_t launch_stack_multi(int kx, int ky, int cb, bool peaks, const StackArgs* fargs,
                                const unsigned long long* unit_base, int n_fields,
                                unsigned long long* counter, size_t smem, int grid, cudaStream_t s);
+// Sets the shared-memory limit of both instantiations.
 cudaError_t stack_set_smem_attr(int kx, int ky, int cb, size_t smem);
+// sas_stack_peaks.cu: the same with peak selection
+cudaError_t launch_stack_peaks(const StackArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_stack_multi_peaks(int kx, int ky, int cb, const StackArgs* fargs,
+                                     const unsigned long long* unit_base, int n_fields,
+                                     unsigned long long* counter, size_t smem, int grid, cudaStream_t s);
+cudaError_t stack_set_smem_attr_peaks(int kx, int ky, int cb, size_t smem);
 
 // sas_post.cu
 // Appends one key per bin of an emitted super-bin that lies in the domain and

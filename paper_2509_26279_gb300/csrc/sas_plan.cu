@@ -143,6 +143,8 @@ int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int
       tc.ty = std::min((int)(cells_bytes * 8 / ((int64_t)kx * ky * cb * tc.tx)) & ~3, dom_y);
     tc.tx = std::max(tc.tx, 4);
     tc.ty = std::max(tc.ty, 4);
+    if (tc.tx >= 4096 || tc.ty >= 4096)  // the kernel packs tile positions in 12 bits
+      return set_error(SAS_ERR_ARG, "tile_bx and tile_by must be below 4096");
     if (((int64_t)tc.tx * tc.ty) % 4 != 0)
       return set_error(SAS_ERR_ARG, "tile_bx * tile_by must be a multiple of 4");
     const int64_t tw = (int64_t)tc.tx * sbin, th = (int64_t)tc.ty * sbin;
@@ -312,7 +314,7 @@ int replan_wider(const sas_grid_desc& d, uint64_t n, uint32_t n_min, const sas_o
   return SAS_OK;
 }
 
-void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, StackArgs* sa) {
+void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, uint32_t peaks_only, StackArgs* sa) {
   const TileCfg& tc = fp.tc;
   sa->g = fp.g;
   sa->cg = fp.cg;
@@ -329,6 +331,7 @@ void fill_stack_args(const FieldPlan& fp, uint32_t n_min, uint32_t n_low, StackA
               spread_bound((int64_t)(per_word - 1) * std::llabs((int64_t)fp.g.dvx), fp.dT, fp.g.tph) < sbin;
   sa->n_min = n_min;
   sa->n_low = n_low && n_low < n_min ? n_low : n_min;
+  sa->select = peaks_only ? kSelectPeaks : (sa->n_low < n_min ? kSelectPlainAndPeaks : kSelectAll);
   sa->kx_lo = 0;
   sa->ky_lo = fp.ky_lo;
   sa->nvt_x = (int)div_ceil_u32((uint32_t)fp.g.nvx, tc.kx * tc.bvx);

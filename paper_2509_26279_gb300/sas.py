@@ -55,7 +55,8 @@ class sas_opts(ctypes.Structure):
                 ("tile_ky", ctypes.c_uint32), ("tile_bx", ctypes.c_uint32),
                 ("tile_by", ctypes.c_uint32), ("counter_bits", ctypes.c_uint32),
                 ("coarse_bins", ctypes.c_uint32), ("superbin", ctypes.c_uint32),
-                ("velocity_block", ctypes.c_uint32), ("n_low", ctypes.c_uint32)]
+                ("velocity_block", ctypes.c_uint32), ("n_low", ctypes.c_uint32),
+                ("peaks_only", ctypes.c_uint32)]
 
 
 class sas_result_info(ctypes.Structure):
@@ -69,7 +70,7 @@ class sas_result_info(ctypes.Structure):
                 ("n_low", ctypes.c_uint32), ("ms_stack", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("ms_prep", ctypes.c_float),
                 ("ms_count", ctypes.c_float), ("ms_ids", ctypes.c_float),
-                ("reserved_f", ctypes.c_float)]
+                ("peaks_only", ctypes.c_uint32)]
 
 
 # sas_candidate as a NumPy record (32 bytes, same layout as the C struct)

@@ -65,6 +65,29 @@ def n_low(n_epochs: int) -> int:
     return max(5, -(-n_epochs // 14))
 
 
+def noise_floor(n_detections: int, grid, budget: float = 5e4, superbin: int = 3) -> int:
+    """Smallest k for which uniform noise of n_detections over the field is
+    expected to fill fewer than `budget` (lattice point, superbin x superbin
+    super-bin) pairs with k or more detections (Poisson tail, Sec. 2.2's
+    false-positive count): below it a lowered threshold finds noise, not
+    fainter movers."""
+    n_sb = -(-grid.nbx // superbin) * -(-grid.nby // superbin)
+    pairs = float(n_sb) * grid.nvx * grid.nvy
+    lam = n_detections / float(n_sb)
+    k, below, term = 0, 0.0, math.exp(-lam)   # below = P(X < k), term = P(X = k)
+    while (1.0 - below) * pairs > budget:
+        below += term
+        k += 1
+        term *= lam / k
+    return max(k, 1)
+
+
+def lowered_threshold(n_epochs: int, n_min: int, n_detections: int, grid, div: int = 6) -> int:
+    """The lowered threshold ceil(E/div), raised to the field's noise floor and
+    capped at n_min."""
+    return min(n_min, max(-(-n_epochs // div), noise_floor(n_detections, grid)))
+
+
 def truth_match(cands, ids, mover: np.ndarray) -> np.ndarray:
     """Mover index matched by each candidate (>= 50 % of its ids), else -1."""
     n = len(cands)

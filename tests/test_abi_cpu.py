@@ -44,7 +44,7 @@ def test_every_declared_symbol_is_exported(sas):
 def test_struct_sizes_match_header(sas):
     assert ctypes.sizeof(sas.sas_grid_desc) == 13 * 4
     assert ctypes.sizeof(sas.sas_catalog) == 8 + 3 * 8 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(sas.sas_opts) == 3 * 8 + 10 * 4   # 9 uint32 fields + tail padding to 8 bytes
+    assert ctypes.sizeof(sas.sas_opts) == 3 * 8 + 10 * 4   # 10 uint32 fields
     assert ctypes.sizeof(sas.sas_result_info) == 5 * 8 + 10 * 4 + 6 * 4
     assert sas.CANDIDATE_DTYPE.itemsize == 32
 

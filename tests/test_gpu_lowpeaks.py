@@ -21,14 +21,15 @@ from paper_2509_26279_gb300 import sas  # noqa: E402
 from tests.test_gpu_parity import assert_same, gpu_tuples, oracle_tuples  # noqa: E402
 
 
-def run_two(cat, grid, n_min, n_low, v_begin=0, v_end=None, **optkw):
-    o = sas.make_opts(n_low=n_low, **optkw)
+def run_two(cat, grid, n_min, n_low, v_begin=0, v_end=None, peaks_only=0, **optkw):
+    o = sas.make_opts(n_low=n_low, peaks_only=peaks_only, **optkw)
     if v_end is not None:
         o.v_begin, o.v_end = v_begin, v_end
     res = sas.stack_catalog(sas.Grid(grid), cat, n_min, opts=o)
     info = res.info()
-    assert info["n_low"] == (n_low or n_min)
-    ref = LP.search(cat, grid, n_min, n_low or n_min, LP.tiles_of(info), v_begin, v_end)
+    assert info["n_low"] == (n_low or n_min) and info["peaks_only"] == peaks_only
+    ref = LP.search(cat, grid, n_min, n_low or n_min, LP.tiles_of(info), v_begin, v_end,
+                    peaks_only=bool(peaks_only))
     return res, ref
 
 
@@ -38,7 +39,7 @@ def test_random_tiny_catalogs(seed):
     rng = np.random.default_rng(seed + 500)
     n_min += int(rng.integers(0, 3))
     n_low = int(rng.integers(1, n_min + 1))
-    res, ref = run_two(cat, grid, n_min, n_low)
+    res, ref = run_two(cat, grid, n_min, n_low, peaks_only=int(seed % 3 == 0))
     assert_same(res, ref)
 
 
@@ -58,12 +59,15 @@ def _scaled(seed=5, **kw):
 def test_tile_configurations(cfg):
     """Every tile shape gives the oracle's list for its own tiles (the peak test
     is tile-local, so the list depends on the tiles; the oracle takes them from
-    the result)."""
+    the result), with and without the cells at N_min outside the peaks."""
     w, cat = _scaled()
     res, ref = run_two(cat, w.grid, 10, 6, **cfg)
     plain = oracle.stack(cat, w.grid, 10)
     assert len(ref.cands) > len(plain.cands) > 0
     assert_same(res, ref)
+    res, ref_po = run_two(cat, w.grid, 10, 6, peaks_only=1, **cfg)
+    assert_same(res, ref_po)
+    assert 0 < len(ref_po.cands) < len(ref.cands)
 
 
 def test_speed_annulus_and_lattice_ranges():
@@ -71,9 +75,12 @@ def test_speed_annulus_and_lattice_ranges():
     g = W.GridSpec(**{**w.grid.__dict__, "speed_min": 2000, "speed_max": 9000})
     res, ref = run_two(cat, g, 9, 5, tile_kx=8, tile_ky=8)
     assert_same(res, ref)
+    res, ref = run_two(cat, g, 9, 5, peaks_only=1, tile_kx=8, tile_ky=8)
+    assert_same(res, ref)
     nv = w.grid.nvx * w.grid.nvy
-    for a, b in [(0, 17), (5, nv // 2), (nv // 3, nv), (nv - 1, nv), (3 * w.grid.nvx + 2, 9 * w.grid.nvx + 5)]:
-        res, ref = run_two(cat, w.grid, 9, 5, v_begin=a, v_end=b, tile_kx=8, tile_ky=4)
+    for k, (a, b) in enumerate([(0, 17), (5, nv // 2), (nv // 3, nv), (nv - 1, nv),
+                                (3 * w.grid.nvx + 2, 9 * w.grid.nvx + 5)]):
+        res, ref = run_two(cat, w.grid, 9, 5, v_begin=a, v_end=b, peaks_only=k % 2, tile_kx=8, tile_ky=4)
         assert_same(res, ref)
 
 
@@ -97,6 +104,18 @@ def test_fewer_emissions_than_the_low_search():
     assert res.info()["n_candidates"] < low.info()["n_candidates"]
 
 
+def test_peaks_only_at_n_min_and_peel_refuses_it():
+    """peaks_only without n_low: the peaks at N_min alone, fewer than the plain
+    list; cluster finding needs the complete list and refuses it."""
+    w, cat = _scaled(seed=12)
+    res, ref = run_two(cat, w.grid, 9, 0, peaks_only=1)
+    assert_same(res, ref)
+    plain = oracle.stack(cat, w.grid, 9)
+    assert 0 < len(ref.cands) < len(plain.cands)
+    with pytest.raises(sas.SasError):
+        sas.sas_peel(res, 9, 100)
+
+
 def test_counter_wrap_reruns_wider():
     x = [5000] * 300 + [5000] + [9000] * 3
     y = [7000] * 300 + [7000] + [3000] * 3
@@ -107,6 +126,8 @@ def test_counter_wrap_reruns_wider():
     res, ref = run_two(cat, grid, 3, 2)
     assert_same(res, ref)
     assert res.info()["counter_bits"] >= 16
+    res, ref = run_two(cat, grid, 3, 2, peaks_only=1)
+    assert_same(res, ref)
 
 
 def test_argument_errors():
@@ -118,6 +139,11 @@ def test_argument_errors():
     with pytest.raises(sas.SasError):
         sas.sas_stack_weighted(g, cat.x, cat.y, cat.epoch, wts, cat.t, cat.ticks_per_hour, 5,
                                opts=sas.make_opts(n_low=3))
+    with pytest.raises(sas.SasError):
+        sas.sas_stack_weighted(g, cat.x, cat.y, cat.epoch, wts, cat.t, cat.ticks_per_hour, 5,
+                               opts=sas.make_opts(peaks_only=1))
+    with pytest.raises(sas.SasError):
+        sas.stack_catalog(g, cat, 5, opts=sas.make_opts(peaks_only=2))
 
 
 def _dev(cat):
@@ -128,8 +154,8 @@ def _dev(cat):
 
 def test_batch_fields_match_the_oracle():
     """Uneven small fields in one batch, each at N_min = ceil(E/4) with n_low =
-    ceil(E/6) (two of them with n_low off), field by field against the oracle
-    with the field's own tiles."""
+    ceil(E/6) (two of them with n_low off; three with the peaks alone), field
+    by field against the oracle with the field's own tiles."""
     rng = np.random.default_rng(77)
     fields, specs, opts = [], [], []
     for i in range(6):
@@ -139,17 +165,18 @@ def test_batch_fields_match_the_oracle():
                      grid_half=int(rng.integers(6, 14)), seed=7700 + i)
         cat = W.load(w)
         n_min, n_low = max(3, -(-E // 4)), (0 if i in (2, 4) else max(2, -(-E // 6)))
+        po = int(i in (1, 4, 5))
         x, y, e = _dev(cat)
         fields.append((sas.Grid(w.grid), x, y, e, cat.t, cat.ticks_per_hour, n_min))
-        specs.append((w, cat, n_min, n_low))
-        opts.append(sas.make_opts(n_low=n_low, tile_kx=8, tile_ky=8 if i % 2 else 4))
+        specs.append((w, cat, n_min, n_low, po))
+        opts.append(sas.make_opts(n_low=n_low, peaks_only=po, tile_kx=8, tile_ky=8 if i % 2 else 4))
     b = sas.Batch(fields, opts=opts)
     b.run()
     assert b.stats()[1] == 0
-    for f, (w, cat, n_min, n_low) in enumerate(specs):
+    for f, (w, cat, n_min, n_low, po) in enumerate(specs):
         info = b.field_info(f)
-        assert info["n_low"] == (n_low or n_min)
-        ref = LP.search(cat, w.grid, n_min, n_low or n_min, LP.tiles_of(info))
+        assert info["n_low"] == (n_low or n_min) and info["peaks_only"] == po
+        ref = LP.search(cat, w.grid, n_min, n_low or n_min, LP.tiles_of(info), peaks_only=bool(po))
         c, ids = b.candidates(f)
         assert len(c) == len(ref.cands)
         for fg, fo in [("v_idx", "v_idx"), ("bx", "bx"), ("by", "by"), ("count", "distinct"), ("raw", "raw"),

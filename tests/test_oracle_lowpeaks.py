@@ -13,7 +13,7 @@ from paper_2509_26279_gb300 import workloads as W
 from tests import cases
 
 
-def brute_two(cat, grid, n_min, n_low, tiles, v_begin, v_end):
+def brute_two(cat, grid, n_min, n_low, tiles, v_begin, v_end, peaks_only=False):
     """Every nonempty cell from the brute-force search, R as sums of raw counts
     over each super-bin, the peak test against every other super-bin."""
     cells, _ = brute.search(cat.x, cat.y, cat.epoch, cat.t, cat.ticks_per_hour, grid, 1)
@@ -39,7 +39,8 @@ def brute_two(cat, grid, n_min, n_low, tiles, v_begin, v_end):
     out = []
     for c in cells:
         v, bx, by, d = c[0], c[1], c[2], c[3]
-        if d >= n_min or (d >= n_low and peak((v % grid.nvx, v // grid.nvx, bx // s, by // s))):
+        plain = d >= n_min and not peaks_only
+        if plain or (d >= n_low and peak((v % grid.nvx, v // grid.nvx, bx // s, by // s))):
             out.append(c)
     return out
 
@@ -64,7 +65,7 @@ def random_case(seed):
     if rng.random() < 0.4:
         v_begin = int(rng.integers(0, nv))
         v_end = int(rng.integers(v_begin, nv + 1))
-    return cat, grid, n_min, n_low, random_tiles(rng), v_begin, v_end
+    return cat, grid, n_min, n_low, random_tiles(rng), v_begin, v_end, bool(rng.random() < 0.35)
 
 
 def pins_pass(mod) -> bool:
@@ -72,9 +73,9 @@ def pins_pass(mod) -> bool:
     an exception counts as a failed pin."""
     try:
         for seed in range(40):
-            cat, grid, n_min, n_low, tiles, vb, ve = random_case(seed)
-            got = tuples(mod.search(cat, grid, n_min, n_low, tiles, vb, ve))
-            if got != brute_two(cat, grid, n_min, n_low, tiles, vb, ve):
+            cat, grid, n_min, n_low, tiles, vb, ve, po = random_case(seed)
+            got = tuples(mod.search(cat, grid, n_min, n_low, tiles, vb, ve, peaks_only=po))
+            if got != brute_two(cat, grid, n_min, n_low, tiles, vb, ve, po):
                 return False
         return hand_built_holds(mod)
     except Exception:
@@ -83,9 +84,9 @@ def pins_pass(mod) -> bool:
 
 @pytest.mark.parametrize("seed", range(40))
 def test_equals_brute_force(seed):
-    cat, grid, n_min, n_low, tiles, vb, ve = random_case(seed)
-    got = tuples(LP.search(cat, grid, n_min, n_low, tiles, vb, ve))
-    assert got == brute_two(cat, grid, n_min, n_low, tiles, vb, ve)
+    cat, grid, n_min, n_low, tiles, vb, ve, po = random_case(seed)
+    got = tuples(LP.search(cat, grid, n_min, n_low, tiles, vb, ve, peaks_only=po))
+    assert got == brute_two(cat, grid, n_min, n_low, tiles, vb, ve, po)
 
 
 @pytest.mark.parametrize("seed", range(10))
@@ -102,6 +103,7 @@ def test_one_point_tiles_is_the_low_search(seed):
     n_min += 2
     tiles = {"kx": 1, "ky": 1, "bx": 1, "by": 1, "s": int(np.random.default_rng(seed).integers(1, 5))}
     assert tuples(LP.search(cat, grid, n_min, 1, tiles)) == tuples(oracle.stack(cat, grid, 1))
+    assert tuples(LP.search(cat, grid, n_min, 1, tiles, peaks_only=True)) == tuples(oracle.stack(cat, grid, 1))
 
 
 def test_between_the_plain_searches_on_a_field():
@@ -137,6 +139,7 @@ def hand_built_holds(mod) -> bool:
     cat, grid = hand_built()
     tiles = {"kx": 8, "ky": 8, "bx": 64, "by": 64, "s": 2}
     got = {(c[0], c[1], c[2]): c[3] for c in tuples(mod.search(cat, grid, 10, 5, tiles))}
+    only = {(c[0], c[1], c[2]): c[3] for c in tuples(mod.search(cat, grid, 10, 5, tiles, peaks_only=True))}
     v00, v10 = 4 * 8 + 4, 4 * 8 + 5       # (vx, vy) = (0, 0) and (1, 0)
     return (got.get((v00, 10, 10)) == 6      # the faint source at its velocity
             and got.get((v10, 10, 10)) == 6  # and at the next one (equal super-bin count: a tie)
@@ -144,7 +147,12 @@ def hand_built_holds(mod) -> bool:
             and got.get((v10, 29, 30)) == 10  # its neighbour at N_min (plain threshold)
             # at v = (1, 0) its 6 detections of epochs 0-5 stay in bin 30, a ghost
             # below N_min whose super-bin holds 6 against 20 at v = (0, 0): pruned
-            and (v10, 30, 30) not in got)
+            and (v10, 30, 30) not in got
+            # peaks only: the sources' peaks stay; the cell at N_min whose super-bin
+            # (bins 28-29: 14 detections) sits next to the 20 at v = (0, 0) goes
+            and only.get((v00, 10, 10)) == 6 and only.get((v10, 10, 10)) == 6
+            and only.get((v00, 30, 30)) == 20 and (v10, 29, 30) not in only
+            and set(only) <= set(got))
 
 
 def test_hand_built_movers():
@@ -163,7 +171,9 @@ MUTANTS = {
     "range_not_zeroed": ("    if not (v_begin <= v < v_end):\n        return False\n", ""),
     "superbin_transposed": ('sb = (int(c["bx"]) // tiles["s"], int(c["by"]) // tiles["s"])',
                             'sb = (int(c["by"]) // tiles["s"], int(c["bx"]) // tiles["s"])'),
-    "plain_exclusive": ('if int(c["distinct"]) >= n_min:', 'if int(c["distinct"]) > n_min:'),
+    "plain_exclusive": ('if int(c["distinct"]) >= n_min and not peaks_only:',
+                        'if int(c["distinct"]) > n_min and not peaks_only:'),
+    "peaks_only_ignored": ('if int(c["distinct"]) >= n_min and not peaks_only:', 'if int(c["distinct"]) >= n_min:'),
     "neighbourhood_one_sided": ("for kx2 in (kx - 1, kx, kx + 1):", "for kx2 in (kx - 1, kx):"),
     "spatial_one_sided": ("for sby2 in (sby - 1, sby, sby + 1):", "for sby2 in (sby, sby + 1):"),
 }
