@@ -89,6 +89,7 @@ struct TileCfg {
   int seg_cap;       // segment slots per chunk (= nt)
   int scap;          // staged detection records
   int emit_cap;      // per-CTA emission buffer entries
+  int peak_cap;      // per-CTA list of counters awaiting the peak test (0: no peak selection)
   size_t smem;       // dynamic shared memory bytes
 };
 

@@ -48,6 +48,7 @@ bool magic_exact(int32_t bin, int64_t x_max) {
 constexpr int kStackThreads = 1024;
 constexpr int kSegCap = kStackThreads;  // one (epoch, bucket row) segment per thread
 constexpr int kEmitCap = 256;
+constexpr int kPeakCap = 1024;  // one counter per thread and batch
 constexpr int kMaxEpochChunk = 256;     // staged records carry the epoch in 8 bits
 
 struct Plan {
@@ -111,6 +112,7 @@ int choose_tiles(const sas_grid_desc& d, uint32_t E, uint64_t n, int64_t dT, int
   tc.nt = kStackThreads;
   tc.seg_cap = kSegCap;
   tc.emit_cap = kEmitCap;
+  tc.peak_cap = (o.n_low || o.peaks_only) ? kPeakCap : 0;
   const int64_t budget = (int64_t)di.smem_optin - 1024;  // room for static shared memory
   const int64_t sbin = (int64_t)sb * d.bin;
   // velocity block: keep the union window within ~15% of the tile per axis

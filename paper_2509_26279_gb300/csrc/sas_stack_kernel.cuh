@@ -60,7 +60,7 @@ constexpr int kNT = 1024;
 constexpr int32_t kOutside = -(1 << 30);  // table entry of a lattice column that does not exist
 
 struct SmemLayout {
-  size_t cells, staged, ox, oy, win, seg_pos, seg_src, emit, misc, total;
+  size_t cells, staged, ox, oy, win, seg_pos, seg_src, emit, peaks, misc, total;
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -91,6 +91,8 @@ __host__ __device__ inline SmemLayout layout(const TileCfg& tc) {
   off += align16((size_t)tc.seg_cap * 4);
   L.emit = off;
   off += align16((size_t)tc.emit_cap * sizeof(Emit));
+  L.peaks = off;
+  off += align16((size_t)tc.peak_cap * 4);
   L.misc = off;
   off += 512;
   L.total = off;
@@ -314,10 +316,11 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
   uint32_t* s_seg_pos = reinterpret_cast<uint32_t*>(smem + L.seg_pos);
   uint32_t* s_seg_src = reinterpret_cast<uint32_t*>(smem + L.seg_src);
   Emit* s_emit = reinterpret_cast<Emit*>(smem + L.emit);
+  uint32_t* s_peaks = reinterpret_cast<uint32_t*>(smem + L.peaks);
   uint32_t* s_misc = reinterpret_cast<uint32_t*>(smem + L.misc);
   // s_misc: [0..33) scan scratch, [42] active mask (points 0-31), [45] (points 32-63),
   //         [43] emission count,
-  //         [44] flush base
+  //         [44] flush base, [46] peak-test list fill
   const int tid = threadIdx.x;
   constexpr int P = C::P;
   const uint32_t n_words = (uint32_t)KY * (KX / P) * tc.tx * tc.ty;
@@ -334,7 +337,6 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
   // counter start value: the top bit turns on when the count reaches n_low
   // (n_min with one threshold)
   const uint32_t start = (1u << (CB - 1)) - a.n_low;
-  constexpr bool two_thr = PEAKS;  // peak tests (and a second pass resetting what they read)
   uint32_t start_word = 0;
 #pragma unroll
   for (int q = 0; q < P; ++q) start_word |= start << (CB * q);
@@ -577,7 +579,11 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       if (tid == 0) s_misc[43] = 0;
     };
 
-    // Peak selection: the counters with the top bit set are taken warp by warp.
+    // Peak selection.  A first pass reads every word like the one-threshold
+    // pass (and resets the words with no counter at or over n_low: only such
+    // a counter can be larger than one that is); a second pass takes, warp by
+    // warp, only the rounds in which some lane holds one, and the words it
+    // read are reset after a barrier.
     auto finish_peaks = [&](int kx0, int ky0) {
       __syncthreads();
       using Acc = typename std::conditional<CB <= 16, uint32_t, uint64_t>::type;
@@ -586,124 +592,125 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
       const int wl = tid & 31;
       const uint32_t lt_mask = (1u << wl) - 1u;
       const uint32_t nv4 = n_words / 4;
-      // Peak tests read neighbours, so a word holding a counter with the top
-      // bit set is reset only after every test (second pass, bit k of
-      // `deferred` for round k).  Every other word is reset at once: only a
-      // counter with the top bit set can be larger than one that has it.
-      uint32_t deferred = 0;
-      // Every thread runs the same number of rounds (the last one partly idle),
-      // so the emissions of a round are taken warp by warp: one shared-memory
-      // reservation per warp and step, and one global one for what overflows
-      // the CTA's buffer.
-      for (uint32_t i0 = 0, k = 0; i0 < nv4; i0 += kNT, ++k) {
-        const uint32_t i = i0 + tid;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (i < nv4) {
-          v = reinterpret_cast<const uint4*>(cells)[i];
+      uint32_t hit = 0;   // bit k: this thread's word of round k holds a counter with the top bit set
+      uint32_t ntop = 0;  // how many such counters this thread's words hold
+      {
+        uint32_t k = 0;
+        for (uint32_t i = tid; i < nv4; i += kNT, ++k) {
+          const uint4 v = reinterpret_cast<const uint4*>(cells)[i];
           acc += (Acc)word_sum<CB>(v.x) + (Acc)word_sum<CB>(v.y) + (Acc)word_sum<CB>(v.z) + (Acc)word_sum<CB>(v.w);
           ++n_vec;
-        }
-        // bit q * P + l: counter l of word q has its top bit set
-        uint32_t todo = 0;
-        if ((v.x | v.y | v.z | v.w) & tmask) {
-#pragma unroll
-          for (int l = 0; l < P; ++l) {
-            const int sh = CB * l + CB - 1;
-            todo |= ((v.x >> sh) & 1u) << l;
-            todo |= ((v.y >> sh) & 1u) << (P + l);
-            todo |= ((v.z >> sh) & 1u) << (2 * P + l);
-            todo |= ((v.w >> sh) & 1u) << (3 * P + l);
+          if ((v.x | v.y | v.z | v.w) & tmask) {
+            hit |= 1u << k;
+            ntop += __popc(v.x & tmask) + __popc(v.y & tmask) + __popc(v.z & tmask) + __popc(v.w & tmask);
+          } else {
+            reinterpret_cast<uint4*>(cells)[i] = start4;
           }
         }
-        if (i < nv4) {
-          if (two_thr && todo) deferred |= 1u << k;
-          else reinterpret_cast<uint4*>(cells)[i] = start4;
-        }
-        while (__any_sync(0xffffffffu, todo != 0)) {
-          uint32_t why = 0, c = 0;
-          uint32_t pos = 0;  // ky << 28 | kx << 24 | row << 12 | col (tiles of < 4096 super-bins a side)
-          bool test = false;
-          if (todo) {
-            const int b = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int q = b / P, l = b % P;
-            const uint32_t wq = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-            const uint32_t widx = 4 * i + q;
-            const uint32_t r = widx / (uint32_t)txty, rem = widx % (uint32_t)txty;
-            const uint32_t col = rem % (uint32_t)tc.tx;
-            pos = (r / (KX / P)) << 28 | ((r % (KX / P)) * P + l) << 24 | (rem / (uint32_t)tc.tx) << 12 | col;
-            c = (wq >> (CB * l)) & C::CMASK;
-            why = kEmitPlain;
-            if (two_thr) {
-              why = (a.select == kSelectPlainAndPeaks && c - start >= a.n_min) ? kEmitPlain : 0u;
-              // neighbours already in registers: kx -/+ 1 in this word, and in
-              // the words of col -/+ 1 of the same row held by this uint4
-              bool beaten = false;
+      }
+      balance += (int64_t)acc - (int64_t)n_vec * 4 * P * start;
+      // Second pass: the counters with the top bit set are listed in s_peaks
+      // (as counter index widx * P + lane; slots from a block-wide scan of the
+      // per-thread counts, in batches of tc.peak_cap) and tested by groups of
+      // G threads each (G = 32 for a short list, down to 1 for a long one),
+      // whichever warps hold them; a group's threads split the 27 (ky, row,
+      // col) neighbour positions between them.
+      const uint32_t cap = (uint32_t)tc.peak_cap;
+      if (cap == 0) my_flags |= kFlagInternal;  // the plan reserves the list with peak selection
+      uint32_t n_top = 0, off = 0;
+      if (__syncthreads_or(cap != 0 && ntop != 0))  // one barrier for a tile with no candidate
+        off = block_scan(cap ? ntop : 0u, s_misc, n_top);
+      for (uint32_t b0 = 0; b0 < n_top; b0 += cap) {
+        const uint32_t n_list = min(n_top - b0, cap);
+        if (ntop && off < b0 + n_list && off + ntop > b0) {
+          uint32_t idx = off, rr = hit;
+          while (rr && idx < b0 + n_list) {
+            const uint32_t k = (uint32_t)(__ffs(rr) - 1);
+            rr &= rr - 1;
+            const uint4 v = reinterpret_cast<const uint4*>(cells)[k * kNT + tid];
+            uint32_t todo = 0;
 #pragma unroll
-              for (int dq = -1; dq <= 1; ++dq) {
-                const int q2 = q + dq;
-                if (q2 < 0 || q2 > 3 || (int)col + dq < 0 || (int)col + dq >= tc.tx) continue;
-                const uint32_t w2 = q2 == 0 ? v.x : q2 == 1 ? v.y : q2 == 2 ? v.z : v.w;
-#pragma unroll
-                for (int dl = -1; dl <= 1; ++dl) {
-                  const int l2 = l + dl;
-                  if (l2 < 0 || l2 >= P) continue;
-                  beaten |= ((w2 >> (CB * l2)) & C::CMASK) > c;
-                }
-              }
-              test = !beaten;
+            for (int l = 0; l < P; ++l) {
+              const int sh = CB * l + CB - 1;
+              todo |= ((v.x >> sh) & 1u) << l;
+              todo |= ((v.y >> sh) & 1u) << (P + l);
+              todo |= ((v.z >> sh) & 1u) << (2 * P + l);
+              todo |= ((v.w >> sh) & 1u) << (3 * P + l);
+            }
+            while (todo && idx < b0 + n_list) {
+              const int bb = __ffs(todo) - 1;
+              todo &= todo - 1;
+              if (idx >= b0) s_peaks[idx - b0] = (4u * (k * kNT + tid) + (uint32_t)(bb / P)) * P + (uint32_t)(bb % P);
+              ++idx;
             }
           }
-          if (two_thr) {
-            // Tile-local peak test of up to three counters per step: lanes
-            // 9g .. 9g + 8 take the g-th pending counter, lane 9g + j the
-            // neighbours at row + j/3 - 1, col + j%3 - 1, every ky - 1 .. ky + 1
-            // and kx - 1 .. kx + 1 of the tile.
-            uint32_t pend = __ballot_sync(0xffffffffu, test);
-            while (pend) {
-              const int grp = wl / 9;
-              const int mine = __popc(pend & lt_mask);  // this lane's rank among the pending ones
-              const bool tested = ((pend >> wl) & 1u) && mine < 3;
-              // the first three pending lanes (-1 past the last), then the rest
-              const int L0 = __ffs(pend) - 1;
-              pend &= pend - 1;
-              const int L1 = __ffs(pend) - 1;
-              pend &= pend - 1;
-              const int L2 = __ffs(pend) - 1;
-              pend &= pend - 1;
-              const int L = grp == 0 ? L0 : grp == 1 ? L1 : grp == 2 ? L2 : -1;
-              const int src = L >= 0 ? L : wl;
-              const uint32_t qpos = __shfl_sync(0xffffffffu, pos, src);
-              const uint32_t qc = __shfl_sync(0xffffffffu, c, src);
-              bool bigger = false;
-              if (L >= 0) {
-                const int qky = (int)(qpos >> 28), qkx = (int)((qpos >> 24) & 15u);
-                const int qrow = (int)((qpos >> 12) & 4095u), qcol = (int)(qpos & 4095u);
-                const int j = wl - 9 * grp;
-                const int r2 = qrow + j / 3 - 1, c2 = qcol + j % 3 - 1;
-                if (r2 >= 0 && r2 < tc.ty && c2 >= 0 && c2 < tc.tx) {
-                  const int xa = max(qkx - 1, 0), xb = min(qkx + 1, KX - 1);
-                  const uint32_t* wb = cells + (uint32_t)(r2 * tc.tx + c2);
-                  for (int ky2 = max(qky - 1, 0); ky2 <= min(qky + 1, KY - 1); ++ky2)
-                    for (int g2 = xa / P; g2 <= xb / P; ++g2) {
-                      const uint32_t w = wb[(uint32_t)(ky2 * (KX / P) + g2) * (uint32_t)txty];
-#pragma unroll
-                      for (int l2 = 0; l2 < P; ++l2) {
-                        const int kx2 = g2 * P + l2;
-                        if (kx2 >= xa && kx2 <= xb) bigger |= ((w >> (CB * l2)) & C::CMASK) > qc;
-                      }
-                    }
-                }
-              }
-              const uint32_t bm = __ballot_sync(0xffffffffu, bigger);
-              if (tested && !((bm >> (9 * mine)) & 0x1FFu)) why |= kEmitLowPeak;
-            }
-          }
+        }
+        __syncthreads();
+        const int G = n_list <= kNT / 32 ? 32 : n_list <= kNT / 8 ? 8 : n_list <= kNT / 4 ? 4 : 1;
+        const uint32_t gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
+        const int j = tid % G;
+        for (uint32_t e0 = 0; e0 < n_list; e0 += (uint32_t)(kNT / G)) {
+          const uint32_t e = e0 + (uint32_t)(tid / G);
+          uint32_t why = 0;
           Emit em;
-          em.v_idx = (uint32_t)(ky0 + (int)(pos >> 28)) * (uint32_t)g.nvx + (uint32_t)(kx0 + (int)((pos >> 24) & 15u));
-          em.bx = (uint32_t)bx0 + (pos & 4095u) * sbins;
-          em.by = (uint32_t)by0 + ((pos >> 12) & 4095u) * sbins;
-          em.flags = why;
+          bool bigger = false;
+          int kx = 0, ky = 0, row = 0, col = 0;
+          uint32_t c = 0;
+          if (e < n_list) {
+            const uint32_t ci = s_peaks[e];
+            const uint32_t widx = ci / P;
+            const int q = (int)(widx & 3u), l = (int)(ci % P);
+            const uint4 v = reinterpret_cast<const uint4*>(cells)[widx >> 2];
+            const uint32_t wq = q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+            c = (wq >> (CB * l)) & C::CMASK;
+            const uint32_t r = widx / (uint32_t)txty, rem_w = widx % (uint32_t)txty;
+            row = (int)(rem_w / (uint32_t)tc.tx);
+            col = (int)(rem_w % (uint32_t)tc.tx);
+            ky = (int)(r / (KX / P));
+            kx = (int)(r % (KX / P)) * P + l;
+            // neighbours already in registers: kx -/+ 1 in this word, and in
+            // the words of col -/+ 1 of the same row held by this uint4
+#pragma unroll
+            for (int dq = -1; dq <= 1; ++dq) {
+              const int q2 = q + dq;
+              if (q2 < 0 || q2 > 3 || col + dq < 0 || col + dq >= tc.tx) continue;
+              const uint32_t w2 = q2 == 0 ? v.x : q2 == 1 ? v.y : q2 == 2 ? v.z : v.w;
+#pragma unroll
+              for (int dl = -1; dl <= 1; ++dl) {
+                const int l2 = l + dl;
+                if (l2 < 0 || l2 >= P) continue;
+                bigger |= ((w2 >> (CB * l2)) & C::CMASK) > c;
+              }
+            }
+            if (!bigger) {
+              // this thread's share of the 27 positions (ky + t/9 - 1, row +
+              // (t/3)%3 - 1, col + t%3 - 1), every kx - 1 .. kx + 1 (the
+              // counter itself is not larger than itself)
+              const int xa = max(kx - 1, 0), xb = min(kx + 1, KX - 1);
+              for (int t = j; t < 27; t += G) {
+                const int ky2 = ky + t / 9 - 1, r2 = row + (t / 3) % 3 - 1, c2 = col + t % 3 - 1;
+                if (ky2 < 0 || ky2 >= KY || r2 < 0 || r2 >= tc.ty || c2 < 0 || c2 >= tc.tx) continue;
+                const uint32_t* wb = cells + (uint32_t)(r2 * tc.tx + c2) + (uint32_t)(ky2 * (KX / P)) * (uint32_t)txty;
+                for (int g2 = xa / P; g2 <= xb / P; ++g2) {
+                  const uint32_t w = wb[(uint32_t)g2 * (uint32_t)txty];
+#pragma unroll
+                  for (int l2 = 0; l2 < P; ++l2) {
+                    const int kx2 = g2 * P + l2;
+                    if (kx2 >= xa && kx2 <= xb) bigger |= ((w >> (CB * l2)) & C::CMASK) > c;
+                  }
+                }
+              }
+            }
+          }
+          const bool any_bigger = (__ballot_sync(0xffffffffu, bigger) & gmask) != 0u;
+          if (e < n_list && j == 0) {
+            why = (a.select == kSelectPlainAndPeaks && c - start >= a.n_min) ? kEmitPlain : 0u;
+            if (!any_bigger) why |= kEmitLowPeak;
+            em.v_idx = (uint32_t)(ky0 + ky) * (uint32_t)g.nvx + (uint32_t)(kx0 + kx);
+            em.bx = (uint32_t)bx0 + (uint32_t)col * sbins;
+            em.by = (uint32_t)by0 + (uint32_t)row * sbins;
+            em.flags = why;
+          }
           const uint32_t m = __ballot_sync(0xffffffffu, why != 0);
           if (!m) continue;
           const int lead = __ffs(m) - 1;
@@ -725,12 +732,12 @@ __device__ __forceinline__ void run_unit(const StackArgs& a, uint64_t unit, unsi
             }
           }
         }
+        __syncthreads();  // the list's reads before its next batch
       }
-      balance += (int64_t)acc - (int64_t)n_vec * 4 * P * start;
       __syncthreads();
-      while (deferred) {  // every peak test has read its neighbours
-        const uint32_t k = (uint32_t)(__ffs(deferred) - 1);
-        deferred &= deferred - 1;
+      while (hit) {  // every peak test has read its neighbours
+        const uint32_t k = (uint32_t)(__ffs(hit) - 1);
+        hit &= hit - 1;
         reinterpret_cast<uint4*>(cells)[k * kNT + tid] = start4;
       }
       const uint32_t ne_tile = min(s_misc[43], (uint32_t)tc.emit_cap);
