@@ -205,13 +205,14 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                    reps: int = 2) -> dict:
     """fields/s on the batched uneven fields (60 CCDs, epochs U{20..150}, noise
     log-U[1e3, 8e3]): the plain form (one sas_stack per field at N_min =
-    ceil(E/4)) against the batched + vetted form (one graph-captured batch
+    ceil(E/4)) against the batched + vetted forms (one graph-captured batch
     pass with the autotuner's per-size-class tiles, then ownership selection,
-    stamps and the CNN), at the plain
-    threshold and at the lowered one (sas_batch_vet: ownership, stamps and CNN of
-    all fields in one pass); recall per 0.5-mag bin and purity of each
-    form's reported candidates.  The vetter is trained first (not timed) on
-    separate seeded fields."""
+    stamps and the CNN of all fields in one pass, sas_batch_vet): at the plain
+    threshold, at a lowered one, with the tile-local super-bin peaks at a
+    lowered threshold added to the plain list, and with the peaks alone (the
+    cells every mover raises around its best cell pruned before counting);
+    recall per 0.5-mag bin and purity of each form's reported candidates.  The
+    vetter is trained first (not timed) on separate seeded fields."""
     import torch
     from paper_2509_26279_gb300 import sas, vetting
 
@@ -281,14 +282,26 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     tune_s = time.perf_counter() - t1
     tuned_opts = [cache.opts_for(f) for f in fields]
 
-    def make_batch(thr, low=None):
-        opts = tuned_opts
-        if low is not None:
-            opts = []
-            for f, o in zip(fields, tuned_opts):
-                o2 = sas.make_opts(**{k: getattr(o, k) for k, _ in sas.sas_opts._fields_})
-                o2.n_low = low(f)
-                opts.append(o2)
+    def lowered(div):
+        # ceil(E/div), raised to the field's noise floor (vetting.lowered_threshold)
+        return lambda f: vetting.lowered_threshold(f.E, f.w.n_min, f.cat.n, f.w.grid, div)
+
+    # the peaks-only form at the lowered threshold gets its own tuning pass: the
+    # peak tests and the smaller count stage change what each tile shape costs
+    t2 = time.perf_counter()
+    po_tag = "peaks_only_e6:"
+    for f in fields:
+        cache.tune(f, gpu_name, base=sas.make_opts(n_low=lowered(6)(f), peaks_only=1), tag=po_tag)
+    tune_po_s = time.perf_counter() - t2
+    po_opts = [cache.opts_for(f, po_tag) for f in fields]
+
+    def make_batch(thr, low=None, peaks_only=0, opts_base=None):
+        opts = []
+        for f, o in zip(fields, opts_base or tuned_opts):
+            o2 = sas.make_opts(**{k: getattr(o, k) for k, _ in sas.sas_opts._fields_})
+            o2.n_low = low(f) if low is not None else 0
+            o2.peaks_only = peaks_only
+            opts.append(o2)
         return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
                          opts=opts, stream=stream)
 
@@ -307,7 +320,7 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                           f"noise/epoch log-U[1e3,8e3], 200 movers each, 111x111 lattice, bin 2 px",
               "plain": {"form": "one sas_stack per field, N_min = ceil(E/4)", "ms": round(ms_plain, 3),
                         "fields_per_s": round(n_fields / (ms_plain * 1e-3), 2), **score(plain_out)},
-              "autotune": {"classes": len(cache.entries), "seconds": round(tune_s, 1),
+              "autotune": {"classes": len(cache.entries), "seconds": round(tune_s + tune_po_s, 1),
                            "choices": {k: tuning.shape_of(v) for k, v in cache.entries.items()},
                            "ms": {k: v["ms"] for k, v in cache.entries.items()},
                            "planner_ms": {k: v.get("planner_ms") for k, v in cache.entries.items()},
@@ -319,20 +332,22 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
                                   "threshold_rule": "purity 0.95 on 10 separate calibration fields"}}
     e4 = lambda f: f.w.n_min
     e6 = lambda f: -(-f.E // 6)
-    e8 = lambda f: -(-f.E // 8)
-    e14 = lambda f: vetting.n_low(f.E)
-    for name, thr, low, desc in (
-            ("batched_vetted", e4, None, "batch at N_min = ceil(E/4)"),
-            ("batched_vetted_e6", e6, None, "batch at N_min = ceil(E/6)"),
-            ("batched_vetted_e8", e8, None, "batch at N_min = ceil(E/8)"),
-            ("batched_vetted_low", e14, None, "batch at N_min = max(5, ceil(E/14))"),
-            ("batched_peaks_e6", e4, e6, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
-                                         "at n_low = ceil(E/6)"),
-            ("batched_peaks_e8", e4, e8, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
-                                         "at n_low = ceil(E/8)"),
-            ("batched_peaks_low", e4, e14, "batch at N_min = ceil(E/4) plus the tile-local super-bin peaks "
-                                           "at n_low = max(5, ceil(E/14))")):
-        batch = make_batch(thr, low)
+    floor_note = " (raised to the field's noise floor: fewer than 5e4 expected noise pairs)"
+    for name, thr, low, po, obase, desc in (
+            ("batched_vetted", e4, None, 0, None, "batch at N_min = ceil(E/4)"),
+            ("batched_vetted_e6", e6, None, 0, None, "batch at N_min = ceil(E/6)"),
+            ("batched_peaks_e6", e4, lowered(6), 0, None,
+             "batch at N_min = ceil(E/4) plus the cells of tile-local super-bin peaks at n_low = ceil(E/6)"
+             + floor_note),
+            ("batched_peaksonly_e4", e4, None, 1, None,
+             "batch keeping only the cells of tile-local super-bin peaks, at N_min = ceil(E/4)"),
+            ("batched_peaksonly_e5", e4, lowered(5), 1, po_opts,
+             "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/5)" + floor_note),
+            ("batched_peaksonly_e6", e4, lowered(6), 1, po_opts,
+             "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/6)" + floor_note),
+            ("batched_peaksonly_e8", e4, lowered(8), 1, po_opts,
+             "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/8)" + floor_note)):
+        batch = make_batch(thr, low, po, obase)
         batch.run(stream)
         cap = sum(max(batch.field_info(k)["n_candidates"], 1) for k in range(len(fields))) + 1
         ms, (fo, co, lo) = timed(vetted_pass(batch, cap))
@@ -347,9 +362,10 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
             dd[idx[vetting.vetted_keep(c["count"][idx], lo[sel], fields[k].w.n_min, tau)]] = True
             per_field_dedup.append((c, i, dd))
         _, fallbacks = batch.stats()
-        result[name] = {"form": desc + "; every candidate with count >= ceil(E/4) kept, plus the "
+        result[name] = {"form": desc + "; every reported candidate with count >= ceil(E/4) kept, plus the "
                                        "ownership-selected candidates below it whose CNN logit >= the "
                                        "calibrated threshold",
+                        "tiles": "tuned for this form" if obase is not None else "tuned at N_min",
                         "ms": round(ms, 3),
                         "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
                         "rebuilds": int(batch.rebuilds),

@@ -66,21 +66,24 @@ class TuneCache:
     def lookup(self, key: str):
         return self.entries.get(key)
 
-    def tune(self, field, device_name: str = "", reps: int = 3) -> dict:
+    def tune(self, field, device_name: str = "", reps: int = 3, base=None, tag: str = "") -> dict:
         """Entry of field's class, measured with sas_autotune if missing.
         field: an object with grid (sas.Grid), w (workload: grid spec, n_min),
-        cat, dx, dy, de (device catalog) and E -- e.g. vetting.Field."""
+        cat, dx, dy, de (device catalog) and E -- e.g. vetting.Field.  base:
+        sas_opts the search runs with besides the tiles (e.g. n_low and
+        peaks_only, which change what the tiles cost); tag: prefix of the class
+        key that keeps such entries apart."""
         from . import sas
-        key = size_class(field.E, field.cat.n, field.w.grid, field.w.n_min)
+        key = tag + size_class(field.E, field.cat.n, field.w.grid, field.w.n_min)
         if key not in self.entries:
             best, ms = sas.sas_autotune(field.grid, field.dx, field.dy, field.de, field.cat.t,
-                                        field.cat.ticks_per_hour, field.w.n_min, reps=reps)
+                                        field.cat.ticks_per_hour, field.w.n_min, base=base, reps=reps)
             # the planner's own choice on the same field, timed the same way (device
             # time of the whole search, median of reps after one warm-up)
             ts = []
             for r in range(reps + 1):
                 res = sas.sas_stack(field.grid, field.dx, field.dy, field.de, field.cat.t,
-                                    field.cat.ticks_per_hour, field.w.n_min, on_device=True)
+                                    field.cat.ticks_per_hour, field.w.n_min, on_device=True, opts=base)
                 if r:
                     ts.append(res.info()["ms_total"])
                 res.free()
@@ -91,10 +94,10 @@ class TuneCache:
                                  "device": device_name}
         return self.entries[key]
 
-    def opts_for(self, field):
+    def opts_for(self, field, tag: str = ""):
         """sas_opts for a field from its class entry (planner defaults if none)."""
         from . import sas
-        e = self.lookup(size_class(field.E, field.cat.n, field.w.grid, field.w.n_min))
+        e = self.lookup(tag + size_class(field.E, field.cat.n, field.w.grid, field.w.n_min))
         if e is None:
             return sas.make_opts()
         return sas.make_opts(**{k: e.get(k, 0) for k in OPTION_KEYS})
