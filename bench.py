@@ -26,8 +26,10 @@ N_min = 25.  The metric is detection-shifts per second: in-domain
 
 --impl reference times the CPU oracle (the plain definition; its OpenMP form
 over velocity chunks on all host cores) on a bounded lattice sample of the same
-workload.  --vetter-timing and --refine-timing print only the timing of the
-vetter's kernels or of refinement (the commands the profiles were taken with).
+workload.  --vetter-timing, --refine-timing and --selection-timing print only
+the timing of the vetter's kernels, of refinement, or of the stack kernel with
+one threshold and with the peaks alone (the commands the profiles were taken
+with).
 Multi-GPU (torchrun): each rank searches its own field (weak scaling); the
 only collectives are the timing barrier and the max over ranks.
 """
@@ -127,11 +129,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+STACK_SOURCES = ("sas_stack_kernel.cuh", "sas_stack.cu")  # the kernel and its one-threshold instantiations
+
+
+def stack_source_sha256() -> str:
+    """sha256 over the stack kernel's source files, in STACK_SOURCES order."""
+    h = hashlib.sha256()
+    for name in STACK_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2509_26279_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def stack_traffic(workload: str):
     """DRAM bytes per stack launch from the committed ncu summary of this
     workload, if it was taken on the current stack kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"k_stack_{workload}.md")
-    src = os.path.join(ROOT, "paper_2509_26279_gb300", "csrc", "sas_stack.cu")
     if not os.path.exists(p):
         return None
     fields = {}
@@ -139,7 +151,7 @@ def stack_traffic(workload: str):
         k, sep, v = line.strip().partition(":")
         if sep and k in ("stack_source_sha256", "traffic_bytes_per_launch"):
             fields[k] = v.strip()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = stack_source_sha256()
     if fields.get("stack_source_sha256") != h or "traffic_bytes_per_launch" not in fields:
         return None
     return int(fields["traffic_bytes_per_launch"])
@@ -617,6 +629,30 @@ def vetter_timing(dev, stream, n_forward: int = 32768, batch: int = 4096, reps: 
             "timing": f"CUDA events on the launching stream, best of {reps} after one warm-up"}
 
 
+def selection_timing(dev, stream, reps: int = 5) -> dict:
+    """The stack kernel with one threshold and with the tile-local peaks alone
+    on one of the batched uneven fields (100 epochs, 423402 detections, N_min
+    = 25; n_low = ceil(E/6) raised to the field's noise floor): device time of
+    the kernel (ms_stack, median of reps after one warm-up), super-bins
+    emitted, candidates."""
+    from paper_2509_26279_gb300 import sas, vetting
+    f = vetting.Field(W.batched_fields(60)[0], dev)
+    out = {"workload": f"batched_fields[0]: {f.E} epochs, {f.cat.n} detections, 111x111 lattice, N_min {f.w.n_min}"}
+    n_low = vetting.lowered_threshold(f.E, f.w.n_min, f.cat.n, f.w.grid, 6)
+    for tag, o in (("one_threshold", sas.make_opts()), ("peaks_only", sas.make_opts(n_low=n_low, peaks_only=1))):
+        ms = []
+        for i in range(reps + 1):
+            res = sas.sas_stack(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, f.w.n_min, on_device=True,
+                                opts=o, stream=stream)
+            inf = res.info()
+            if i:
+                ms.append(inf["ms_stack"])
+            res.free()
+        out[tag] = {"n_low": int(inf["n_low"]), "ms_stack": round(statistics.median(ms), 4),
+                    "superbins_emitted": int(inf["n_emitted"]), "candidates": int(inf["n_candidates"])}
+    return out
+
+
 def refine_timing(dev, stream, reps: int = 5) -> dict:
     """Cluster finding and refinement on one search of the DECam TNO field:
     sas_peel, then sas_refine with one fit round and with the default loop,
@@ -714,6 +750,8 @@ def main():
                     help="only time the vetter's forward and training kernels and print that line")
     ap.add_argument("--refine-timing", action="store_true",
                     help="only time cluster finding's refinement on the TNO field and print that line")
+    ap.add_argument("--selection-timing", action="store_true",
+                    help="only time the stack kernel with one threshold and with the peaks alone on one field")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -732,12 +770,13 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.vetter_timing or args.refine_timing:
+    if args.vetter_timing or args.refine_timing or args.selection_timing:
         stream = torch.cuda.current_stream(dev)
         if rank == 0:
-            fn = vetter_timing if args.vetter_timing else refine_timing
-            print(json.dumps({"mode": "vetter_timing" if args.vetter_timing else "refine_timing",
-                              **fn(dev, stream)}), flush=True)
+            mode, fn = (("vetter_timing", vetter_timing) if args.vetter_timing else
+                        ("refine_timing", refine_timing) if args.refine_timing else
+                        ("selection_timing", selection_timing))
+            print(json.dumps({"mode": mode, **fn(dev, stream)}), flush=True)
         return 0
 
     w = getattr(W, args.workload)()
