@@ -22,3 +22,23 @@ def test_cache_round_trip(tmp_path):
     c2 = tuning.TuneCache(p)
     assert c2.lookup("E4-d11-v111x111-b2000-f2")["superbin"] == 3
     assert json.load(open(p)) == c.entries
+
+
+def test_tagged_entries_are_kept_apart():
+    """Entries tuned for another search form live under their own key prefix."""
+    from paper_2509_26279_gb300 import workloads as W
+
+    class F:
+        pass
+
+    w = W.batched_fields(1)[0]
+    f = F()
+    f.E, f.w = w.recipe.n_epochs, w
+    f.cat = W.load(w)
+    c = tuning.TuneCache()
+    key = tuning.size_class(f.E, f.cat.n, w.grid, w.n_min)
+    c.entries[key] = {"tile_kx": 8, "tile_ky": 8, "superbin": 3, "tile_bx": 0, "tile_by": 0, "velocity_block": 0}
+    c.entries["peaks_only_e6:" + key] = {"tile_kx": 8, "tile_ky": 4, "superbin": 4, "tile_bx": 64, "tile_by": 0,
+                                         "velocity_block": 2}
+    assert c.lookup(key)["superbin"] == 3
+    assert c.lookup("peaks_only_e6:" + key)["superbin"] == 4
