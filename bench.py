@@ -309,13 +309,38 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
 
     def make_batch(thr, low=None, peaks_only=0, opts_base=None):
         opts = []
-        for f, o in zip(fields, opts_base or tuned_opts):
+        for f, o in zip(fields, opts_base):
             o2 = sas.make_opts(**{k: getattr(o, k) for k, _ in sas.sas_opts._fields_})
             o2.n_low = low(f) if low is not None else 0
             o2.peaks_only = peaks_only
             opts.append(o2)
         return sas.Batch([(f.grid, f.dx, f.dy, f.de, f.cat.t, f.cat.ticks_per_hour, thr(f)) for f in fields],
                          opts=opts, stream=stream)
+
+    planner_opts = [sas.make_opts() for _ in fields]
+
+    def pick_batch(thr, low, peaks_only, tuned):
+        """The batch built with the autotuner's per-class tiles or with the
+        planner's, whichever replays faster (the tuner times single searches;
+        its choice does not always carry over to one pass over all fields).
+        Untimed: one warm-up and two timed replays of each."""
+        best = None
+        for label, ob in (("autotuned", tuned), ("planner", planner_opts)):
+            b = make_batch(thr, low, peaks_only, ob)
+            b.run(stream)
+            ts = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                b.run(stream)
+                ts.append(time.perf_counter() - t)
+            if best is None or min(ts) < best[0]:
+                if best is not None:
+                    best[2].destroy()
+                best = (min(ts), label, b)
+            else:
+                b.destroy()
+        return best[2], best[1]
 
     def vetted_pass(batch, cap):
         fo = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -346,12 +371,12 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
     e6 = lambda f: -(-f.E // 6)
     floor_note = " (raised to the field's noise floor: fewer than 5e4 expected noise pairs)"
     for name, thr, low, po, obase, desc in (
-            ("batched_vetted", e4, None, 0, None, "batch at N_min = ceil(E/4)"),
-            ("batched_vetted_e6", e6, None, 0, None, "batch at N_min = ceil(E/6)"),
-            ("batched_peaks_e6", e4, lowered(6), 0, None,
+            ("batched_vetted", e4, None, 0, tuned_opts, "batch at N_min = ceil(E/4)"),
+            ("batched_vetted_e6", e6, None, 0, tuned_opts, "batch at N_min = ceil(E/6)"),
+            ("batched_peaks_e6", e4, lowered(6), 0, tuned_opts,
              "batch at N_min = ceil(E/4) plus the cells of tile-local super-bin peaks at n_low = ceil(E/6)"
              + floor_note),
-            ("batched_peaksonly_e4", e4, None, 1, None,
+            ("batched_peaksonly_e4", e4, None, 1, tuned_opts,
              "batch keeping only the cells of tile-local super-bin peaks, at N_min = ceil(E/4)"),
             ("batched_peaksonly_e5", e4, lowered(5), 1, po_opts,
              "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/5)" + floor_note),
@@ -359,7 +384,10 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
              "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/6)" + floor_note),
             ("batched_peaksonly_e8", e4, lowered(8), 1, po_opts,
              "batch keeping only the cells of tile-local super-bin peaks, at n_low = ceil(E/8)" + floor_note)):
-        batch = make_batch(thr, low, po, obase)
+        if name == "batched_vetted_e6":  # the slow one-threshold comparison: the tuned tiles only
+            batch, tiles = make_batch(thr, low, po, obase), "autotuned"
+        else:
+            batch, tiles = pick_batch(thr, low, po, obase)
         batch.run(stream)
         cap = sum(max(batch.field_info(k)["n_candidates"], 1) for k in range(len(fields))) + 1
         ms, (fo, co, lo) = timed(vetted_pass(batch, cap))
@@ -377,7 +405,8 @@ def fields_section(dev, stream, n_fields: int = 60, train_fields: int = 30, epoc
         result[name] = {"form": desc + "; every reported candidate with count >= ceil(E/4) kept, plus the "
                                        "ownership-selected candidates below it whose CNN logit >= the "
                                        "calibrated threshold",
-                        "tiles": "tuned for this form" if obase is not None else "tuned at N_min",
+                        "tiles": tiles if tiles == "planner" else
+                        ("autotuned for this form" if obase is po_opts else "autotuned at N_min"),
                         "ms": round(ms, 3),
                         "fields_per_s": round(n_fields / (ms * 1e-3), 2), "fallbacks": int(fallbacks),
                         "rebuilds": int(batch.rebuilds),
