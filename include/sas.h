@@ -280,7 +280,8 @@ int sas_batch_owned(const sas_batch* batch, uint32_t field, uint32_t n_keep, uin
 typedef struct sas_vet sas_vet;
 
 /* Vetting of every field of the last run in one pass: ownership selection
- * (as sas_owned with n_keep = the field's n_min), stamps of the kept candidates and their CNN logits (as
+ * (as sas_owned with n_keep = the field's n_low, which is its n_min when the
+ * field has no lower threshold), stamps of the kept candidates and their CNN logits (as
  * sas_vet_forward).  Writes one item per kept candidate: field_out[i],
  * cand_out[i] (its index in the field's candidate list) and logit_out[i]
  * (device arrays with room for `cap` items; the batch's total candidate count
