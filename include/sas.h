@@ -184,7 +184,8 @@ int sas_grid_get_desc(const sas_grid* grid, sas_grid_desc* desc);
  * sas_candidate.count holds the score.  Everything else as sas_stack; the
  * result supports sas_candidates, sas_stamps and sas_refine (not sas_peel,
  * whose recounts are distinct epochs).  s_min in [1, 2^31].
- * Errors: as sas_stack; SAS_ERR_ARG for null weights with n > 0. */
+ * Errors: as sas_stack; SAS_ERR_ARG for null weights with n > 0, or for
+ * opts->n_low or opts->peaks_only set (peak selection counts distinct epochs). */
 int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8_t* weights, uint32_t s_min,
                        const sas_opts* opts, void* stream, sas_result** out);
 
@@ -211,7 +212,8 @@ int sas_stack_weighted(const sas_grid* grid, const sas_catalog* cat, const uint8
  * cudaStream_t (NULL = legacy default).  On success *out holds a new result
  * that the caller releases with sas_result_free; the result owns its device
  * memory.  The call synchronizes the stream before returning.
- * Errors: SAS_ERR_ARG, SAS_ERR_RANGE (catalog or shifts out of limits, or an
+ * Errors: SAS_ERR_ARG (also n_low > n_min, peaks_only > 1, tile sides of
+ * 4096 super-bins or more), SAS_ERR_RANGE (catalog or shifts out of limits, or an
  * epoch index >= n_epochs), SAS_ERR_OOM, SAS_ERR_CUDA; *out is untouched. */
 int sas_stack(const sas_grid* grid, const sas_catalog* cat, uint32_t n_min,
               const sas_opts* opts, void* stream, sas_result** out);
@@ -243,7 +245,8 @@ void sas_result_free(sas_result* result);
  *
  * grids[f], cats[f], n_min[f]: field f (catalogs in device memory, on_device
  * = 1, n >= 1; 1 <= n_min <= 128).  opts: NULL or an array of n_fields option
- * sets (v_begin/v_end are ignored; n_low as in sas_stack, per field).  The
+ * sets (v_begin/v_end are ignored; n_low and peaks_only as in sas_stack, per
+ * field).  The
  * batch keeps the catalogs' device pointers:
  * the caller may rewrite their contents between runs (same sizes, same
  * epoch times) and must keep them alive until sas_batch_destroy.
